@@ -1,0 +1,186 @@
+/*
+ * smi.h -- C ABI of the GB300 staggered-grid acoustic modelling / RTM /
+ * FWI-gradient library (libsmi.so, CUDA, sm_103a).
+ *
+ * Method: SMIwiz, arXiv 2311.02293.  The library computes, on one GPU:
+ *   smi_forward      seismograms of the first-order acoustic system
+ *                    (Sec. 2.1, Eq. acoustic and its leap-frog update
+ *                    equations) with CPML layers, Kaiser-sinc source
+ *                    injection / receiver extraction and the dynamic
+ *                    computing box (Sec. 4.1);
+ *   smi_rtm          the zero-lag cross-correlation image (Sec. 2.3,
+ *                    Eq. rtmimage), the observed data back-propagated as
+ *                    the adjoint source;
+ *   smi_fwi_gradient the least-squares misfit (Eq. objfwi) and its exact
+ *                    discrete gradient with respect to Vp (Eq.
+ *                    gradrhokappa via kappa = rho Vp^2), Algorithm 2, with
+ *                    the source field rebuilt backwards from saved
+ *                    boundaries (Sec. 4.2, dr = 1).
+ *
+ * Conventions
+ *   - Axes: n1 = z (fastest), n2 = x, n3 = y (Sec. 3.6).  A 2D model has
+ *     n3 = 1.  Model arrays hold n1*n2*n3 floats, z fastest.
+ *   - Positions: metres (z, x, y) from the first physical node (Sec. 3.4).
+ *     A position within 1e-6 cells of a node uses that node alone; other
+ *     positions use the Kaiser-windowed sinc of radius order/2 (Sec. 3.8).
+ *   - Seismograms: for shot s, nt x nrec_s floats (receiver fastest) at
+ *     offset nt * rec_offset[s]; sample it holds p at time (it+1) dt.
+ *   - The extended grid adds nb CPML layers on every face; the model is
+ *     extended into them by copying the nearest physical value.
+ *
+ * Pointers
+ *   Model arrays, the wavelet, observed data and every output may be host
+ *   or device pointers (the library asks the CUDA runtime which); geometry
+ *   arrays are always host pointers.  The caller owns all of them.  The
+ *   library allocates its working state (wavefields, CPML slabs, saved
+ *   boundaries, tables) on the device with stream-ordered allocations on
+ *   opts->stream and frees it before returning.
+ *
+ * Calls are blocking: each returns after its work on opts->stream has
+ * finished.  Calls on different streams from different host threads may
+ * run concurrently on the GPU.
+ *
+ * Errors: every int-returning call returns SMI_OK (0) or a negative
+ * SMI_ERR_* code and records a message readable with smi_last_error() on
+ * the calling thread.  No call exits the process.
+ */
+#ifndef SMI_H
+#define SMI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SMI_OK 0
+#define SMI_ERR_ARG (-1)          /* bad size, option, pointer or position */
+#define SMI_ERR_CFL (-2)          /* Eq. cfl violated (Sec. 3.8: the paper stops) */
+#define SMI_ERR_DISPERSION (-3)   /* too few points per wavelength (Sec. 3.8) */
+#define SMI_ERR_NOMEM (-4)        /* device allocation failed / over budget */
+#define SMI_ERR_UNSTABLE (-5)     /* a non-finite value appeared */
+#define SMI_ERR_TIMEOUT (-6)      /* a bounded device wait gave up */
+#define SMI_ERR_CUDA (-7)         /* a CUDA runtime call failed */
+#define SMI_ERR_UNSUPPORTED (-8)  /* option outside this build (freesurf, dr > 1) */
+
+/* Storage precision of the saved boundaries (Sec. 4.2). */
+#define SMI_PREC_F32 0
+#define SMI_PREC_F16 1            /* FP16 with one FP32 scale per step, face and axis */
+#define SMI_PREC_BF16 2           /* BF16 with the same scaling */
+
+/* Velocity model (Secs. 2.1, 3.5, 3.6).  vp, rho: n1*n2*n3 floats, z
+ * fastest, host or device, strictly positive.  kappa = rho vp^2. */
+typedef struct {
+    int ndim;                 /* 2 or 3 */
+    int n1, n2, n3;           /* physical sizes z, x, y (n3 = 1 in 2D) */
+    double d1, d2, d3;        /* grid spacings in metres (d3 unused in 2D) */
+    const float *vp;
+    const float *rho;
+} smi_model;
+
+/* Acquisition (Sec. 3.4): one pressure source per shot and its receivers,
+ * stored like the paper's acquisition file (z, x, y per line) in CSR form.
+ * All host pointers. */
+typedef struct {
+    int nshot;
+    const double *src;        /* [nshot][3] source position (z, x, y) in metres */
+    const int *rec_offset;    /* [nshot + 1] receivers of shot s: rec_offset[s] .. rec_offset[s+1]-1 */
+    const double *rec;        /* [rec_offset[nshot]][3] receiver positions */
+} smi_geometry;
+
+/* Source time function (Sec. 3.5): nt samples, stf[it] applied at step it
+ * as p += dt * stf[it] * w / dV over the source stencil.  Host or device. */
+typedef struct {
+    int nt;                   /* time steps */
+    double dt;                /* time step (s) */
+    double fm;                /* centre frequency (Hz): CPML alpha and the dispersion check */
+    const float *stf;
+} smi_wavelet;
+
+/* Scheme options (Secs. 3.6, 3.8, 4.1, 4.2).  Fill with smi_opts_default(). */
+typedef struct {
+    int order;                /* 4 or 8 (FD order in space, Sec. 3.8) */
+    int nb;                   /* CPML layers per face, >= order/2 (paper: 20) */
+    int freesurf;             /* 0 only (free surface is not built: SMI_ERR_UNSUPPORTED) */
+    int dr;                   /* boundary decimation ratio: 1 only (SMI_ERR_UNSUPPORTED otherwise) */
+    int use_box;              /* dynamic computing box (Sec. 4.1), 1 = on */
+    int shell_prec;           /* SMI_PREC_* storage of the saved boundaries */
+    double kaiser_b;          /* Kaiser window shape (default 4.0) */
+    double cpml_R;            /* CPML target reflection (default 1e-3; 1 = no absorption) */
+    void *stream;             /* cudaStream_t to run on; NULL = the legacy default stream */
+    int max_batch;            /* shots propagated together in one launch; 0 = automatic */
+    int profile;              /* 1: time the stencil kernels with CUDA events (smi_last_stats) */
+} smi_opts;
+
+/* Per-call measurements, filled for the calling thread's last call.  Index
+ * 0 = forward stencil steps, 1 = adjoint stencil steps, 2 = source-field
+ * reconstruction steps (with the fused imaging / gradient accumulation). */
+typedef struct {
+    double point_updates;     /* grid points advanced one step, summed over all propagations */
+    double bytes[3];          /* algorithmic HBM bytes of those steps (FP32: 40 B per 3D point,
+                                 32 B per 2D point, +16 B per CPML axis at slab points;
+                                 reconstruction 52 B (3D) / 44 B (2D) with the accumulator) */
+    double ms[3];             /* summed CUDA-event time of those steps (opts.profile = 1) */
+    long long steps[3];       /* stencil steps taken (per shot) */
+    long long kernel_launches;   /* every kernel the call launched */
+    double device_bytes;      /* peak device memory allocated by the call (set-up arena) */
+    long long band_values;    /* boundary values saved per shot per step (0 for forward) */
+} smi_stats;
+
+/* Fills *o with: order 4, nb 20, freesurf 0, dr 1, use_box 1, FP32
+ * boundaries, kaiser_b 4.0, cpml_R 1e-3, default stream, automatic batch,
+ * no profiling. */
+void smi_opts_default(smi_opts *o);
+
+/* Forward modelling, Algorithm 2 forward loop (Sec. 2.1; box Sec. 4.1).
+ * seis: sum_s nt*nrec_s floats (layout above), host or device, written. */
+int smi_forward(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                const smi_opts *opts, float *seis);
+
+/* RTM image, Eq. rtmimage with the observed data as adjoint source
+ * (Sec. 2.3; Algorithm 2).  dobs: observed seismograms (seis layout).
+ * image: n1*n2*n3 floats, written with sum_s sum_it kappa*pbar * p at equal
+ * time levels, pbar being the exact discrete adjoint field. */
+int smi_rtm(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+            const smi_opts *opts, const float *dobs, float *image);
+
+/* FWI misfit J = 1/2 sum (u - d)^2 over shots, receivers and samples
+ * (Eq. objfwi) and its gradient with respect to Vp on the physical grid
+ * (Eq. gradrhokappa, exact for the discrete scheme, CPML-layer model held
+ * fixed), Algorithm 2.  misfit: one double, host or device.  grad_vp:
+ * n1*n2*n3 floats, host or device.  Either may be NULL. */
+int smi_fwi_gradient(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                     const smi_opts *opts, const float *dobs, double *misfit, float *grad_vp);
+
+/* Sizes a caller needs before a call: seismogram floats, image floats and
+ * the device bytes the call will allocate (kind: 0 forward, 1 rtm, 2
+ * gradient).  Validates like the calls themselves (CFL, dispersion,
+ * positions) and launches one small reduction to find vmin/vmax.  Any
+ * output pointer may be NULL. */
+int smi_query(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+              const smi_opts *opts, int kind, size_t *seis_elems, size_t *image_elems,
+              size_t *device_bytes);
+
+/* Computing-box bounds (Sec. 4.1) as the kernels compute them on the
+ * device: for shot `shot`, the box around its source (which = 0) or its
+ * receivers (which = 1) after n = n0 .. n0+count-1 steps.  lo, hi: host
+ * [count][3] ints, inclusive extended-grid indices in axis order z, x, y;
+ * an empty box has hi < lo. */
+int smi_box_table(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                  const smi_opts *opts, int shot, int which, int n0, int count, int *lo, int *hi);
+
+/* Measurements of the calling thread's last smi_forward / smi_rtm /
+ * smi_fwi_gradient call. */
+int smi_last_stats(smi_stats *st);
+
+/* Message of the calling thread's last error ("" after success). */
+const char *smi_last_error(void);
+
+/* Library version and target, e.g. "smi 0.1 sm_103a". */
+const char *smi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMI_H */

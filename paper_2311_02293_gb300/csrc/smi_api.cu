@@ -1,0 +1,721 @@
+// smi_api.cu -- the C ABI of libsmi (include/smi.h) and the per-call driver:
+// validation, set-up, shot batching and the forward / reverse time loops of
+// Algorithm 2 (SMIwiz, arXiv 2311.02293).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "smi_box.h"
+#include "smi_internal.h"
+
+namespace smi {
+namespace {
+
+thread_local std::string t_err;
+thread_local smi_stats t_stats;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Stream-ordered device allocations of one call, released in the destructor.
+struct Arena {
+    cudaStream_t st;
+    std::vector<std::pair<void *, size_t>> ptrs;
+    size_t cur = 0, peak = 0;
+    bool ok = true;
+    explicit Arena(cudaStream_t s) : st(s) {}
+    void *raw(size_t bytes)
+    {
+        bytes = std::max<size_t>(bytes, 256);
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+            return nullptr;
+        }
+        ptrs.emplace_back(p, bytes);
+        cur += bytes;
+        peak = std::max(peak, cur);
+        return p;
+    }
+    template <class T> T *get(size_t n) { return static_cast<T *>(raw(n * sizeof(T))); }
+    ~Arena()
+    {
+        for (auto &pr : ptrs) cudaFreeAsync(pr.first, st);
+    }
+};
+
+struct Setup {
+    Grid g{};
+    int ndim = 0, n[3] = {1, 1, 1};
+    int nshot = 0, nt = 0;
+    long long nrec_total = 0;
+    std::vector<int> rec_offset;
+    std::vector<Stencil> src_st, rec_st;
+    std::vector<int> box_src, box_rec;      // [nshot][6]
+    float vmin = 0, vmax = 0;
+    double src_scale = 0;                   // dt / dV
+    const float *vp = nullptr, *rho = nullptr, *stf = nullptr;   // device
+    // device tables
+    Stencil *d_src = nullptr, *d_rec = nullptr;
+    int *d_box_src = nullptr, *d_box_rec = nullptr;
+    Bands bands{};
+};
+
+int classify_and_upload(Arena &ar, const float *p, size_t n, const float **dev, cudaStream_t st)
+{
+    if (is_device_ptr(p)) {
+        *dev = p;
+        return SMI_OK;
+    }
+    float *d = ar.get<float>(n);
+    if (!d) return fail(SMI_ERR_NOMEM, "device allocation of %zu bytes failed", n * sizeof(float));
+    if (cudaMemcpyAsync(d, p, n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return fail(SMI_ERR_CUDA, "host-to-device copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+    *dev = d;
+    return SMI_OK;
+}
+
+// Nominal stencil extent along each axis (the box is grown around it).
+void stencil_extent(const Grid &g, const Stencil &s, int lo[3], int hi[3])
+{
+    for (int a = 0; a < 3; a++) {
+        if (a >= g.ndim) { lo[a] = hi[a] = 0; continue; }
+        if (s.cnt[a] == 1) {
+            lo[a] = s.first[a] - g.ri + 1;
+            hi[a] = s.first[a] + g.ri;
+        } else {
+            lo[a] = s.first[a];
+            hi[a] = s.first[a] + s.cnt[a] - 1;
+        }
+    }
+}
+
+int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wavelet *w,
+                       const smi_opts *o, Arena &ar, cudaStream_t st, long long *launches, Setup &S)
+{
+    if (!m || !geo || !w || !o) return fail(SMI_ERR_ARG, "null argument");
+    if (m->ndim != 2 && m->ndim != 3) return fail(SMI_ERR_ARG, "ndim must be 2 or 3");
+    if (o->order != 4 && o->order != 8) return fail(SMI_ERR_ARG, "order must be 4 or 8");
+    if (o->freesurf != 0) return fail(SMI_ERR_UNSUPPORTED, "free surface is not built (freesurf must be 0)");
+    if (o->dr != 1) return fail(SMI_ERR_UNSUPPORTED, "boundary decimation dr > 1 is not built (dr must be 1)");
+    if (o->shell_prec < SMI_PREC_F32 || o->shell_prec > SMI_PREC_BF16)
+        return fail(SMI_ERR_ARG, "shell_prec must be SMI_PREC_F32, F16 or BF16");
+    const int N = o->order / 2;
+    if (o->nb < N) return fail(SMI_ERR_ARG, "nb must be >= order/2");
+    if (!m->vp || !m->rho) return fail(SMI_ERR_ARG, "model arrays are null");
+    if (!w->stf) return fail(SMI_ERR_ARG, "wavelet is null");
+    if (w->nt < 1 || !(w->dt > 0.0) || !(w->fm >= 0.0)) return fail(SMI_ERR_ARG, "bad nt, dt or fm");
+    if (geo->nshot < 1 || !geo->src || !geo->rec_offset) return fail(SMI_ERR_ARG, "bad geometry");
+    S.ndim = m->ndim;
+    S.n[0] = m->n1;
+    S.n[1] = m->n2;
+    S.n[2] = m->ndim == 3 ? m->n3 : 1;
+    if (m->ndim == 2 && m->n3 != 1 && m->n3 != 0) return fail(SMI_ERR_ARG, "n3 must be 1 in 2D");
+    const double hh[3] = {m->d1, m->d2, m->ndim == 3 ? m->d3 : 1.0};
+    for (int a = 0; a < m->ndim; a++) {
+        if (S.n[a] < 2 * N) return fail(SMI_ERR_ARG, "axis %d has fewer than order nodes", a);
+        if (!(hh[a] > 0.0)) return fail(SMI_ERR_ARG, "grid spacing must be positive");
+    }
+    S.nshot = geo->nshot;
+    S.nt = w->nt;
+    S.rec_offset.assign(geo->rec_offset, geo->rec_offset + geo->nshot + 1);
+    if (S.rec_offset[0] != 0) return fail(SMI_ERR_ARG, "rec_offset[0] must be 0");
+    for (int s = 0; s < S.nshot; s++)
+        if (S.rec_offset[s + 1] < S.rec_offset[s]) return fail(SMI_ERR_ARG, "rec_offset must be nondecreasing");
+    S.nrec_total = S.rec_offset[S.nshot];
+    if (S.nrec_total > 0 && !geo->rec) return fail(SMI_ERR_ARG, "receiver array is null");
+
+    Grid &g = S.g;
+    g.ndim = m->ndim;
+    g.N = N;
+    g.ri = N;
+    g.nb = o->nb;
+    g.ntot = 1;
+    g.nphys = 1;
+    for (int a = 0; a < 3; a++) {
+        const bool act = a < m->ndim;
+        g.ne[a] = act ? S.n[a] + 2 * o->nb : 1;
+        g.L[a] = act ? o->nb : 0;
+        g.H[a] = act ? o->nb + S.n[a] - 1 : 0;
+        g.h[a] = hh[a];
+        g.ntot *= g.ne[a];
+        g.nphys *= S.n[a];
+    }
+    g.S = 2 * o->nb + 1;
+    for (int a = 0; a < 3; a++) g.slab_n[a] = a < m->ndim ? g.ntot / g.ne[a] * g.S : 0;
+    g.dt = (float)w->dt;
+    g.use_box = o->use_box ? 1 : 0;
+    double coef[kMaxHalf] = {0};
+    fd_coefficients(N, coef);
+    for (int a = 0; a < 3; a++)
+        for (int l = 0; l < kMaxHalf; l++) g.c[a][l] = (a < m->ndim && l < N) ? (float)(coef[l] / hh[a]) : 0.0f;
+
+    // inputs on the device
+    const size_t nphys = (size_t)g.nphys;
+    int rc = classify_and_upload(ar, m->vp, nphys, &S.vp, st);
+    if (!rc) rc = classify_and_upload(ar, m->rho, nphys, &S.rho, st);
+    if (!rc) rc = classify_and_upload(ar, w->stf, (size_t)w->nt, &S.stf, st);
+    if (rc) return rc;
+
+    // vmin / vmax (and rho positivity) on the device
+    float *mm = ar.get<float>(4);
+    unsigned *tmp = ar.get<unsigned>(4);
+    if (!mm || !tmp) return fail(SMI_ERR_NOMEM, "device allocation failed");
+    LaunchCtx lc{st, launches};
+    launch_minmax(lc, S.vp, g.nphys, mm, tmp);
+    launch_minmax(lc, S.rho, g.nphys, mm + 2, tmp + 2);
+    float hm[4];
+    if (cudaMemcpyAsync(hm, mm, sizeof hm, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(SMI_ERR_CUDA, "model reduction failed: %s", cudaGetErrorString(cudaGetLastError()));
+    if (!(hm[0] > 0.0f) || !(hm[2] > 0.0f) || !std::isfinite(hm[1]) || !std::isfinite(hm[3]))
+        return fail(SMI_ERR_ARG, "vp and rho must be positive and finite");
+    S.vmin = hm[0];
+    S.vmax = hm[1];
+    g.vdt = (double)S.vmax * w->dt;
+    const double cfl = cfl_number(m->ndim, hh, w->dt, S.vmax, N);
+    if (cfl > 1.0) return fail(SMI_ERR_CFL, "CFL number %.4f exceeds 1 (Eq. cfl)", cfl);
+    if (w->fm > 0.0) {
+        const double ppw = points_per_wavelength(m->ndim, hh, S.vmin, w->fm);
+        const double need = N >= 4 ? 4.0 : 5.0;
+        if (ppw < need)
+            return fail(SMI_ERR_DISPERSION, "%.2f points per shortest wavelength, order %d needs %.0f",
+                        ppw, o->order, need);
+    }
+
+    // CPML tables
+    const double R = o->cpml_R > 0.0 ? o->cpml_R : 1e-3;
+    const double kb = o->kaiser_b > 0.0 ? o->kaiser_b : 4.0;
+    for (int a = 0; a < m->ndim; a++) {
+        std::vector<float> tab(4 * (size_t)g.ne[a]);
+        cpml_tables(g.ne[a], o->nb, hh[a], S.vmax, w->fm, R, w->dt, false, tab.data(), tab.data() + g.ne[a]);
+        cpml_tables(g.ne[a], o->nb, hh[a], S.vmax, w->fm, R, w->dt, true, tab.data() + 2 * g.ne[a],
+                    tab.data() + 3 * g.ne[a]);
+        float *d = ar.get<float>(tab.size());
+        if (!d) return fail(SMI_ERR_NOMEM, "device allocation failed");
+        cudaMemcpyAsync(d, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+        g.cpa[a] = d;
+        g.cpb[a] = d + g.ne[a];
+        g.cva[a] = d + 2 * g.ne[a];
+        g.cvb[a] = d + 3 * g.ne[a];
+    }
+    for (int a = m->ndim; a < 3; a++) g.cpa[a] = g.cpb[a] = g.cva[a] = g.cvb[a] = nullptr;
+
+    // extended model
+    float *K = ar.get<float>((size_t)g.ntot), *rho_e = ar.get<float>((size_t)g.ntot);
+    if (!K || !rho_e) return fail(SMI_ERR_NOMEM, "device allocation of the extended model failed");
+    g.K = K;
+    g.rho = rho_e;
+    launch_extend_model(lc, g, S.vp, S.rho, S.n[0], S.n[1], S.n[2], K, rho_e);
+
+    // stencils and box extents
+    S.src_st.resize(S.nshot);
+    S.rec_st.resize((size_t)S.nrec_total);
+    S.box_src.resize(6 * (size_t)S.nshot);
+    S.box_rec.resize(6 * (size_t)S.nshot);
+    for (int s = 0; s < S.nshot; s++) {
+        if (!make_stencil(g, geo->src + 3 * s, kb, &S.src_st[s]))
+            return fail(SMI_ERR_ARG, "source %d lies outside the model or its stencil leaves the grid", s);
+        int lo[3], hi[3];
+        stencil_extent(g, S.src_st[s], lo, hi);
+        for (int a = 0; a < 3; a++) {
+            S.box_src[6 * s + a] = lo[a];
+            S.box_src[6 * s + 3 + a] = hi[a];
+        }
+        int rlo[3] = {1 << 30, 1 << 30, 1 << 30}, rhi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+        for (int r = S.rec_offset[s]; r < S.rec_offset[s + 1]; r++) {
+            if (!make_stencil(g, geo->rec + 3 * (size_t)r, kb, &S.rec_st[r]))
+                return fail(SMI_ERR_ARG, "receiver %d lies outside the model or its stencil leaves the grid", r);
+            stencil_extent(g, S.rec_st[r], lo, hi);
+            for (int a = 0; a < 3; a++) {
+                rlo[a] = std::min(rlo[a], lo[a]);
+                rhi[a] = std::max(rhi[a], hi[a]);
+            }
+        }
+        if (S.rec_offset[s + 1] == S.rec_offset[s])   // no receivers: empty adjoint box seed
+            for (int a = 0; a < 3; a++) { rlo[a] = lo[a]; rhi[a] = hi[a]; }
+        for (int a = 0; a < 3; a++) {
+            S.box_rec[6 * s + a] = rlo[a];
+            S.box_rec[6 * s + 3 + a] = rhi[a];
+        }
+    }
+    S.d_src = ar.get<Stencil>(S.nshot);
+    S.d_rec = ar.get<Stencil>(std::max<size_t>(1, (size_t)S.nrec_total));
+    S.d_box_src = ar.get<int>(6 * (size_t)S.nshot);
+    S.d_box_rec = ar.get<int>(6 * (size_t)S.nshot);
+    if (!ar.ok) return fail(SMI_ERR_NOMEM, "device allocation failed");
+    cudaMemcpyAsync(S.d_src, S.src_st.data(), sizeof(Stencil) * S.nshot, cudaMemcpyHostToDevice, st);
+    if (S.nrec_total)
+        cudaMemcpyAsync(S.d_rec, S.rec_st.data(), sizeof(Stencil) * S.nrec_total, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(S.d_box_src, S.box_src.data(), sizeof(int) * 6 * S.nshot, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(S.d_box_rec, S.box_rec.data(), sizeof(int) * 6 * S.nshot, cudaMemcpyHostToDevice, st);
+    double dV = 1.0;
+    for (int a = 0; a < m->ndim; a++) dV *= hh[a];
+    S.src_scale = w->dt / dV;
+
+    // boundary bands: v_a on the 2N-1 half nodes straddling each face of the
+    // physical domain, over the physical cross-section (Sec. 4.2, dr = 1)
+    Bands &bd = S.bands;
+    bd.count = 0;
+    bd.prec = o->shell_prec;
+    bd.nt = S.nt;
+    for (int a = 0; a < 3; a++)
+        for (int sd = 0; sd < 2; sd++) {
+            bd.off[a][sd] = bd.count;
+            for (int b = 0; b < 3; b++) {
+                bd.lo[a][sd][b] = g.L[b];
+                bd.hi[a][sd][b] = g.H[b];
+            }
+            if (a >= m->ndim) {
+                bd.hi[a][sd][0] = bd.lo[a][sd][0] - 1;   // empty
+                continue;
+            }
+            if (sd == 0) {
+                bd.lo[a][sd][a] = g.L[a] - N;
+                bd.hi[a][sd][a] = g.L[a] + N - 2;
+            } else {
+                bd.lo[a][sd][a] = g.H[a] - N + 1;
+                bd.hi[a][sd][a] = g.H[a] + N - 1;
+            }
+            long long c = 1;
+            for (int b = 0; b < 3; b++) c *= bd.hi[a][sd][b] - bd.lo[a][sd][b] + 1;
+            bd.count += c;
+        }
+    return SMI_OK;
+}
+
+size_t band_bytes(int prec) { return prec == SMI_PREC_F32 ? 4 : 2; }
+
+// Device bytes of one shot in a batch.
+size_t per_shot_bytes(const Setup &S, int kind)
+{
+    const Grid &g = S.g;
+    size_t fields = (size_t)(1 + g.ndim) * g.ntot * 4;
+    size_t slabs = 0;
+    for (int a = 0; a < g.ndim; a++) slabs += 2 * (size_t)g.slab_n[a] * 4;
+    const long long maxrec = S.nrec_total;     // upper bound of one shot's receivers
+    size_t b = fields + slabs + (size_t)S.nt * maxrec * 4;
+    if (kind != 0) {
+        b += fields;                                                   // adjoint fields
+        b += (size_t)S.nt * S.bands.count * band_bytes(S.bands.prec);   // saved bands
+        b += (size_t)S.nt * 6 * 4;                                     // band scales
+        b += (size_t)g.nphys * 4;                                      // accumulator
+        b += (size_t)S.nt * maxrec * 4 * 2;                            // seis + residual
+    }
+    return b;
+}
+
+struct Timer {
+    bool on = false;
+    cudaStream_t st{};
+    std::vector<cudaEvent_t> ev;   // pairs
+    std::vector<int> cls;
+    size_t used = 0;
+    void begin(int c)
+    {
+        if (!on) return;
+        if (used + 2 > ev.size()) {
+            for (int k = 0; k < 2; k++) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                ev.push_back(e);
+            }
+        }
+        cudaEventRecord(ev[used], st);
+        cls.push_back(c);
+    }
+    void end()
+    {
+        if (!on) return;
+        cudaEventRecord(ev[used + 1], st);
+        used += 2;
+    }
+    void collect(smi_stats &s)
+    {
+        for (size_t i = 0; i + 1 < used; i += 2) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            s.ms[cls[i / 2]] += ms;
+        }
+    }
+    ~Timer()
+    {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+// Algorithmic bytes and point updates of one stencil step of one shot.
+void account(const Grid &g, const int lo[3], const int hi[3], int cls, smi_stats &s)
+{
+    long long w[3];
+    for (int a = 0; a < 3; a++) w[a] = std::max(0, hi[a] - lo[a] + 1);
+    const double vol = (double)w[0] * w[1] * w[2];
+    if (vol <= 0) return;
+    double bytes;
+    if (cls == 2) {
+        bytes = vol * (g.ndim == 3 ? 52.0 : 44.0);
+    } else {
+        bytes = vol * (g.ndim == 3 ? 40.0 : 32.0);
+        for (int a = 0; a < g.ndim; a++) {
+            // slab nodes of axis a inside the box: two memory variables r/w
+            long long in = 0;
+            for (int j = lo[a]; j <= hi[a]; j++) in += (j < g.nb || j >= g.ne[a] - g.nb - 1);
+            bytes += 16.0 * (double)in * vol / (double)w[a];
+        }
+    }
+    s.bytes[cls] += bytes;
+    s.point_updates += vol;
+    s.steps[cls] += 1;
+}
+
+int finish_stream(cudaStream_t st)
+{
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(SMI_ERR_CUDA, "CUDA error: %s", cudaGetErrorString(e));
+    return SMI_OK;
+}
+
+// kind: 0 forward, 1 rtm, 2 gradient
+int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet *w, const smi_opts *o,
+        const float *dobs, float *seis_out, float *img_out, double *misfit_out)
+{
+    t_err.clear();
+    memset(&t_stats, 0, sizeof t_stats);
+    if (!o) return fail(SMI_ERR_ARG, "null options");
+    cudaStream_t st = static_cast<cudaStream_t>(o->stream);
+    long long launches = 0;
+    Setup S;
+    int rc;
+    {
+        Arena ar(st);
+        rc = validate_and_setup(m, geo, w, o, ar, st, &launches, S);
+        if (rc) {
+            cudaStreamSynchronize(st);
+            return rc;
+        }
+        const Grid &g = S.g;
+        LaunchCtx lc{st, &launches};
+        const size_t nseis = (size_t)S.nt * S.nrec_total;
+        if (kind == 0 && !seis_out) return fail(SMI_ERR_ARG, "seis is null");
+        if (kind != 0 && !dobs) return fail(SMI_ERR_ARG, "dobs is null");
+
+        // outputs and observed data on the device
+        float *d_seis_out = nullptr, *d_img = nullptr;
+        const float *d_dobs = nullptr;
+        double *d_misfit = ar.get<double>(1);
+        if (!d_misfit) return fail(SMI_ERR_NOMEM, "device allocation failed");
+        launch_zero(lc, d_misfit, sizeof(double));
+        if (kind == 0) {
+            d_seis_out = is_device_ptr(seis_out) ? seis_out : ar.get<float>(nseis);
+        } else {
+            rc = classify_and_upload(ar, dobs, nseis, &d_dobs, st);
+            if (rc) return rc;
+            if (img_out) d_img = is_device_ptr(img_out) ? img_out : ar.get<float>((size_t)g.nphys);
+            else d_img = ar.get<float>((size_t)g.nphys);
+        }
+        if (!ar.ok) return fail(SMI_ERR_NOMEM, "device allocation of outputs failed");
+
+        // batch size by device memory
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        const size_t per = std::max<size_t>(per_shot_bytes(S, kind), 1);
+        int B = (int)std::max<size_t>(1, (size_t)(0.8 * (double)free_b) / per);
+        B = std::min(B, S.nshot);
+        if (o->max_batch > 0) B = std::min(B, o->max_batch);
+
+        Timer tm;
+        tm.on = o->profile != 0;
+        tm.st = st;
+        unsigned *d_flag = ar.get<unsigned>(1);
+        unsigned *d_absmax = ar.get<unsigned>(6 * (size_t)B);
+        if (!ar.ok) return fail(SMI_ERR_NOMEM, "device allocation failed");
+        launch_zero(lc, d_flag, sizeof(unsigned));
+
+        for (int s0 = 0; s0 < S.nshot; s0 += B) {
+            const int nb_shot = std::min(B, S.nshot - s0);
+            // per-batch tables
+            std::vector<int> roff(nb_shot + 1);
+            std::vector<long long> soff(nb_shot);
+            int max_rec = 0;
+            for (int s = 0; s <= nb_shot; s++) roff[s] = S.rec_offset[s0 + s] - S.rec_offset[s0];
+            for (int s = 0; s < nb_shot; s++) {
+                soff[s] = (long long)S.nt * roff[s];
+                max_rec = std::max(max_rec, roff[s + 1] - roff[s]);
+            }
+            const long long batch_seis = (long long)S.nt * roff[nb_shot];
+            Arena ba(st);
+            int *d_roff = ba.get<int>(roff.size());
+            long long *d_soff = ba.get<long long>(soff.size());
+            Fields F{}, A{};
+            F.p = ba.get<float>((size_t)g.ntot * nb_shot);
+            for (int a = 0; a < g.ndim; a++) {
+                F.v[a] = ba.get<float>((size_t)g.ntot * nb_shot);
+                F.psip[a] = ba.get<float>((size_t)g.slab_n[a] * nb_shot);
+                F.psiv[a] = ba.get<float>((size_t)g.slab_n[a] * nb_shot);
+            }
+            float *seis = (kind == 0) ? d_seis_out + (size_t)S.nt * S.rec_offset[s0]
+                                      : ba.get<float>(std::max<long long>(1, batch_seis));
+            Bands bd = S.bands;
+            float *res = nullptr, *acc = nullptr;
+            double *partials = nullptr;
+            const int npart = 256;
+            if (kind != 0) {
+                A.p = ba.get<float>((size_t)g.ntot * nb_shot);
+                for (int a = 0; a < g.ndim; a++) {
+                    A.v[a] = ba.get<float>((size_t)g.ntot * nb_shot);
+                    A.psip[a] = F.psip[a];
+                    A.psiv[a] = F.psiv[a];
+                }
+                bd.data = ba.raw((size_t)nb_shot * S.nt * bd.count * band_bytes(bd.prec));
+                bd.scale = ba.get<float>((size_t)nb_shot * S.nt * 6);
+                res = ba.get<float>(std::max<long long>(1, batch_seis));
+                acc = ba.get<float>((size_t)g.nphys * nb_shot);
+                partials = ba.get<double>(npart);
+            }
+            if (!ba.ok) return fail(SMI_ERR_NOMEM, "device allocation for a batch of %d shots failed", nb_shot);
+            cudaMemcpyAsync(d_roff, roff.data(), sizeof(int) * roff.size(), cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(d_soff, soff.data(), sizeof(long long) * soff.size(), cudaMemcpyHostToDevice, st);
+            Batch b{};
+            b.nshot = nb_shot;
+            b.box_src = S.d_box_src + 6 * s0;
+            b.box_rec = S.d_box_rec + 6 * s0;
+            b.src = S.d_src + s0;
+            b.rec = S.d_rec + S.rec_offset[s0];
+            b.rec_off = d_roff;
+            b.max_rec = max_rec;
+            launch_zero(lc, F.p, sizeof(float) * g.ntot * nb_shot);
+            for (int a = 0; a < g.ndim; a++) {
+                launch_zero(lc, F.v[a], sizeof(float) * g.ntot * nb_shot);
+                launch_zero(lc, F.psip[a], sizeof(float) * g.slab_n[a] * nb_shot);
+                launch_zero(lc, F.psiv[a], sizeof(float) * g.slab_n[a] * nb_shot);
+            }
+
+            // ---- forward loop (Algorithm 2) ----
+            for (int it = 0; it < S.nt; it++) {
+                if (kind != 0) launch_save_bands(lc, g, b, F, bd, it, d_absmax);
+                tm.begin(0);
+                launch_fwd_v(lc, g, b, F, it);
+                launch_fwd_p(lc, g, b, F, it);
+                tm.end();
+                launch_inject_source(lc, g, b, F.p, S.stf, it, (float)S.src_scale);
+                if (max_rec > 0) launch_gather(lc, g, b, F.p, seis, d_soff, S.nt, it);
+                for (int s = 0; s < nb_shot; s++) {
+                    int lo[3], hi[3];
+                    box_bounds(g, S.box_src.data() + 6 * (s0 + s), it, lo, hi);
+                    account(g, lo, hi, 0, t_stats);
+                }
+            }
+            if (batch_seis > 0) launch_nonfinite(lc, seis, batch_seis, d_flag);
+            launch_nonfinite(lc, F.p, g.ntot * nb_shot, d_flag);
+            if (kind == 0) continue;
+
+            // ---- residual, misfit ----
+            if (batch_seis > 0) {
+                const float *dob = d_dobs + (size_t)S.nt * S.rec_offset[s0];
+                launch_residual(lc, seis, dob, batch_seis, kind == 2 ? 0 : 1, res, partials, npart);
+                if (kind == 2) launch_sum_partials(lc, partials, npart, d_misfit);
+            }
+            // ---- reverse loop ----
+            launch_zero(lc, A.p, sizeof(float) * g.ntot * nb_shot);
+            for (int a = 0; a < g.ndim; a++) {
+                launch_zero(lc, A.v[a], sizeof(float) * g.ntot * nb_shot);
+                launch_zero(lc, A.psip[a], sizeof(float) * g.slab_n[a] * nb_shot);
+                launch_zero(lc, A.psiv[a], sizeof(float) * g.slab_n[a] * nb_shot);
+            }
+            launch_zero(lc, acc, sizeof(float) * g.nphys * nb_shot);
+            const int mode = kind == 2 ? 0 : 1;
+            for (int it = S.nt - 1; it >= 0; it--) {
+                const int mrev = S.nt - 1 - it;
+                if (max_rec > 0) launch_adj_inject(lc, g, b, A.p, res, d_soff, S.nt, it);
+                tm.begin(2);
+                launch_recon_p(lc, g, b, F, A.p, acc, mode, S.stf, it, (float)S.src_scale);
+                launch_recon_v(lc, g, b, F, it);
+                tm.end();
+                launch_restore_bands(lc, g, b, F, bd, it);
+                tm.begin(1);
+                launch_adj_v(lc, g, b, A, mrev);
+                launch_adj_p(lc, g, b, A, mrev);
+                tm.end();
+                for (int s = 0; s < nb_shot; s++) {
+                    int lo[3], hi[3];
+                    box_bounds(g, S.box_rec.data() + 6 * (s0 + s), mrev, lo, hi);
+                    account(g, lo, hi, 1, t_stats);
+                    box_bounds(g, S.box_src.data() + 6 * (s0 + s), it, lo, hi);
+                    for (int a = 0; a < 3; a++) {
+                        lo[a] = std::max(lo[a], g.L[a]);
+                        hi[a] = std::min(hi[a], g.H[a]);
+                    }
+                    account(g, lo, hi, 2, t_stats);
+                }
+            }
+            launch_nonfinite(lc, acc, g.nphys * nb_shot, d_flag);
+            launch_reduce_shots(lc, g, acc, nb_shot, d_img, s0 > 0);
+            // batch buffers are released (stream-ordered) when `ba` goes out of scope
+        }
+        if (kind == 2) launch_finalize_grad(lc, g.nphys, S.vp, g.dt, d_img);
+
+        // outputs back to the host where needed
+        if (kind == 0 && d_seis_out != seis_out)
+            cudaMemcpyAsync(seis_out, d_seis_out, nseis * sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (kind != 0 && img_out && d_img != img_out)
+            cudaMemcpyAsync(img_out, d_img, (size_t)g.nphys * sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (kind == 2 && misfit_out) {
+            cudaMemcpyAsync(misfit_out, d_misfit, sizeof(double),
+                            is_device_ptr(misfit_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+        }
+        unsigned flag = 0;
+        cudaMemcpyAsync(&flag, d_flag, sizeof flag, cudaMemcpyDeviceToHost, st);
+        rc = finish_stream(st);
+        if (!rc && flag) rc = fail(SMI_ERR_UNSTABLE, "non-finite values in the wavefield or outputs");
+        tm.collect(t_stats);
+        t_stats.kernel_launches = launches;
+        t_stats.device_bytes = (double)ar.peak;
+        t_stats.band_values = kind == 0 ? 0 : S.bands.count;
+    }
+    // the arena's frees are stream ordered; make them complete before return
+    if (!rc) rc = finish_stream(st);
+    return rc;
+}
+
+}  // namespace
+}  // namespace smi
+
+using namespace smi;
+
+extern "C" {
+
+void smi_opts_default(smi_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->order = 4;
+    o->nb = 20;
+    o->freesurf = 0;
+    o->dr = 1;
+    o->use_box = 1;
+    o->shell_prec = SMI_PREC_F32;
+    o->kaiser_b = 4.0;
+    o->cpml_R = 1e-3;
+    o->stream = nullptr;
+    o->max_batch = 0;
+    o->profile = 0;
+}
+
+int smi_forward(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                const smi_opts *opts, float *seis)
+{
+    return run(0, model, geom, wav, opts, nullptr, seis, nullptr, nullptr);
+}
+
+int smi_rtm(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+            const smi_opts *opts, const float *dobs, float *image)
+{
+    if (!image) return fail(SMI_ERR_ARG, "image is null");
+    return run(1, model, geom, wav, opts, dobs, nullptr, image, nullptr);
+}
+
+int smi_fwi_gradient(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                     const smi_opts *opts, const float *dobs, double *misfit, float *grad_vp)
+{
+    return run(2, model, geom, wav, opts, dobs, nullptr, grad_vp, misfit);
+}
+
+int smi_query(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+              const smi_opts *opts, int kind, size_t *seis_elems, size_t *image_elems,
+              size_t *device_bytes)
+{
+    t_err.clear();
+    if (!opts) return fail(SMI_ERR_ARG, "null options");
+    if (kind < 0 || kind > 2) return fail(SMI_ERR_ARG, "kind must be 0, 1 or 2");
+    cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
+    long long launches = 0;
+    Setup S;
+    int rc;
+    {
+        Arena ar(st);
+        rc = validate_and_setup(model, geom, wav, opts, ar, st, &launches, S);
+        if (!rc) {
+            if (seis_elems) *seis_elems = (size_t)S.nt * S.nrec_total;
+            if (image_elems) *image_elems = (size_t)S.g.nphys;
+            if (device_bytes) {
+                int B = S.nshot;
+                if (opts->max_batch > 0) B = std::min(B, opts->max_batch);
+                *device_bytes = ar.peak + (size_t)B * per_shot_bytes(S, kind);
+            }
+        }
+    }
+    int rc2 = finish_stream(st);
+    return rc ? rc : rc2;
+}
+
+int smi_box_table(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                  const smi_opts *opts, int shot, int which, int n0, int count, int *lo, int *hi)
+{
+    t_err.clear();
+    if (!opts || !lo || !hi || count < 0) return fail(SMI_ERR_ARG, "bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
+    long long launches = 0;
+    Setup S;
+    int rc;
+    {
+        Arena ar(st);
+        rc = validate_and_setup(model, geom, wav, opts, ar, st, &launches, S);
+        if (!rc && (shot < 0 || shot >= S.nshot || (which != 0 && which != 1)))
+            rc = fail(SMI_ERR_ARG, "bad shot or which");
+        if (!rc && count > 0) {
+            int *d = ar.get<int>(6 * (size_t)count);
+            if (!d) {
+                rc = fail(SMI_ERR_NOMEM, "device allocation failed");
+            } else {
+                LaunchCtx lc{st, &launches};
+                const int *ext = (which == 0 ? S.d_box_src : S.d_box_rec) + 6 * shot;
+                launch_box_table(lc, S.g, ext, n0, count, d, d + 3 * (size_t)count);
+                cudaMemcpyAsync(lo, d, sizeof(int) * 3 * count, cudaMemcpyDeviceToHost, st);
+                cudaMemcpyAsync(hi, d + 3 * (size_t)count, sizeof(int) * 3 * count, cudaMemcpyDeviceToHost, st);
+                rc = finish_stream(st);
+            }
+        }
+    }
+    int rc2 = finish_stream(st);
+    return rc ? rc : rc2;
+}
+
+int smi_last_stats(smi_stats *st)
+{
+    if (!st) return fail(SMI_ERR_ARG, "null stats");
+    *st = t_stats;
+    return SMI_OK;
+}
+
+const char *smi_last_error(void) { return t_err.c_str(); }
+
+const char *smi_version(void) { return "smi 0.1 sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,64 @@
+// smi_box.h -- the dynamic computing box (Sec. 4.1), evaluated identically
+// by the kernels and by the host's byte accounting.
+#pragma once
+
+#include <cmath>
+
+#include "smi_internal.h"
+
+namespace smi {
+
+#ifdef __CUDACC__
+#define SMI_HD __host__ __device__ __forceinline__
+#else
+#define SMI_HD inline
+#endif
+
+SMI_HD double box_mul(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+
+SMI_HD double box_div(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __ddiv_rn(a, b);
+#else
+    return a / b;
+#endif
+}
+
+// Box after n elapsed steps around the stencil extent ext = {lo0, lo1, lo2,
+// hi0, hi1, hi2}: the wavefront has travelled at most vmax (n+1) dt, so each
+// face moves out by r_n = ceil(vmax dt (n+1) / h) + 2N + ri cells (2N for the
+// two half-step stencils, ri for the injection width), clipped to the
+// extended grid.  FP64 with round-to-nearest products in a fixed order, so
+// host and device agree bit for bit.  n < 0: empty box (hi < lo).
+SMI_HD void box_bounds(const Grid &g, const int *ext, int n, int lo[3], int hi[3])
+{
+    for (int a = 0; a < 3; a++) {
+        if (n < 0) {
+            lo[a] = 0;
+            hi[a] = -1;
+        } else if (a >= g.ndim) {
+            lo[a] = 0;
+            hi[a] = 0;
+        } else if (!g.use_box) {
+            lo[a] = 0;
+            hi[a] = g.ne[a] - 1;
+        } else {
+            double r = box_mul(g.vdt, (double)(n + 1));
+            r = box_div(r, g.h[a]);
+            const int rn = (int)ceil(r) + 2 * g.N + g.ri;
+            const int l = ext[a] - rn, h = ext[3 + a] + rn;
+            lo[a] = l < 0 ? 0 : l;
+            hi[a] = h > g.ne[a] - 1 ? g.ne[a] - 1 : h;
+        }
+    }
+}
+
+}  // namespace smi

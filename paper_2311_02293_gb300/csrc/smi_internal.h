@@ -1,0 +1,139 @@
+// smi_internal.h -- data shared by the host driver (smi_api.cu, smi_setup.cpp)
+// and the CUDA kernels (smi_kernels.cu) of libsmi.  Not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/smi.h"
+
+namespace smi {
+
+constexpr int kMaxHalf = 4;        // N = order/2 <= 4
+constexpr int kMaxTaps = 8;        // 2 * ri, ri = order/2 <= 4
+
+// Grid, scheme constants and read-only model arrays, passed by value to
+// every kernel.  Axis 0 = z (fastest), 1 = x, 2 = y.
+struct Grid {
+    int ndim, N, ri, nb;
+    int ne[3];             // extended sizes (1 for an inactive axis)
+    int L[3], H[3];        // first/last physical node along each axis (extended index)
+    long long ntot;        // points of one extended field
+    long long nphys;       // points of the physical grid
+    int S;                 // slab length along its axis: 2*nb + 1
+    long long slab_n[3];   // points of the slab array of axis a
+    float dt;
+    float c[3][kMaxHalf];  // a_l / h_a
+    double vdt;            // vmax * dt (FP64, for the computing box)
+    double h[3];           // spacings (FP64, for the computing box)
+    int use_box;
+    const float *K;        // bulk modulus rho*vp^2 on the extended grid
+    const float *rho;      // density on the extended grid
+    const float *cpa[3], *cpb[3];   // CPML a, b on the p grid of axis a (length ne[a])
+    const float *cva[3], *cvb[3];   // CPML a, b on the v grid of axis a
+};
+
+// Interpolation stencil of one point: per axis a first node, a node count
+// (1 on a node, 2*ri otherwise) and the 1D weights.
+struct Stencil {
+    int first[3];
+    int cnt[3];
+    float w[3][kMaxTaps];
+};
+
+// Shots propagated together in one launch (blockIdx.y / grid.z = shot).
+struct Batch {
+    int nshot;
+    const int *box_src;     // [nshot][6] source stencil extent lo0,lo1,lo2,hi0,hi1,hi2
+    const int *box_rec;     // [nshot][6] receiver stencil extent
+    const Stencil *src;     // [nshot]
+    const Stencil *rec;     // [nrec_total of the batch]
+    const int *rec_off;     // [nshot+1] batch-local receiver offsets
+    int max_rec;            // largest receiver count of a shot in the batch
+};
+
+// Wavefields of a batch; shot s of field f is at f + s * ntot.
+struct Fields {
+    float *p;
+    float *v[3];
+    float *psip[3];        // slab memory variables on the v grid of axis a (stride slab_n[a])
+    float *psiv[3];        // slab memory variables on the p grid of axis a
+};
+
+// Boundary bands (saved source-field velocities, Sec. 4.2).
+struct Bands {
+    long long count;             // values per shot per step
+    long long off[3][2];         // start of (axis, side) within one step
+    int lo[3][2][3], hi[3][2][3];  // region of (axis, side): inclusive bounds per axis
+    int prec;                    // SMI_PREC_*
+    void *data;                  // [nshot][nt][count] of float / half / bf16
+    float *scale;                // [nshot][nt][3][2] (16-bit storage only)
+    int nt;
+};
+
+// ---------------------------------------------------------------------------
+// Host set-up (smi_setup.cpp): exact FP64 arithmetic, rounded to FP32 tables.
+
+// Staggered FD coefficients a_1..a_N (Sec. 2.1) from the closed-form product
+// a_m = (-1)^{m+1}/(2m-1) prod_{n != m} (2n-1)^2 / |(2m-1)^2 - (2n-1)^2|.
+void fd_coefficients(int N, double *a);
+
+// CFL number of Eq. cfl; the call fails if it exceeds 1.
+double cfl_number(int ndim, const double *h, double dt, double vmax, int N);
+
+// Points per shortest wavelength vmin / (2.5 fm) / max(h).
+double points_per_wavelength(int ndim, const double *h, double vmin, double fm);
+
+// CPML a/b tables along one axis (length ne) on the p grid or the v grid.
+void cpml_tables(int ne, int nb, double h, double vmax, double fm, double R, double dt,
+                 bool vgrid, float *a, float *b);
+
+// Kaiser-windowed sinc stencil of a position (metres) on the extended grid;
+// false if it leaves the physical domain or its stencil leaves the grid.
+bool make_stencil(const Grid &g, const double pos[3], double kaiser_b, Stencil *st);
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (smi_kernels.cu).  All run on `stream`.
+
+struct LaunchCtx {
+    void *stream;           // cudaStream_t
+    long long *launches;    // incremented per kernel launch
+};
+
+void launch_extend_model(const LaunchCtx &lc, const Grid &g, const float *vp, const float *rho,
+                         int n1, int n2, int n3, float *K, float *rho_e);
+void launch_minmax(const LaunchCtx &lc, const float *vp, long long n, float *out2, unsigned *tmp);
+void launch_zero(const LaunchCtx &lc, void *ptr, size_t bytes);
+
+void launch_fwd_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it);
+void launch_fwd_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it);
+void launch_inject_source(const LaunchCtx &lc, const Grid &g, const Batch &b, float *p,
+                          const float *stf, int it, float scale);
+void launch_gather(const LaunchCtx &lc, const Grid &g, const Batch &b, const float *p,
+                   float *seis, const long long *seis_off, int nt, int it);
+void launch_save_bands(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f,
+                       Bands bd, int it, unsigned *absmax_tmp);
+void launch_restore_bands(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f,
+                          Bands bd, int it);
+void launch_residual(const LaunchCtx &lc, const float *seis, const float *dobs, long long n,
+                     int mode, float *res, double *partials, int npart);
+void launch_sum_partials(const LaunchCtx &lc, const double *partials, int npart, double *out);
+void launch_adj_inject(const LaunchCtx &lc, const Grid &g, const Batch &b, float *lp,
+                       const float *res, const long long *seis_off, int nt, int it);
+void launch_adj_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m);
+void launch_adj_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m);
+void launch_recon_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f,
+                    const float *lp, float *acc, int mode, const float *stf, int it,
+                    float src_scale);
+void launch_recon_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it);
+void launch_reduce_shots(const LaunchCtx &lc, const Grid &g, const float *acc, int nshot,
+                         float *out, int accumulate);
+void launch_finalize_grad(const LaunchCtx &lc, long long n, const float *vp, float dt,
+                          float *g);
+void launch_nonfinite(const LaunchCtx &lc, const float *x, long long n, unsigned *flag);
+void launch_box_table(const LaunchCtx &lc, const Grid &g, const int *ext, int n0, int count,
+                      int *lo, int *hi);
+
+}  // namespace smi

@@ -1,0 +1,228 @@
+"""GPU (libsmi, FP32) against the FP64 CPU oracle, through the C ABI.
+
+Bars: computing-box bounds bit-exact; seismograms within 1e-4 relative L2;
+RTM images and FWI gradients within 1e-3 relative L2 with FP32 saved
+boundaries; misfits within 1e-5 relative.  16-bit boundary storage reports
+its own measured error.  Cases span several thread blocks, ragged box
+edges, off-node sources and receivers (Kaiser-sinc stencils), orders 4
+and 8, 2D and 3D, with the computing box on and off.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2311_02293_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+SEIS_TOL = 1e-4
+IMG_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def smi():
+    import torch
+    from paper_2311_02293_gb300 import build
+    build.build()
+    from paper_2311_02293_gb300 import smi as mod
+    torch.cuda.init()
+    return mod
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _gprob(smi, w, **kw):
+    args = dict(order=w.order, nb=w.nb)
+    args.update(kw)
+    return smi.Problem(w.d, w.nt, w.dt, w.fm, **args)
+
+
+def _oprob(w, **kw):
+    args = dict(order=w.order, nb=w.nb, fm=w.fm)
+    args.update(kw)
+    return O.Problem(w.n, w.d, w.nt, w.dt, **args)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+SMALL = {
+    "2d_o4_off": lambda: S.tiny_2d(nz=50, nx=44, nt=150, nb=8, src=(9, 21), off_grid=True),
+    "2d_o8_on": lambda: S.tiny_2d(nz=45, nx=61, nt=160, nb=10, order=8, src=(12, 30)),
+    "3d_o4_off": lambda: S.tiny_3d(nz=30, nx=26, ny=22, nt=70, nb=6, off_grid=True),
+    "3d_o8_on": lambda: S.tiny_3d(nz=28, nx=24, ny=26, nt=60, nb=8, order=8),
+}
+
+
+@pytest.mark.parametrize("case", sorted(SMALL))
+@pytest.mark.parametrize("use_box", [True, False])
+def test_forward_parity(smi, case, use_box):
+    w = SMALL[case]()
+    seis = smi.smi_forward(_dev(w.vp), _dev(w.rho), _gprob(smi, w, use_box=use_box), w.srcs,
+                           w.recs, _dev(w.stf))[0].cpu().numpy()
+    ref = O.forward(_oprob(w, use_box=use_box), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0])
+    assert _rel(seis, ref) <= SEIS_TOL
+
+
+def test_forward_parity_two_layer_2d_full_size(smi):
+    """201 x 201, order 4, nt = 1000, 201 surface receivers (the 2D forward
+    workload), all samples compared."""
+    w = S.two_layer_2d()
+    seis = smi.smi_forward(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs,
+                           _dev(w.stf))[0].cpu().numpy()
+    ref = O.forward(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0])
+    assert _rel(seis, ref) <= SEIS_TOL
+
+
+@pytest.mark.parametrize("which", ["source", "receivers"])
+@pytest.mark.parametrize("case", ["2d_o4_off", "3d_o8_on"])
+def test_box_bounds_bit_exact(smi, case, which):
+    w = SMALL[case]()
+    prob = _gprob(smi, w)
+    n0, count = -1, w.nt + 5
+    lo, hi = smi.smi_box_table(_dev(w.vp), _dev(w.rho), prob, w.srcs, w.recs, _dev(w.stf), 0,
+                               which, n0, count)
+    pts = w.srcs[0] if which == "source" else w.recs[0]
+    rlo, rhi = O.box_table(_oprob(w), w.vp, w.rho, pts, n0, count)
+    # the oracle marks an empty box by hi < lo on every axis, like the library
+    assert np.array_equal(lo, rlo) and np.array_equal(hi, rhi)
+
+
+def test_box_bounds_bit_exact_3d_corner_source_full_grid(smi):
+    """The 400 x 400 x 200 random-medium geometry (corner source, 200 x 200
+    receiver carpet): every step of nt = 3000, source and receiver boxes."""
+    w = S.random_smooth_3d(nt=3000)
+    prob = _gprob(smi, w)
+    for which, pts in (("source", w.srcs[0]), ("receivers", w.recs[0])):
+        lo, hi = smi.smi_box_table(_dev(w.vp), _dev(w.rho), prob, w.srcs, w.recs, _dev(w.stf), 0,
+                                   which, 0, w.nt)
+        rlo, rhi = O.box_table(_oprob(w), w.vp, w.rho, pts, 0, w.nt)
+        assert np.array_equal(lo, rlo) and np.array_equal(hi, rhi)
+
+
+def _observed(w, scale=0.8):
+    """Observed data from the oracle (never from the GPU path): a scaled
+    copy of the oracle's seismograms plus seeded noise."""
+    ref = O.forward(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0])
+    rng = np.random.default_rng(7)
+    return (scale * ref + 0.02 * np.abs(ref).max() * rng.standard_normal(ref.shape)).astype(np.float32)
+
+
+@pytest.mark.parametrize("case", sorted(SMALL))
+@pytest.mark.parametrize("use_box", [True, False])
+def test_gradient_parity(smi, case, use_box):
+    w = SMALL[case]()
+    dobs = _observed(w)
+    J, g = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), _gprob(smi, w, use_box=use_box), w.srcs,
+                                w.recs, _dev(w.stf), _dev(dobs))
+    Jr, gr, _ = O.gradient(_oprob(w, use_box=use_box), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
+    assert abs(float(J.item()) - Jr) <= 1e-5 * Jr
+    assert _rel(g.cpu().numpy(), gr) <= IMG_TOL
+
+
+@pytest.mark.parametrize("case", sorted(SMALL))
+def test_rtm_parity(smi, case):
+    w = SMALL[case]()
+    dobs = _observed(w, scale=1.0)
+    img = smi.smi_rtm(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs, _dev(w.stf),
+                      _dev(dobs))
+    _, ir, _ = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs, mode="rtm")
+    assert _rel(img.cpu().numpy(), ir) <= IMG_TOL
+
+
+@pytest.mark.parametrize("prec,tol", [("f16", 5e-3), ("bf16", 3e-2)])
+def test_16bit_boundaries_report_their_error(smi, prec, tol):
+    w = SMALL["2d_o8_on"]()
+    dobs = _observed(w)
+    _, g32 = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs,
+                                  _dev(w.stf), _dev(dobs))
+    _, g16 = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), _gprob(smi, w, shell_prec=prec),
+                                  w.srcs, w.recs, _dev(w.stf), _dev(dobs))
+    _, gr, _ = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
+    e16 = _rel(g16.cpu().numpy(), gr)
+    e32 = _rel(g32.cpu().numpy(), gr)
+    print(f"{prec} boundary storage: gradient error {e16:.2e} (FP32 storage {e32:.2e})")
+    assert e16 <= tol
+
+
+def test_host_pointers_match_device_pointers(smi):
+    w = SMALL["2d_o4_off"]()
+    prob = _gprob(smi, w)
+    d = smi.smi_forward(_dev(w.vp), _dev(w.rho), prob, w.srcs, w.recs, _dev(w.stf))[0].cpu().numpy()
+    h = smi.smi_forward(w.vp, w.rho, prob, w.srcs, w.recs, w.stf)[0]
+    assert isinstance(h, np.ndarray) and np.array_equal(d, h)
+    dobs = _observed(w)
+    Jd, gd = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), prob, w.srcs, w.recs, _dev(w.stf), _dev(dobs))
+    Jh, gh = smi.smi_fwi_gradient(w.vp, w.rho, prob, w.srcs, w.recs, w.stf, dobs)
+    assert float(Jd.item()) == float(Jh[0]) and np.array_equal(gd.cpu().numpy(), gh)
+
+
+def test_shot_batching_is_bitwise_invariant(smi):
+    """Shots propagated together or one at a time give identical results."""
+    base = S.layered_fault_2d(nz=60, nx=140, nt=300, nshot=4, order=4)
+    base.srcs[:, 1] = [200.0, 600.0, 1000.0, 1500.0]
+    prob_all = _gprob(smi, base)
+    prob_one = _gprob(smi, base, max_batch=1)
+    vp, rho, stf = _dev(base.vp), _dev(base.rho), _dev(base.stf)
+    a = smi.smi_forward(vp, rho, prob_all, base.srcs, base.recs, stf, flat=True)
+    b = smi.smi_forward(vp, rho, prob_one, base.srcs, base.recs, stf, flat=True)
+    assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+    dobs = 0.5 * a
+    ga = smi.smi_fwi_gradient(vp, rho, prob_all, base.srcs, base.recs, stf, dobs)[1]
+    gb = smi.smi_fwi_gradient(vp, rho, prob_one, base.srcs, base.recs, stf, dobs)[1]
+    assert np.array_equal(ga.cpu().numpy(), gb.cpu().numpy())
+
+
+def test_multi_shot_gradient_sums_single_shots(smi):
+    base = S.layered_fault_2d(nz=50, nx=120, nt=250, nshot=3, order=4)
+    base.srcs[:, 1] = [150.0, 700.0, 1300.0]
+    prob = _gprob(smi, base)
+    vp, rho, stf = _dev(base.vp), _dev(base.rho), _dev(base.stf)
+    seis = smi.smi_forward(_dev(base.vp_true), rho, prob, base.srcs, base.recs, stf)
+    J, g = smi.smi_fwi_gradient(vp, rho, prob, base.srcs, base.recs, stf, seis)
+    Js, gs = 0.0, 0.0
+    for s in range(3):
+        j, gg = smi.smi_fwi_gradient(vp, rho, prob, base.srcs[s:s + 1], base.recs[s:s + 1], stf, seis[s])
+        Js += float(j.item())
+        gs = gs + gg.cpu().numpy().astype(np.float64)
+    assert abs(float(J.item()) - Js) <= 1e-12 * Js
+    assert _rel(g.cpu().numpy(), gs) <= 1e-6
+
+
+def test_gradient_parity_layered_fault_2d_full_grid(smi):
+    """Full 301 x 1001 grid, order 8, 1001 receivers, one shot of the 40,
+    observed data from the oracle on the true model; nt shortened to 500
+    so that the FP64 oracle finishes in a test."""
+    w = S.layered_fault_2d(nt=500).subset([5])
+    dobs = O.forward(_oprob(w), w.vp_true, w.rho, w.stf, w.srcs[0], w.recs[0]).astype(np.float32)
+    J, g = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs,
+                                _dev(w.stf), _dev(dobs))
+    Jr, gr, _ = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
+    assert abs(float(J.item()) - Jr) <= 1e-5 * Jr
+    assert _rel(g.cpu().numpy(), gr) <= IMG_TOL
+
+
+def test_errors_are_reported(smi):
+    w = SMALL["2d_o4_off"]()
+    with pytest.raises(smi.SmiError) as e:
+        smi.smi_forward(_dev(w.vp), _dev(w.rho), smi.Problem(w.d, w.nt, 5e-3, w.fm, nb=8), w.srcs,
+                        w.recs, _dev(w.stf))
+    assert e.value.code == -2
+    with pytest.raises(smi.SmiError) as e:
+        smi.smi_forward(_dev(w.vp), _dev(w.rho), smi.Problem(w.d, w.nt, w.dt, 60.0, nb=8), w.srcs,
+                        w.recs, _dev(w.stf))
+    assert e.value.code == -3
+    bad = w.srcs.copy()
+    bad[0, 0] = -100.0
+    with pytest.raises(smi.SmiError) as e:
+        smi.smi_forward(_dev(w.vp), _dev(w.rho), _gprob(smi, w), bad, w.recs, _dev(w.stf))
+    assert e.value.code == -1
+    vp = w.vp.copy()
+    vp[3, 3] = -1.0
+    with pytest.raises(smi.SmiError) as e:
+        smi.smi_forward(_dev(vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs, _dev(w.stf))
+    assert e.value.code == -1
