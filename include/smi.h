@@ -169,6 +169,27 @@ int smi_query(const smi_model *model, const smi_geometry *geom, const smi_wavele
 int smi_box_table(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
                   const smi_opts *opts, int shot, int which, int n0, int count, int *lo, int *hi);
 
+/* Forward modelling that allocates no device memory, for callers that may
+ * not call cudaMalloc: code running where another runtime or a caching
+ * allocator already owns the device's memory, or loops that cannot afford an
+ * allocation's synchronisation or failure.  The paper has no counterpart; it
+ * computes exactly what smi_forward computes.
+ *   - Working memory is one fixed 64 MiB device array inside the library
+ *     (resident on every GPU that loads the library until the process
+ *     exits).  A problem needs about 4*(ndim+3) bytes per extended grid
+ *     node plus CPML and stencil tables; larger problems, or an axis of more
+ *     than 8192 extended nodes, return SMI_ERR_ARG with the size needed.
+ *   - vp, rho, stf and seis must be device pointers (SMI_ERR_ARG otherwise);
+ *     geometry stays on the host.  Shots run one after another.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and corrupt each other's results.
+ *     The array keeps the last call's contents; every shot clears what must
+ *     start at zero. */
+int smi_forward_noalloc(const smi_model *model, const smi_geometry *geom,
+                        const smi_wavelet *wav, const smi_opts *opts, float *seis);
+
 /* Measurements of the calling thread's last smi_forward / smi_rtm /
  * smi_fwi_gradient call. */
 int smi_last_stats(smi_stats *st);

@@ -605,6 +605,10 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
 }
 
 }  // namespace
+
+// Error message of the calling thread, for entry points in other files.
+void record_error(const char *msg) { t_err = msg; }
+
 }  // namespace smi
 
 using namespace smi;

@@ -79,7 +79,7 @@ class smi_stats(ctypes.Structure):
 
 # C functions exported by libsmi (the names of include/smi.h)
 EXPORTS = ["smi_opts_default", "smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query",
-           "smi_box_table", "smi_last_stats", "smi_last_error", "smi_version"]
+           "smi_box_table", "smi_last_stats", "smi_last_error", "smi_version", "smi_forward_noalloc"]
 
 
 def _load():
@@ -92,6 +92,7 @@ def _load():
     L.smi_opts_default.restype = None
     common = [P(smi_model), P(smi_geometry), P(smi_wavelet), P(smi_opts)]
     L.smi_forward.argtypes = common + [vp]
+    L.smi_forward_noalloc.argtypes = common + [vp]
     L.smi_rtm.argtypes = common + [vp, vp]
     L.smi_fwi_gradient.argtypes = common + [vp, vp, vp]
     L.smi_query.argtypes = common + [c_int, P(ctypes.c_size_t), P(ctypes.c_size_t), P(ctypes.c_size_t)]
@@ -100,7 +101,7 @@ def _load():
     L.smi_last_error.restype = ctypes.c_char_p
     L.smi_version.restype = ctypes.c_char_p
     for name in ("smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query", "smi_box_table",
-                 "smi_last_stats"):
+                 "smi_last_stats", "smi_forward_noalloc"):
         getattr(L, name).restype = c_int
     return L
 
@@ -242,6 +243,22 @@ def smi_forward(vp, rho, prob: Problem, srcs, recs, stf, stream=None, flat=False
     o = _opts(prob, stream)
     out, pout = _out(out, int(prob.nt * off[-1]), cuda, vp.device if cuda else None)
     _check(_lib.smi_forward(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w), ctypes.byref(o), pout))
+    return out if flat else _split(out, prob.nt, off)
+
+
+def smi_forward_noalloc(vp, rho, prob: Problem, srcs, recs, stf, out, stream=None, flat=False):
+    """smi_forward without device allocations: working memory comes from a
+    fixed array inside the library (for callers that may not allocate device
+    memory).  vp, rho, stf and the preallocated output `out` must be CUDA
+    tensors; calls that overlap on the GPU race on that shared array."""
+    m, keep_m, cuda, shape = _model(vp, rho, prob.d)
+    geo, keep_g, off = _geometry(srcs, recs)
+    ks, ps, _ = _as_f32(stf)
+    w = smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
+    o = _opts(prob, stream)
+    out, pout = _out(out, int(prob.nt * off[-1]), cuda, vp.device if cuda else None)
+    _check(_lib.smi_forward_noalloc(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w),
+                                    ctypes.byref(o), pout))
     return out if flat else _split(out, prob.nt, off)
 
 
