@@ -13,6 +13,7 @@
 
 #include "smi_box.h"
 #include "smi_internal.h"
+#include "smi_stencil3d.h"
 
 namespace smi {
 namespace {
@@ -167,8 +168,7 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
         g.ntot *= g.ne[a];
         g.nphys *= S.n[a];
     }
-    g.S = 2 * o->nb + 1;
-    for (int a = 0; a < 3; a++) g.slab_n[a] = a < m->ndim ? g.ntot / g.ne[a] * g.S : 0;
+    set_layout(g, S.n);
     g.dt = (float)w->dt;
     g.use_box = o->use_box ? 1 : 0;
     double coef[kMaxHalf] = {0};
@@ -454,9 +454,12 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         tm.on = o->profile != 0;
         tm.st = st;
         unsigned *d_flag = ar.get<unsigned>(1);
+        unsigned *d_wait = ar.get<unsigned>(1);
         unsigned *d_absmax = ar.get<unsigned>(6 * (size_t)B);
         if (!ar.ok) return fail(SMI_ERR_NOMEM, "device allocation failed");
         launch_zero(lc, d_flag, sizeof(unsigned));
+        launch_zero(lc, d_wait, sizeof(unsigned));
+        const bool fast3 = stencil3d_supported(g);
 
         for (int s0 = 0; s0 < S.nshot; s0 += B) {
             const int nb_shot = std::min(B, S.nshot - s0);
@@ -502,6 +505,9 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             if (!ba.ok) return fail(SMI_ERR_NOMEM, "device allocation for a batch of %d shots failed", nb_shot);
             cudaMemcpyAsync(d_roff, roff.data(), sizeof(int) * roff.size(), cudaMemcpyHostToDevice, st);
             cudaMemcpyAsync(d_soff, soff.data(), sizeof(long long) * soff.size(), cudaMemcpyHostToDevice, st);
+            Maps3 mF{}, mA{};
+            if (fast3 && (!make_maps3(mF, g, F, nb_shot) || (kind != 0 && !make_maps3(mA, g, A, nb_shot))))
+                return fail(SMI_ERR_CUDA, "tensor map encoding failed");
             Batch b{};
             b.nshot = nb_shot;
             b.box_src = S.d_box_src + 6 * s0;
@@ -521,8 +527,13 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             for (int it = 0; it < S.nt; it++) {
                 if (kind != 0) launch_save_bands(lc, g, b, F, bd, it, d_absmax);
                 tm.begin(0);
-                launch_fwd_v(lc, g, b, F, it);
-                launch_fwd_p(lc, g, b, F, it);
+                if (fast3) {
+                    launch3_v(lc, mF, g, b, F, it, 0, d_wait);
+                    launch3_p(lc, mF, nullptr, g, b, F, it, 0, d_wait, nullptr, 0, nullptr, 0.0f);
+                } else {
+                    launch_fwd_v(lc, g, b, F, it);
+                    launch_fwd_p(lc, g, b, F, it);
+                }
                 tm.end();
                 launch_inject_source(lc, g, b, F.p, S.stf, it, (float)S.src_scale);
                 if (max_rec > 0) launch_gather(lc, g, b, F.p, seis, d_soff, S.nt, it);
@@ -555,13 +566,25 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 const int mrev = S.nt - 1 - it;
                 if (max_rec > 0) launch_adj_inject(lc, g, b, A.p, res, d_soff, S.nt, it);
                 tm.begin(2);
-                launch_recon_p(lc, g, b, F, A.p, acc, mode, S.stf, it, (float)S.src_scale);
-                launch_recon_v(lc, g, b, F, it);
+                if (fast3) {
+                    launch3_p(lc, mF, &mA, g, b, F, it, 2, d_wait, acc, mode, S.stf, (float)S.src_scale);
+                    launch3_v(lc, mF, g, b, F, it, 2, d_wait);
+                } else {
+                    launch_recon_p(lc, g, b, F, A.p, acc, mode, S.stf, it, (float)S.src_scale);
+                    launch_recon_v(lc, g, b, F, it);
+                }
                 tm.end();
                 launch_restore_bands(lc, g, b, F, bd, it);
                 tm.begin(1);
-                launch_adj_v(lc, g, b, A, mrev);
-                launch_adj_p(lc, g, b, A, mrev);
+                if (fast3) {
+                    launch_adj_corrections(lc, g, b, A, mrev, true);
+                    launch3_v(lc, mA, g, b, A, mrev, 1, d_wait);
+                    launch_adj_corrections(lc, g, b, A, mrev, false);
+                    launch3_p(lc, mA, nullptr, g, b, A, mrev, 1, d_wait, nullptr, 0, nullptr, 0.0f);
+                } else {
+                    launch_adj_v(lc, g, b, A, mrev);
+                    launch_adj_p(lc, g, b, A, mrev);
+                }
                 tm.end();
                 for (int s = 0; s < nb_shot; s++) {
                     int lo[3], hi[3];
@@ -590,9 +613,11 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             cudaMemcpyAsync(misfit_out, d_misfit, sizeof(double),
                             is_device_ptr(misfit_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
         }
-        unsigned flag = 0;
+        unsigned flag = 0, waitflag = 0;
         cudaMemcpyAsync(&flag, d_flag, sizeof flag, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(&waitflag, d_wait, sizeof waitflag, cudaMemcpyDeviceToHost, st);
         rc = finish_stream(st);
+        if (!rc && waitflag) rc = fail(SMI_ERR_TIMEOUT, "a bounded wait for a tile copy gave up");
         if (!rc && flag) rc = fail(SMI_ERR_UNSTABLE, "non-finite values in the wavefield or outputs");
         tm.collect(t_stats);
         t_stats.kernel_launches = launches;

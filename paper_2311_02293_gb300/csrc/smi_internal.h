@@ -19,8 +19,9 @@ constexpr int kMaxTaps = 8;        // 2 * ri, ri = order/2 <= 4
 struct Grid {
     int ndim, N, ri, nb;
     int ne[3];             // extended sizes (1 for an inactive axis)
+    int px;                // allocated row length along z: ne[0] rounded up to 8 (16-byte rows)
     int L[3], H[3];        // first/last physical node along each axis (extended index)
-    long long ntot;        // points of one extended field
+    long long ntot;        // allocated points of one extended field: px * ne[1] * ne[2]
     long long nphys;       // points of the physical grid
     int S;                 // slab length along its axis: 2*nb + 1
     long long slab_n[3];   // points of the slab array of axis a
@@ -54,7 +55,9 @@ struct Batch {
     int max_rec;            // largest receiver count of a shot in the batch
 };
 
-// Wavefields of a batch; shot s of field f is at f + s * ntot.
+// Wavefields of a batch; shot s of field f is at f + s * ntot, node
+// (i1, i2, i3) at i1 + px * (i2 + ne1 * i3); z nodes px > i1 >= ne0 are padding
+// that no kernel reads as grid data.
 struct Fields {
     float *p;
     float *v[3];
@@ -124,6 +127,9 @@ void launch_adj_inject(const LaunchCtx &lc, const Grid &g, const Batch &b, float
                        const float *res, const long long *seis_off, int nt, int it);
 void launch_adj_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m);
 void launch_adj_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m);
+// Transposed CPML terms of the adjoint over the slabs (vel: velocity part,
+// else pressure part), one launch per axis; run before the interior kernels.
+void launch_adj_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, bool vel);
 void launch_recon_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f,
                     const float *lp, float *acc, int mode, const float *stf, int it,
                     float src_scale);
@@ -133,6 +139,9 @@ void launch_reduce_shots(const LaunchCtx &lc, const Grid &g, const float *acc, i
 void launch_finalize_grad(const LaunchCtx &lc, long long n, const float *vp, float dt,
                           float *g);
 void launch_nonfinite(const LaunchCtx &lc, const float *x, long long n, unsigned *flag);
+// Sets the padded layout: px, ntot, nphys and the slab sizes (ne, nb, ndim set).
+void set_layout(Grid &g, const int n[3]);
+
 void launch_box_table(const LaunchCtx &lc, const Grid &g, const int *ext, int n0, int count,
                       int *lo, int *hi);
 

@@ -8,6 +8,8 @@
 // 4.1), computed on the device from the step counter; threads stride over
 // the box's points.  Stencil reads outside the extended grid are zero.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -23,12 +25,12 @@ constexpr int kMaxBlocksX = 152 * 16;
 
 __device__ __forceinline__ long long gidx(const Grid &g, int i1, int i2, int i3)
 {
-    return (long long)i1 + (long long)g.ne[0] * ((long long)i2 + (long long)g.ne[1] * i3);
+    return (long long)i1 + (long long)g.px * ((long long)i2 + (long long)g.ne[1] * i3);
 }
 
 __device__ __forceinline__ long long gstride(const Grid &g, int a)
 {
-    return a == 0 ? 1LL : (a == 1 ? (long long)g.ne[0] : (long long)g.ne[0] * g.ne[1]);
+    return a == 0 ? 1LL : (a == 1 ? (long long)g.px : (long long)g.px * g.ne[1]);
 }
 
 // CPML slab membership along axis a: nodes 0..nb-1 and ne-nb-1..ne-1 (the
@@ -276,6 +278,164 @@ __global__ void __launch_bounds__(kThreads) k_adj_p(Grid g, Batch b, Fields f, i
             div += D;
         }
         lp[k] = lpk - g.dt * g.K[k] * div;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Transposed CPML terms of the adjoint, applied over the slabs only, before
+// the interior adjoint kernels (which then run the plain forward scheme).
+// Axis a, band of nodes whose stencil reaches the axis-a CPML layer:
+//   V (lam_v update): lv_a -= dt b_a D_a[eta_a],  eta_a = Ap_a (lp + phi_a),
+//                     after the deferred chi_a <- Bv_a (chi_a + lv_a);
+//   P (lam_p update): lp -= dt kappa D_a[zeta_a], zeta_a = Av_a (lv_a + chi_a),
+//                     after phi_a <- Bp_a (phi_a + lp).
+// Region: the receiver box (m reverse steps) with axis a restricted to
+// [0, nb+N-1] and [ne_a-nb-N-1, ne_a-1].
+struct Band {
+    int lo[3], hi[3];
+    int n0, i1a, nband;   // nodes in the low interval (from lo[a]), start of the high interval, band nodes
+    long long vol;
+};
+
+__device__ __forceinline__ Band band_region(const Grid &g, const int *ext, int m, int a, int N)
+{
+    Band r;
+    box_bounds(g, ext, m, r.lo, r.hi);
+    const int wl = g.nb + N;                  // low interval [0, wl-1]
+    const int hs = max(g.ne[a] - g.nb - N - 1, wl);
+    const int a0 = r.lo[a], a1 = min(r.hi[a], wl - 1);
+    r.n0 = max(0, a1 - a0 + 1);
+    r.i1a = max(r.lo[a], hs);
+    const int n1 = max(0, r.hi[a] - r.i1a + 1);
+    r.nband = r.n0 + n1;
+    long long v = r.nband;
+    for (int b = 0; b < 3; b++)
+        if (b != a) v *= max(0, r.hi[b] - r.lo[b] + 1);
+    r.vol = v;
+    return r;
+}
+
+__device__ __forceinline__ void band_node(const Band &r, int a, long long t, int i[3])
+{
+    // the band axis runs fastest only for a = 0; otherwise z stays fastest
+    int w[3];
+    for (int b = 0; b < 3; b++) w[b] = (b == a) ? 0 : r.hi[b] - r.lo[b] + 1;
+    const int nband = r.nband;
+    int j;
+    if (a == 0) {
+        j = (int)(t % nband);
+        const long long u = t / nband;
+        i[1] = r.lo[1] + (int)(u % w[1]);
+        i[2] = r.lo[2] + (int)(u / w[1]);
+    } else if (a == 1) {
+        i[0] = r.lo[0] + (int)(t % w[0]);
+        const long long u = t / w[0];
+        j = (int)(u % nband);
+        i[2] = r.lo[2] + (int)(u / nband);
+    } else {
+        i[0] = r.lo[0] + (int)(t % w[0]);
+        const long long u = t / w[0];
+        i[1] = r.lo[1] + (int)(u % w[1]);
+        j = (int)(u / w[1]);
+    }
+    i[a] = j < r.n0 ? r.lo[a] + j : r.i1a + (j - r.n0);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_adjc_v(Grid g, Batch b, Fields f, int m)
+{
+    const int s = blockIdx.y, a = blockIdx.z;
+    const Band r = band_region(g, b.box_rec + 6 * s, m, a, N);
+    const long long st = gstride(g, a);
+    const float *lp = f.p + s * g.ntot;
+    float *lv = f.v[a] + s * g.ntot;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < r.vol;
+         t += (long long)gridDim.x * blockDim.x) {
+        int i[3];
+        band_node(r, a, t, i);
+        const long long k = gidx(g, i[0], i[1], i[2]);
+        const int ia = i[a];
+        if (in_slab(g, a, ia)) {
+            float *ch = f.psip[a] + s * g.slab_n[a] + slab_index(g, a, i[0], i[1], i[2]);
+            *ch = g.cvb[a][ia] * (*ch + lv[k]);
+        }
+        float E = 0.0f;
+#pragma unroll
+        for (int l = 1; l <= N; l++) {
+            float h[2];
+            const int off[2] = {l, 1 - l};
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                const int j = ia + off[e];
+                h[e] = 0.0f;
+                if (j >= 0 && j < g.ne[a] && in_slab(g, a, j)) {
+                    const float A = g.cpa[a][j];
+                    if (A != 0.0f) {
+                        int jj[3] = {i[0], i[1], i[2]};
+                        jj[a] = j;
+                        h[e] = A * (lp[k + off[e] * st] + f.psiv[a][s * g.slab_n[a] + slab_index(g, a, jj[0], jj[1], jj[2])]);
+                    }
+                }
+            }
+            E += g.c[a][l - 1] * (h[0] - h[1]);
+        }
+        if (E != 0.0f) lv[k] -= g.dt * buoyancy(g, a, ia, k, g.rho[k]) * E;
+    }
+}
+
+// phi_a <- Bp_a (phi_a + lp) over the p-grid slab of every axis (blockIdx.z),
+// with lp before any of this step's pressure corrections.
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_adjc_phi(Grid g, Batch b, Fields f, int m)
+{
+    const int s = blockIdx.y, a = blockIdx.z;
+    const Band r = band_region(g, b.box_rec + 6 * s, m, a, N);
+    const float *lp = f.p + s * g.ntot;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < r.vol;
+         t += (long long)gridDim.x * blockDim.x) {
+        int i[3];
+        band_node(r, a, t, i);
+        if (!in_slab(g, a, i[a])) continue;
+        float *ph = f.psiv[a] + s * g.slab_n[a] + slab_index(g, a, i[0], i[1], i[2]);
+        *ph = g.cpb[a][i[a]] * (*ph + lp[gidx(g, i[0], i[1], i[2])]);
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_adjc_p(Grid g, Batch b, Fields f, int m, int a)
+{
+    const int s = blockIdx.y;
+    const Band r = band_region(g, b.box_rec + 6 * s, m, a, N);
+    const long long st = gstride(g, a);
+    float *lp = f.p + s * g.ntot;
+    const float *lv = f.v[a] + s * g.ntot;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < r.vol;
+         t += (long long)gridDim.x * blockDim.x) {
+        int i[3];
+        band_node(r, a, t, i);
+        const long long k = gidx(g, i[0], i[1], i[2]);
+        const int ia = i[a];
+        float F = 0.0f;
+#pragma unroll
+        for (int l = 1; l <= N; l++) {
+            float h[2];
+            const int off[2] = {l - 1, -l};
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                const int j = ia + off[e];
+                h[e] = 0.0f;
+                if (j >= 0 && j < g.ne[a] && in_slab(g, a, j)) {
+                    const float A = g.cva[a][j];
+                    if (A != 0.0f) {
+                        int jj[3] = {i[0], i[1], i[2]};
+                        jj[a] = j;
+                        h[e] = A * (lv[k + off[e] * st] + f.psip[a][s * g.slab_n[a] + slab_index(g, a, jj[0], jj[1], jj[2])]);
+                    }
+                }
+            }
+            F += g.c[a][l - 1] * (h[0] - h[1]);
+        }
+        if (F != 0.0f) lp[k] -= g.dt * g.K[k] * F;
     }
 }
 
@@ -572,9 +732,14 @@ __global__ void k_extend_model(Grid g, const float *vp, const float *rho, int n1
 {
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < g.ntot;
          t += (long long)gridDim.x * blockDim.x) {
-        const int i1 = (int)(t % g.ne[0]);
-        const int i2 = (int)((t / g.ne[0]) % g.ne[1]);
-        const int i3 = (int)(t / ((long long)g.ne[0] * g.ne[1]));
+        const int i1 = (int)(t % g.px);
+        const int i2 = (int)((t / g.px) % g.ne[1]);
+        const int i3 = (int)(t / ((long long)g.px * g.ne[1]));
+        if (i1 >= g.ne[0]) {            // row padding
+            rho_e[t] = 0.0f;
+            K[t] = 0.0f;
+            continue;
+        }
         const int j1 = min(max(i1 - g.L[0], 0), n1 - 1);
         const int j2 = min(max(i2 - g.L[1], 0), n2 - 1);
         const int j3 = min(max(i3 - g.L[2], 0), n3 - 1);
@@ -676,6 +841,30 @@ void launch_recon_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f
 {
     dim3 grid(blocks_for(g.nphys), b.nshot);
     SMI_DISPATCH(k_recon_v, grid, g, b, f, it);
+}
+
+void launch_adj_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, bool vel)
+{
+    // a band holds at most 2 (nb + N + 1) nodes along its axis
+    long long vol = 0;
+    for (int a = 0; a < g.ndim; a++) vol = std::max(vol, g.ntot / g.ne[a] * (2LL * (g.nb + g.N + 1)));
+    if (vel) {
+        dim3 grid(blocks_for(vol), b.nshot, g.ndim);     // axes touch disjoint arrays
+        if (g.N == 2) k_adjc_v<2><<<grid, kThreads, 0, S(lc)>>>(g, b, f, m);
+        else k_adjc_v<4><<<grid, kThreads, 0, S(lc)>>>(g, b, f, m);
+        ++*lc.launches;
+        return;
+    }
+    dim3 gphi(blocks_for(vol), b.nshot, g.ndim);
+    if (g.N == 2) k_adjc_phi<2><<<gphi, kThreads, 0, S(lc)>>>(g, b, f, m);
+    else k_adjc_phi<4><<<gphi, kThreads, 0, S(lc)>>>(g, b, f, m);
+    ++*lc.launches;
+    for (int a = 0; a < g.ndim; a++) {          // all axes update lp: one launch each
+        dim3 grid(blocks_for(vol), b.nshot);
+        if (g.N == 2) k_adjc_p<2><<<grid, kThreads, 0, S(lc)>>>(g, b, f, m, a);
+        else k_adjc_p<4><<<grid, kThreads, 0, S(lc)>>>(g, b, f, m, a);
+        ++*lc.launches;
+    }
 }
 
 void launch_inject_source(const LaunchCtx &lc, const Grid &g, const Batch &b, float *p,

@@ -178,8 +178,7 @@ int forward_noalloc(const smi_model *m, const smi_geometry *geo, const smi_wavel
         g.ntot *= g.ne[a];
         g.nphys *= n[a];
     }
-    g.S = 2 * o->nb + 1;
-    for (int a = 0; a < 3; a++) g.slab_n[a] = a < m->ndim ? g.ntot / g.ne[a] * g.S : 0;
+    set_layout(g, n);
     g.dt = (float)w->dt;
     g.use_box = o->use_box ? 1 : 0;
     double coef[kMaxHalf] = {0};

@@ -122,4 +122,14 @@ bool make_stencil(const Grid &g, const double pos[3], double kaiser_b, Stencil *
     return true;
 }
 
+void set_layout(Grid &g, const int n[3])
+{
+    g.px = (g.ne[0] + 7) / 8 * 8;
+    g.ntot = (long long)g.px * g.ne[1] * g.ne[2];
+    g.nphys = (long long)n[0] * n[1] * n[2];
+    g.S = 2 * g.nb + 1;
+    const long long plane = (long long)g.ne[0] * g.ne[1] * g.ne[2];
+    for (int a = 0; a < 3; a++) g.slab_n[a] = a < g.ndim ? plane / g.ne[a] * g.S : 0;
+}
+
 }  // namespace smi

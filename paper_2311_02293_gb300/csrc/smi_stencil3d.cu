@@ -1,0 +1,886 @@
+// smi_stencil3d.cu -- 3D staggered-grid stencil kernels for sm_103a.
+//
+// Two kernels advance one half of a leap-frog step each (Sec. 2.1 update
+// equations): k3_v updates the three velocity components from p, k3_p
+// updates p from the velocities.  Each comes in three modes:
+//   FWD  forward modelling, CPML memory variables in the slabs;
+//   ADJ  the interior part of the exact discrete adjoint in "same solver"
+//        form (the forward scheme itself); the transposed CPML terms are
+//        added beforehand by slab-only correction kernels (smi_kernels.cu);
+//   REC  source-field reconstruction backwards in time (Sec. 4.2) on the
+//        physical domain, with the imaging / gradient accumulation fused
+//        into the pressure kernel.
+//
+// Work decomposition: persistent CTAs (a fixed multiple of the SM count)
+// walk the work items of the computing box (Sec. 4.1, evaluated on the
+// device from the step counter): 32 (z) x 16 (x) column tiles times chunks
+// of y planes.  A CTA streams its chunk along y.  Plane tiles with their z/x
+// halos arrive by TMA (cp.async.bulk.tensor) into a ring of shared-memory
+// slots guarded by mbarriers; out-of-grid parts of a tile are filled with
+// zeros by the TMA unit, which is exactly the scheme's zero value outside
+// the extended grid.  y-neighbours are kept in a register queue.  Each
+// thread owns 4 consecutive z nodes of one x column: z-derivatives read a
+// 12-float window with three 128-bit shared loads, x-derivatives one 128-bit
+// load per tap.  Every mbarrier wait is bounded; a CTA that gives up sets
+// bit 0 of the error word, drains its own copies (bounded) and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "smi_box.h"
+#include "smi_internal.h"
+#include "smi_stencil3d.h"
+
+namespace smi {
+namespace s3 {
+
+constexpr int TZ = 32, TX = 16, NTHR = 128;
+constexpr int ZW = 40;                 // z extent of haloed tiles: [z0-4, z0+36)
+constexpr long long kSpin = 1LL << 22; // bounded mbarrier polls
+
+enum { FWD = 0, ADJ = 1, REC = 2 };
+
+__host__ __device__ constexpr int rup32(int n) { return (n + 31) / 32 * 32; }
+
+// --- shared-memory slot layouts (floats) ---------------------------------
+// Haloed ring: slots resident while their plane feeds a derivative (N+1
+// planes for the velocity kernel, N for the pressure kernel) plus PFP planes
+// of lead.  Core ring: the pointwise 32 x 16 tiles of one plane, SC slots.
+constexpr int PFP = 1, SC = 3, CORE = TZ * TX;
+
+template <int N> struct VLay {
+    static constexpr int PR = TX + 2 * N - 1;            // p tile rows: x0-N+1 .. x0+TX-1+N
+    static constexpr int P_OFF = 0, P_SZ = rup32(ZW * PR);
+    static constexpr int R_OFF = P_SZ, R_SZ = rup32(36 * (TX + 1));   // rho: z0..z0+35, x0..x0+TX
+    static constexpr int SLOT = P_SZ + R_SZ;
+    static constexpr int S = N + 1 + PFP;
+    static constexpr unsigned BYTES = (unsigned)(ZW * PR + 36 * (TX + 1)) * 4u;
+    static constexpr int CSLOT = 3 * CORE;                              // vz, vx, vy
+    static constexpr unsigned CBYTES = 3u * CORE * 4u;
+    static constexpr int SMEM = (S * SLOT + SC * CSLOT) * 4;
+};
+template <int N> struct PLay {
+    static constexpr int XR = TX + 2 * N - 1;            // vx tile rows: x0-N .. x0+TX-2+N
+    static constexpr int Z_OFF = 0, Z_SZ = rup32(ZW * TX);            // vz: z0-4.., x core
+    static constexpr int X_OFF = Z_SZ, X_SZ = rup32(TZ * XR);         // vx: z core
+    static constexpr int Y_OFF = Z_SZ + X_SZ, Y_SZ = CORE;            // vy: core
+    static constexpr int SLOT = Z_SZ + X_SZ + Y_SZ;
+    static constexpr int S = N + PFP;
+    static constexpr unsigned BYTES = (unsigned)(ZW * TX + TZ * XR + CORE) * 4u;
+    static constexpr int CSLOT = 3 * CORE;                              // p, kappa, lambda_p
+    static constexpr int SMEM = (S * SLOT + SC * CSLOT) * 4;
+};
+
+// --- PTX helpers ------------------------------------------------------------
+__device__ __forceinline__ uint32_t sptr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, unsigned n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sptr(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect(uint64_t *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sptr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(sptr(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity)
+{
+    for (long long i = 0; i < kSpin; i++)
+        if (mbar_test(b, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma4(float *dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(sptr(dst)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(sptr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void put(float (&a)[4], float4 v) { a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w; }
+
+__device__ __forceinline__ long long gidx(const Grid &g, int i1, int i2, int i3)
+{
+    return (long long)i1 + (long long)g.px * ((long long)i2 + (long long)g.ne[1] * i3);
+}
+__device__ __forceinline__ bool slab(const Grid &g, int a, int j) { return j < g.nb || j >= g.ne[a] - g.nb - 1; }
+__device__ __forceinline__ long long slab_index(const Grid &g, int a, int i1, int i2, int i3)
+{
+    if (a == 0) {
+        const int js = i1 < g.nb ? i1 : i1 - (g.ne[0] - 2 * g.nb - 1);
+        return (long long)js + (long long)g.S * ((long long)i2 + (long long)g.ne[1] * i3);
+    }
+    if (a == 1) {
+        const int js = i2 < g.nb ? i2 : i2 - (g.ne[1] - 2 * g.nb - 1);
+        return (long long)i1 + (long long)g.ne[0] * ((long long)js + (long long)g.S * i3);
+    }
+    const int js = i3 < g.nb ? i3 : i3 - (g.ne[2] - 2 * g.nb - 1);
+    return (long long)i1 + (long long)g.ne[0] * ((long long)i2 + (long long)g.ne[1] * js);
+}
+
+// --- work decomposition ---------------------------------------------------
+struct Item {
+    int s, z0, x0, ya, yb;
+    int lo[3], hi[3];     // update region (box, clipped per mode)
+    int plo[3], phi[3];   // REC: previous-step box
+};
+
+// Box of shot s for this launch, clipped to the physical domain in REC.
+__device__ __forceinline__ void item_box(const Grid &g, const Batch &b, int mode, int s, int step, int lo[3],
+                                         int hi[3], int plo[3], int phi[3])
+{
+    if (mode == ADJ) {
+        box_bounds(g, b.box_rec + 6 * s, step, lo, hi);
+    } else {
+        box_bounds(g, b.box_src + 6 * s, step, lo, hi);
+    }
+    if (mode == REC) {
+        box_bounds(g, b.box_src + 6 * s, step - 1, plo, phi);
+        for (int a = 0; a < 3; a++) {
+            lo[a] = max(lo[a], g.L[a]);
+            hi[a] = min(hi[a], g.H[a]);
+        }
+    }
+}
+
+struct Decomp {
+    int nzt, nxt, nyc, cy, zb;
+};
+
+// Column tiles x y-chunks of a box.  The chunk count is chosen so that the
+// items fill whole waves of the persistent grid while chunks stay long (each
+// chunk re-reads about 2N+2 planes to start its pipeline).
+__device__ __forceinline__ Decomp decomp(const int lo[3], const int hi[3], int grid)
+{
+    Decomp d;
+    d.zb = lo[0] & ~31;
+    d.nzt = hi[0] >= lo[0] ? (hi[0] - d.zb) / TZ + 1 : 0;
+    d.nxt = hi[1] >= lo[1] ? (hi[1] - lo[1]) / TX + 1 : 0;
+    const int ylen = hi[2] - lo[2] + 1;
+    if (d.nzt == 0 || d.nxt == 0 || ylen <= 0) {
+        d.nzt = d.nxt = d.nyc = 0;
+        d.cy = 1;
+        return d;
+    }
+    const int cols = d.nzt * d.nxt;
+    float best = 1e30f;
+    int best_cy = ylen;
+    const int maxc = max(1, min(ylen / 8, 64));
+    for (int c = 1; c <= maxc; c++) {
+        const int cy = (ylen + c - 1) / c;
+        const int nyc = (ylen + cy - 1) / cy;
+        const long long items = (long long)cols * nyc;
+        const long long waves = (items + grid - 1) / grid;
+        // time ~ waves x (cy + pipeline start-up)
+        const float t = (float)waves * (float)(cy + 10);
+        if (t < best) {
+            best = t;
+            best_cy = cy;
+        }
+    }
+    d.cy = best_cy;
+    d.nyc = (ylen + best_cy - 1) / best_cy;
+    return d;
+}
+
+// Item w of the launch (shots in order), false past the end.
+__device__ __forceinline__ bool get_item(const Grid &g, const Batch &b, int mode, int step, long long w, Item &it)
+{
+    const int target = (int)gridDim.x;
+    for (int s = 0; s < b.nshot; s++) {
+        int lo[3], hi[3], plo[3] = {0, 0, 0}, phi[3] = {-1, -1, -1};
+        item_box(g, b, mode, s, step, lo, hi, plo, phi);
+        const Decomp d = decomp(lo, hi, target);
+        const long long n = (long long)d.nzt * d.nxt * d.nyc;
+        if (w < n) {
+            const int zi = (int)(w % d.nzt);
+            const int xi = (int)((w / d.nzt) % d.nxt);
+            const int ci = (int)(w / ((long long)d.nzt * d.nxt));
+            it.s = s;
+            it.z0 = d.zb + TZ * zi;
+            it.x0 = lo[1] + TX * xi;
+            it.ya = lo[2] + ci * d.cy;
+            it.yb = min(hi[2], it.ya + d.cy - 1);
+            for (int a = 0; a < 3; a++) {
+                it.lo[a] = lo[a];
+                it.hi[a] = hi[a];
+                it.plo[a] = plo[a];
+                it.phi[a] = phi[a];
+            }
+            return true;
+        }
+        w -= n;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool in_range(int v, int lo, int hi) { return v >= lo && v <= hi; }
+
+// ===========================================================================
+// Ring bookkeeping shared by both kernels.  All threads wait on a slot's
+// mbarrier themselves (bounded); `parity` holds the phase parity of the next
+// completion of every slot (bit k for haloed slot k, bit 16+k for core slot k).
+struct Ring {
+    int next_wait;     // next plane to wait for
+    int issued;        // last plane whose copies were issued
+};
+
+__device__ __forceinline__ bool ring_wait(uint64_t *bars, int nslots, int bitbase, unsigned &parity, Ring &r,
+                                          int plane, int base)
+{
+    const int k = (plane - base) % nslots;
+    const bool ok = mbar_wait(&bars[k], (parity >> (bitbase + k)) & 1u);
+    if (ok) {
+        parity ^= 1u << (bitbase + k);
+        r.next_wait = plane + 1;
+    }
+    return ok;
+}
+
+__device__ __forceinline__ void ring_drain(uint64_t *bars, int nslots, int bitbase, unsigned &parity, Ring &r,
+                                           int base)
+{
+    for (int y = r.next_wait; y <= r.issued; y++) {
+        const int k = (y - base) % nslots;
+        if (mbar_wait(&bars[k], (parity >> (bitbase + k)) & 1u)) parity ^= 1u << (bitbase + k);
+    }
+}
+
+__device__ __forceinline__ float buoy(float r0, float r1, bool last) { return last ? 1.0f / r0 : 2.0f / (r0 + r1); }
+
+// ===========================================================================
+// Velocity kernel.  FWD/ADJ: v_a -= dt b_a D_a p (+ CPML terms); REC:
+// v_a += dt b_a D_a p on L_a+N-1..H_a-N, zero outside the previous box.
+template <int N, int MODE>
+__global__ void __launch_bounds__(NTHR, 4)
+k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_rho,
+     const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensorMap tm_vx,
+     const __grid_constant__ CUtensorMap tm_vy, Grid g, Batch b, Fields f, int step, unsigned *err)
+{
+    using Lay = VLay<N>;
+    constexpr int S = Lay::S;
+    extern __shared__ __align__(128) float sm[];
+    float *cbase = sm + S * Lay::SLOT;
+    __shared__ __align__(8) uint64_t bar[S], cbar[SC];
+    const int tid = threadIdx.x, tzi = tid & 7, txi = tid >> 3;
+    if (tid == 0) {
+        for (int k = 0; k < S; k++) mbar_init(&bar[k], 1);
+        for (int k = 0; k < SC; k++) mbar_init(&cbar[k], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    unsigned parity = 0;
+    const float dt = g.dt;
+
+    Item it;
+    for (long long w = blockIdx.x; get_item(g, b, MODE, step, w, it); w += gridDim.x) {
+        const int s = it.s, z0 = it.z0, x0 = it.x0, ya = it.ya, yb = it.yb;
+        const int ylast = yb + N;                 // last haloed plane needed
+        const int oz = z0 + 4 * tzi, ox = x0 + txi;
+        const bool mem = oz < g.ne[0] && ox < g.ne[1];
+        const long long sh = (long long)s * g.ntot;
+        bool mz[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) mz[r] = in_range(oz + r, it.lo[0], it.hi[0]);
+        const bool mx = in_range(ox, it.lo[1], it.hi[1]);
+        // CPML memory variables (FWD only; block uniform): the tile meets a slab.
+        // The adjoint's transposed CPML terms are applied by the slab
+        // correction kernels before this one runs.
+        const int ext = 1;
+        const bool sz = (MODE == FWD) && (z0 < g.nb + ext || z0 + TZ - 1 >= g.ne[0] - g.nb - 1 - ext);
+        const bool sx = (MODE == FWD) && (x0 < g.nb + ext || x0 + TX - 1 >= g.ne[1] - g.nb - 1 - ext);
+        const int own = (txi + N - 1) * ZW + 4 * tzi + 4;   // own nodes in a p tile
+
+        // y queue of own p: entry l = plane y-N+1+l; planes before ya by plain loads
+        float q[2 * N][4];
+#pragma unroll
+        for (int l = 0; l < N - 1; l++) {
+            const int y = ya - N + 1 + l;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (mem && y >= 0 && y < g.ne[2]) v = *reinterpret_cast<const float4 *>(f.p + sh + gidx(g, oz, ox, y));
+            put(q[l], v);
+        }
+        Ring hr{ya, min(ylast, ya + S - 1)}, cr{ya, min(yb, ya + SC - 1)};
+        if (tid == 0) {
+            for (int y = ya; y <= hr.issued; y++) {
+                const int k = (y - ya) % S;
+                float *slot = sm + k * Lay::SLOT;
+                mbar_expect(&bar[k], Lay::BYTES);
+                tma4(slot + Lay::P_OFF, &tm_p, z0 - 4, x0 - N + 1, y, s, &bar[k]);
+                tma4(slot + Lay::R_OFF, &tm_rho, z0, x0, y, 0, &bar[k]);
+            }
+            for (int y = ya; y <= cr.issued; y++) {
+                const int k = (y - ya) % SC;
+                float *cs = cbase + k * Lay::CSLOT;
+                mbar_expect(&cbar[k], Lay::CBYTES);
+                tma4(cs, &tm_vz, z0, x0, y, s, &cbar[k]);
+                tma4(cs + CORE, &tm_vx, z0, x0, y, s, &cbar[k]);
+                tma4(cs + 2 * CORE, &tm_vy, z0, x0, y, s, &cbar[k]);
+            }
+        }
+        bool ok = true;
+#pragma unroll
+        for (int l = 0; l < N; l++) {
+            ok &= ring_wait(bar, S, 0, parity, hr, ya + l, ya);
+            put(q[N - 1 + l], lds4(sm + ((l) % S) * Lay::SLOT + Lay::P_OFF + own));
+        }
+        if (__syncthreads_or(!ok)) goto timeout;
+
+        for (int y = ya; y <= yb; y++) {
+            ok = ring_wait(bar, S, 0, parity, hr, y + N, ya);
+            ok &= ring_wait(cbar, SC, 16, parity, cr, y, ya);
+            const float *pt = sm + ((y - ya) % S) * Lay::SLOT;
+            const float *rt = pt + Lay::R_OFF;
+            const float *rt1 = sm + ((y + 1 - ya) % S) * Lay::SLOT + Lay::R_OFF;
+            put(q[2 * N - 1], lds4(sm + ((y + N - ya) % S) * Lay::SLOT + Lay::P_OFF + own));
+            const float *cs = cbase + ((y - ya) % SC) * Lay::CSLOT + txi * TZ + 4 * tzi;
+            const bool my = in_range(y, it.lo[2], it.hi[2]);
+            const bool sy = (MODE == FWD) && (y < g.nb + ext || y >= g.ne[2] - g.nb - 1 - ext);
+            bool keep[4];
+            if (MODE == REC) {
+                const bool kxy = in_range(ox, it.plo[1], it.phi[1]) && in_range(y, it.plo[2], it.phi[2]);
+#pragma unroll
+                for (int r = 0; r < 4; r++) keep[r] = kxy && in_range(oz + r, it.plo[0], it.phi[0]);
+            }
+            const bool act = mem && mx && my;
+            float rho0[4];
+            put(rho0, lds4(rt + txi * 36 + 4 * tzi));
+            float4 nzv, nxv, nyv;
+
+            // ---- z component ----
+            {
+                float W[12];
+                {
+                    const float *row = pt + Lay::P_OFF + (txi + N - 1) * ZW + 4 * tzi;
+                    float4 a0 = lds4(row), a1 = lds4(row + 4), a2 = lds4(row + 8);
+                    W[0] = a0.x; W[1] = a0.y; W[2] = a0.z; W[3] = a0.w;
+                    W[4] = a1.x; W[5] = a1.y; W[6] = a1.z; W[7] = a1.w;
+                    W[8] = a2.x; W[9] = a2.y; W[10] = a2.z; W[11] = a2.w;
+                }
+                const float r4 = rt[txi * 36 + 4 * tzi + 4];
+                const float rz[5] = {rho0[0], rho0[1], rho0[2], rho0[3], r4};
+                float v[4];
+                put(v, lds4(cs));
+                float D[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    float d = 0.f;
+#pragma unroll
+                    for (int l = 1; l <= N; l++) d += g.c[0][l - 1] * (W[4 + r + l] - W[4 + r - l + 1]);
+                    D[r] = d;
+                }
+                if (MODE == FWD && sz && act) {
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        const int z = oz + r;
+                        if (!mz[r] || !slab(g, 0, z)) continue;
+                        float *ps = f.psip[0] + (long long)s * g.slab_n[0] + slab_index(g, 0, z, ox, y);
+                        const float psi = g.cvb[0][z] * *ps + g.cva[0][z] * D[r];
+                        *ps = psi;
+                        D[r] += psi;
+                    }
+                }
+                float nv[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const float bz = buoy(rz[r], rz[r + 1], oz + r + 1 >= g.ne[0]);
+                    if (MODE == REC) {
+                        const bool rr = mz[r] && in_range(oz + r, g.L[0] + N - 1, g.H[0] - N);
+                        nv[r] = rr ? (keep[r] ? v[r] + dt * bz * D[r] : 0.f) : v[r];
+                    } else {
+                        nv[r] = mz[r] ? v[r] - dt * bz * D[r] : v[r];
+                    }
+                }
+                nzv = make_float4(nv[0], nv[1], nv[2], nv[3]);
+            }
+            // ---- x component ----
+            {
+                float Xr[2 * N][4];
+#pragma unroll
+                for (int l = 1; l <= N; l++) {
+                    put(Xr[N - 1 + l], lds4(pt + Lay::P_OFF + (txi + N - 1 + l) * ZW + 4 * tzi + 4));
+                    put(Xr[N - l], lds4(pt + Lay::P_OFF + (txi + N - l) * ZW + 4 * tzi + 4));
+                }
+                float rx[4], v[4];
+                put(rx, lds4(rt + (txi + 1) * 36 + 4 * tzi));
+                put(v, lds4(cs + CORE));
+                float D[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    float d = 0.f;
+#pragma unroll
+                    for (int l = 1; l <= N; l++) d += g.c[1][l - 1] * (Xr[N - 1 + l][r] - Xr[N - l][r]);
+                    D[r] = d;
+                }
+                if (MODE == FWD && sx && act && slab(g, 1, ox)) {
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        if (!mz[r]) continue;
+                        float *ps = f.psip[1] + (long long)s * g.slab_n[1] + slab_index(g, 1, oz + r, ox, y);
+                        const float psi = g.cvb[1][ox] * *ps + g.cva[1][ox] * D[r];
+                        *ps = psi;
+                        D[r] += psi;
+                    }
+                }
+                const bool lastx = ox + 1 >= g.ne[1];
+                const bool rxm = MODE == REC && in_range(ox, g.L[1] + N - 1, g.H[1] - N);
+                float nv[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const float bx = buoy(rho0[r], rx[r], lastx);
+                    if (MODE == REC) nv[r] = (mz[r] && rxm) ? (keep[r] ? v[r] + dt * bx * D[r] : 0.f) : v[r];
+                    else nv[r] = mz[r] ? v[r] - dt * bx * D[r] : v[r];
+                }
+                nxv = make_float4(nv[0], nv[1], nv[2], nv[3]);
+            }
+            // ---- y component ----
+            {
+                float ry[4], v[4];
+                put(ry, lds4(rt1 + txi * 36 + 4 * tzi));
+                put(v, lds4(cs + 2 * CORE));
+                float D[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    float d = 0.f;
+#pragma unroll
+                    for (int l = 1; l <= N; l++) d += g.c[2][l - 1] * (q[N - 1 + l][r] - q[N - l][r]);
+                    D[r] = d;
+                }
+                if (MODE == FWD && sy && act && slab(g, 2, y)) {
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        if (!mz[r]) continue;
+                        float *ps = f.psip[2] + (long long)s * g.slab_n[2] + slab_index(g, 2, oz + r, ox, y);
+                        const float psi = g.cvb[2][y] * *ps + g.cva[2][y] * D[r];
+                        *ps = psi;
+                        D[r] += psi;
+                    }
+                }
+                const bool lasty = y + 1 >= g.ne[2];
+                const bool rym = MODE == REC && in_range(y, g.L[2] + N - 1, g.H[2] - N);
+                float nv[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const float by = buoy(rho0[r], ry[r], lasty);
+                    if (MODE == REC) nv[r] = (mz[r] && rym) ? (keep[r] ? v[r] + dt * by * D[r] : 0.f) : v[r];
+                    else nv[r] = mz[r] ? v[r] - dt * by * D[r] : v[r];
+                }
+                nyv = make_float4(nv[0], nv[1], nv[2], nv[3]);
+            }
+            if (act) {
+                const long long base = sh + gidx(g, oz, ox, y);
+                *reinterpret_cast<float4 *>(f.v[0] + base) = nzv;
+                *reinterpret_cast<float4 *>(f.v[1] + base) = nxv;
+                *reinterpret_cast<float4 *>(f.v[2] + base) = nyv;
+            }
+#pragma unroll
+            for (int l = 0; l < 2 * N - 1; l++)
+#pragma unroll
+                for (int r = 0; r < 4; r++) q[l][r] = q[l + 1][r];
+            // all reads of plane y's slots are done; refill them
+            if (__syncthreads_or(!ok)) goto timeout;
+            if (tid == 0) {
+                if (hr.issued < ylast) {
+                    const int yn = hr.issued + 1;
+                    const int k = (yn - ya) % S;
+                    float *slot = sm + k * Lay::SLOT;
+                    mbar_expect(&bar[k], Lay::BYTES);
+                    tma4(slot + Lay::P_OFF, &tm_p, z0 - 4, x0 - N + 1, yn, s, &bar[k]);
+                    tma4(slot + Lay::R_OFF, &tm_rho, z0, x0, yn, 0, &bar[k]);
+                }
+                if (cr.issued < yb) {
+                    const int yn = cr.issued + 1;
+                    const int k = (yn - ya) % SC;
+                    float *c2 = cbase + k * Lay::CSLOT;
+                    mbar_expect(&cbar[k], Lay::CBYTES);
+                    tma4(c2, &tm_vz, z0, x0, yn, s, &cbar[k]);
+                    tma4(c2 + CORE, &tm_vx, z0, x0, yn, s, &cbar[k]);
+                    tma4(c2 + 2 * CORE, &tm_vy, z0, x0, yn, s, &cbar[k]);
+                }
+            }
+            if (hr.issued < ylast) hr.issued++;
+            if (cr.issued < yb) cr.issued++;
+        }
+        continue;
+    timeout:
+        if (tid == 0) atomicOr(err, 1u);
+        ring_drain(bar, S, 0, parity, hr, ya);
+        ring_drain(cbar, SC, 16, parity, cr, ya);
+        return;
+    }
+}
+
+// ===========================================================================
+// Pressure kernel.  FWD/ADJ: p -= dt kappa sum_a D_a v_a (+ CPML terms);
+// REC: acc += lp * (div v | p), p += dt kappa div v - source, zero outside the
+// previous box, on the physical domain.
+template <int N, int MODE>
+__global__ void __launch_bounds__(NTHR, 4)
+k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensorMap tm_vx,
+     const __grid_constant__ CUtensorMap tm_vy, const __grid_constant__ CUtensorMap tm_pc,
+     const __grid_constant__ CUtensorMap tm_K, const __grid_constant__ CUtensorMap tm_lp, Grid g, Batch b,
+     Fields f, int step, unsigned *err, float *acc, int img_mode, const float *stf, float src_scale)
+{
+    using Lay = PLay<N>;
+    constexpr int S = Lay::S;
+    constexpr unsigned CBYTES = (MODE == REC ? 3u : 2u) * CORE * 4u;
+    extern __shared__ __align__(128) float sm[];
+    float *cbase = sm + S * Lay::SLOT;
+    __shared__ __align__(8) uint64_t bar[S], cbar[SC];
+    const int tid = threadIdx.x, tzi = tid & 7, txi = tid >> 3;
+    if (tid == 0) {
+        for (int k = 0; k < S; k++) mbar_init(&bar[k], 1);
+        for (int k = 0; k < SC; k++) mbar_init(&cbar[k], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    unsigned parity = 0;
+    const float dt = g.dt;
+
+    Item it;
+    for (long long w = blockIdx.x; get_item(g, b, MODE, step, w, it); w += gridDim.x) {
+        const int s = it.s, z0 = it.z0, x0 = it.x0, ya = it.ya, yb = it.yb;
+        const int ylast = yb + N - 1;
+        const int oz = z0 + 4 * tzi, ox = x0 + txi;
+        const bool mem = oz < g.ne[0] && ox < g.ne[1];
+        const long long sh = (long long)s * g.ntot;
+        bool mz[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) mz[r] = in_range(oz + r, it.lo[0], it.hi[0]);
+        const bool mx = in_range(ox, it.lo[1], it.hi[1]);
+        const int ext = 1;
+        const bool sz = (MODE == FWD) && (z0 < g.nb + ext || z0 + TZ - 1 >= g.ne[0] - g.nb - 1 - ext);
+        const bool sx = (MODE == FWD) && (x0 < g.nb + ext || x0 + TX - 1 >= g.ne[1] - g.nb - 1 - ext);
+        const int own = txi * TZ + 4 * tzi;           // own nodes in a core tile
+
+        // y queue of own vy: entry l = plane y-N+l; planes before ya by plain loads
+        float q[2 * N][4];
+#pragma unroll
+        for (int l = 0; l < N; l++) {
+            const int y = ya - N + l;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (mem && y >= 0 && y < g.ne[2]) v = *reinterpret_cast<const float4 *>(f.v[2] + sh + gidx(g, oz, ox, y));
+            put(q[l], v);
+        }
+        Ring hr{ya, min(ylast, ya + S - 1)}, cr{ya, min(yb, ya + SC - 1)};
+        if (tid == 0) {
+            for (int y = ya; y <= hr.issued; y++) {
+                const int k = (y - ya) % S;
+                float *slot = sm + k * Lay::SLOT;
+                mbar_expect(&bar[k], Lay::BYTES);
+                tma4(slot + Lay::Z_OFF, &tm_vz, z0 - 4, x0, y, s, &bar[k]);
+                tma4(slot + Lay::X_OFF, &tm_vx, z0, x0 - N, y, s, &bar[k]);
+                tma4(slot + Lay::Y_OFF, &tm_vy, z0, x0, y, s, &bar[k]);
+            }
+            for (int y = ya; y <= cr.issued; y++) {
+                const int k = (y - ya) % SC;
+                float *cs = cbase + k * Lay::CSLOT;
+                mbar_expect(&cbar[k], CBYTES);
+                tma4(cs, &tm_pc, z0, x0, y, s, &cbar[k]);
+                tma4(cs + CORE, &tm_K, z0, x0, y, 0, &cbar[k]);
+                if (MODE == REC) tma4(cs + 2 * CORE, &tm_lp, z0, x0, y, s, &cbar[k]);
+            }
+        }
+        bool ok = true;
+#pragma unroll
+        for (int l = 0; l < N - 1; l++) {
+            ok &= ring_wait(bar, S, 0, parity, hr, ya + l, ya);
+            put(q[N + l], lds4(sm + (l % S) * Lay::SLOT + Lay::Y_OFF + own));
+        }
+        if (__syncthreads_or(!ok)) goto timeout;
+
+        for (int y = ya; y <= yb; y++) {
+            ok = ring_wait(bar, S, 0, parity, hr, y + N - 1, ya);
+            ok &= ring_wait(cbar, SC, 16, parity, cr, y, ya);
+            put(q[2 * N - 1], lds4(sm + ((y + N - 1 - ya) % S) * Lay::SLOT + Lay::Y_OFF + own));
+            const float *slot = sm + ((y - ya) % S) * Lay::SLOT;
+            const float *cs = cbase + ((y - ya) % SC) * Lay::CSLOT + own;
+            const bool my = in_range(y, it.lo[2], it.hi[2]);
+            const bool sy = (MODE == FWD) && (y < g.nb + ext || y >= g.ne[2] - g.nb - 1 - ext);
+            const bool act = mem && mx && my;
+            float pv[4], Kv[4];
+            put(pv, lds4(cs));
+            put(Kv, lds4(cs + CORE));
+            float div[4];
+            // ---- z ----
+            {
+                float W[12];
+                {
+                    const float *row = slot + Lay::Z_OFF + txi * ZW + 4 * tzi;
+                    float4 a0 = lds4(row), a1 = lds4(row + 4), a2 = lds4(row + 8);
+                    W[0] = a0.x; W[1] = a0.y; W[2] = a0.z; W[3] = a0.w;
+                    W[4] = a1.x; W[5] = a1.y; W[6] = a1.z; W[7] = a1.w;
+                    W[8] = a2.x; W[9] = a2.y; W[10] = a2.z; W[11] = a2.w;
+                }
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    float d = 0.f;
+#pragma unroll
+                    for (int l = 1; l <= N; l++) d += g.c[0][l - 1] * (W[4 + r + l - 1] - W[4 + r - l]);
+                    div[r] = d;
+                }
+                if (MODE == FWD && sz && act) {
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        const int z = oz + r;
+                        if (!mz[r] || !slab(g, 0, z)) continue;
+                        float *ps = f.psiv[0] + (long long)s * g.slab_n[0] + slab_index(g, 0, z, ox, y);
+                        const float d = div[r];
+                        const float psi = g.cpb[0][z] * *ps + g.cpa[0][z] * d;
+                        *ps = psi;
+                        div[r] = d + psi;
+                    }
+                }
+            }
+            // ---- x ----
+            {
+                float Xr[2 * N][4];
+#pragma unroll
+                for (int l = 1; l <= N; l++) {
+                    put(Xr[N + l - 1], lds4(slot + Lay::X_OFF + (txi + N + l - 1) * TZ + 4 * tzi));
+                    put(Xr[N - l], lds4(slot + Lay::X_OFF + (txi + N - l) * TZ + 4 * tzi));
+                }
+                float D[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    float d = 0.f;
+#pragma unroll
+                    for (int l = 1; l <= N; l++) d += g.c[1][l - 1] * (Xr[N + l - 1][r] - Xr[N - l][r]);
+                    D[r] = d;
+                }
+                if (MODE == FWD && sx && act && slab(g, 1, ox)) {
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        if (!mz[r]) continue;
+                        float *ps = f.psiv[1] + (long long)s * g.slab_n[1] + slab_index(g, 1, oz + r, ox, y);
+                        const float psi = g.cpb[1][ox] * *ps + g.cpa[1][ox] * D[r];
+                        *ps = psi;
+                        D[r] += psi;
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 4; r++) div[r] += D[r];
+            }
+            // ---- y ----
+            {
+                float D[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    float d = 0.f;
+#pragma unroll
+                    for (int l = 1; l <= N; l++) d += g.c[2][l - 1] * (q[N + l - 1][r] - q[N - l][r]);
+                    D[r] = d;
+                }
+                if (MODE == FWD && sy && act && slab(g, 2, y)) {
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        if (!mz[r]) continue;
+                        float *ps = f.psiv[2] + (long long)s * g.slab_n[2] + slab_index(g, 2, oz + r, ox, y);
+                        const float psi = g.cpb[2][y] * *ps + g.cpa[2][y] * D[r];
+                        *ps = psi;
+                        D[r] += psi;
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 4; r++) div[r] += D[r];
+            }
+            if (act) {
+                float np[4];
+                if (MODE == REC) {
+                    const Stencil &st = b.src[s];
+                    const float amp = src_scale * stf[step];
+                    float lpv[4];
+                    put(lpv, lds4(cs + 2 * CORE));
+                    const long long n0 = g.H[0] - g.L[0] + 1, n1 = g.H[1] - g.L[1] + 1;
+                    const bool kxy = in_range(ox, it.plo[1], it.phi[1]) && in_range(y, it.plo[2], it.phi[2]);
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        const int z = oz + r;
+                        np[r] = pv[r];
+                        if (!mz[r]) continue;
+                        const long long kp = (long long)(z - g.L[0]) +
+                                             n0 * ((long long)(ox - g.L[1]) + n1 * (long long)(y - g.L[2]));
+                        acc[(long long)s * g.nphys + kp] += lpv[r] * (img_mode == 0 ? div[r] : pv[r]);
+                        float pn = pv[r] + dt * Kv[r] * div[r];
+                        const int t0 = z - st.first[0], t1 = ox - st.first[1], t2 = y - st.first[2];
+                        if (t0 >= 0 && t0 < st.cnt[0] && t1 >= 0 && t1 < st.cnt[1] && t2 >= 0 && t2 < st.cnt[2])
+                            pn -= amp * st.w[0][t0] * st.w[1][t1] * st.w[2][t2];
+                        np[r] = (kxy && in_range(z, it.plo[0], it.phi[0])) ? pn : 0.f;
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; r++) np[r] = mz[r] ? pv[r] - dt * Kv[r] * div[r] : pv[r];
+                }
+                *reinterpret_cast<float4 *>(f.p + sh + gidx(g, oz, ox, y)) = make_float4(np[0], np[1], np[2], np[3]);
+            }
+#pragma unroll
+            for (int l = 0; l < 2 * N - 1; l++)
+#pragma unroll
+                for (int r = 0; r < 4; r++) q[l][r] = q[l + 1][r];
+            if (__syncthreads_or(!ok)) goto timeout;
+            if (tid == 0) {
+                if (hr.issued < ylast) {
+                    const int yn = hr.issued + 1;
+                    const int k = (yn - ya) % S;
+                    float *sl = sm + k * Lay::SLOT;
+                    mbar_expect(&bar[k], Lay::BYTES);
+                    tma4(sl + Lay::Z_OFF, &tm_vz, z0 - 4, x0, yn, s, &bar[k]);
+                    tma4(sl + Lay::X_OFF, &tm_vx, z0, x0 - N, yn, s, &bar[k]);
+                    tma4(sl + Lay::Y_OFF, &tm_vy, z0, x0, yn, s, &bar[k]);
+                }
+                if (cr.issued < yb) {
+                    const int yn = cr.issued + 1;
+                    const int k = (yn - ya) % SC;
+                    float *c2 = cbase + k * Lay::CSLOT;
+                    mbar_expect(&cbar[k], CBYTES);
+                    tma4(c2, &tm_pc, z0, x0, yn, s, &cbar[k]);
+                    tma4(c2 + CORE, &tm_K, z0, x0, yn, 0, &cbar[k]);
+                    if (MODE == REC) tma4(c2 + 2 * CORE, &tm_lp, z0, x0, yn, s, &cbar[k]);
+                }
+            }
+            if (hr.issued < ylast) hr.issued++;
+            if (cr.issued < yb) cr.issued++;
+        }
+        continue;
+    timeout:
+        if (tid == 0) atomicOr(err, 1u);
+        ring_drain(bar, S, 0, parity, hr, ya);
+        ring_drain(cbar, SC, 16, parity, cr, ya);
+        return;
+    }
+}
+
+}  // namespace s3
+
+
+// ---------------------------------------------------------------------------
+// Host side: tensor maps and launches.
+
+namespace {
+
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encoder()
+{
+    static EncodeFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 4D map (z, x, y, shot) over a padded field array with a box of bz x bx x 1 x 1.
+bool make_map(CUtensorMap *tm, const Grid &g, const float *base, int nshot, int bz, int bx)
+{
+    EncodeFn fn = encoder();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)g.ne[0], (cuuint64_t)g.ne[1], (cuuint64_t)g.ne[2], (cuuint64_t)nshot};
+    cuuint64_t strides[3] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.px * g.ne[1] * 4,
+                             (cuuint64_t)g.px * g.ne[1] * g.ne[2] * 4};
+    cuuint32_t box[4] = {(cuuint32_t)bz, (cuuint32_t)bx, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <class K> int grid_for(K kernel, int smem)
+{
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int per = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, s3::NTHR, smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(1, per) * std::max(1, sms);
+}
+
+template <int N, int MODE>
+void run_v(const LaunchCtx &lc, const Maps3 &m, const Grid &g, const Batch &b, Fields f, int step, unsigned *err)
+{
+    constexpr int smem = s3::VLay<N>::SMEM;
+    static const int grid = grid_for(s3::k3_v<N, MODE>, smem);
+    s3::k3_v<N, MODE><<<grid, s3::NTHR, smem, static_cast<cudaStream_t>(lc.stream)>>>(
+        m.p_halo, m.rho_v, m.vz_core, m.vx_core, m.vy_core, g, b, f, step, err);
+    ++*lc.launches;
+}
+
+template <int N, int MODE>
+void run_p(const LaunchCtx &lc, const Maps3 &m, const Maps3 *lpm, const Grid &g, const Batch &b, Fields f, int step,
+           unsigned *err, float *acc, int img_mode, const float *stf, float src_scale)
+{
+    constexpr int smem = s3::PLay<N>::SMEM;
+    static const int grid = grid_for(s3::k3_p<N, MODE>, smem);
+    s3::k3_p<N, MODE><<<grid, s3::NTHR, smem, static_cast<cudaStream_t>(lc.stream)>>>(
+        m.vz_halo, m.vx_halo, m.vy_core, m.p_core, m.K_core, lpm ? lpm->p_core : m.p_core, g, b, f, step, err, acc,
+        img_mode, stf, src_scale);
+    ++*lc.launches;
+}
+
+}  // namespace
+
+bool stencil3d_supported(const Grid &g) { return g.ndim == 3 && (g.N == 2 || g.N == 4) && encoder() != nullptr; }
+
+bool make_maps3(Maps3 &m, const Grid &g, const Fields &f, int nshot)
+{
+    const int R = s3::TX + 2 * g.N - 1;
+    return make_map(&m.p_halo, g, f.p, nshot, s3::ZW, R) && make_map(&m.p_core, g, f.p, nshot, s3::TZ, s3::TX) &&
+           make_map(&m.vz_core, g, f.v[0], nshot, s3::TZ, s3::TX) &&
+           make_map(&m.vx_core, g, f.v[1], nshot, s3::TZ, s3::TX) &&
+           make_map(&m.vy_core, g, f.v[2], nshot, s3::TZ, s3::TX) &&
+           make_map(&m.vz_halo, g, f.v[0], nshot, s3::ZW, s3::TX) &&
+           make_map(&m.vx_halo, g, f.v[1], nshot, s3::TZ, R) &&
+           make_map(&m.rho_v, g, g.rho, 1, 36, s3::TX + 1) && make_map(&m.K_core, g, g.K, 1, s3::TZ, s3::TX);
+}
+
+void launch3_v(const LaunchCtx &lc, const Maps3 &m, const Grid &g, const Batch &b, Fields f, int step, int mode,
+               unsigned *err)
+{
+    if (g.N == 2) {
+        if (mode == 0) run_v<2, 0>(lc, m, g, b, f, step, err);
+        else if (mode == 1) run_v<2, 1>(lc, m, g, b, f, step, err);
+        else run_v<2, 2>(lc, m, g, b, f, step, err);
+    } else {
+        if (mode == 0) run_v<4, 0>(lc, m, g, b, f, step, err);
+        else if (mode == 1) run_v<4, 1>(lc, m, g, b, f, step, err);
+        else run_v<4, 2>(lc, m, g, b, f, step, err);
+    }
+}
+
+void launch3_p(const LaunchCtx &lc, const Maps3 &m, const Maps3 *lpm, const Grid &g, const Batch &b, Fields f,
+               int step, int mode, unsigned *err, float *acc, int img_mode, const float *stf, float src_scale)
+{
+    if (g.N == 2) {
+        if (mode == 0) run_p<2, 0>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
+        else if (mode == 1) run_p<2, 1>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
+        else run_p<2, 2>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
+    } else {
+        if (mode == 0) run_p<4, 0>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
+        else if (mode == 1) run_p<4, 1>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
+        else run_p<4, 2>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
+    }
+}
+
+}  // namespace smi

@@ -1,0 +1,31 @@
+// smi_stencil3d.h -- TMA-streamed 3D stencil kernels (smi_stencil3d.cu).
+#pragma once
+
+#include <cuda.h>
+
+#include "smi_internal.h"
+
+namespace smi {
+
+// Tensor maps of one batch's fields (haloed plane tiles and 32 x 16 core
+// tiles) and of the model arrays.
+struct Maps3 {
+    CUtensorMap p_halo, p_core, vz_core, vx_core, vy_core, vz_halo, vx_halo, rho_v, K_core;
+};
+
+// True when the 3D kernels can run (3D, order 4 or 8, tensor-map encoder found).
+bool stencil3d_supported(const Grid &g);
+
+// Builds the maps for fields f of a batch of nshot shots; false on failure.
+bool make_maps3(Maps3 &m, const Grid &g, const Fields &f, int nshot);
+
+// mode 0: forward, 1: adjoint (step = reverse steps elapsed), 2: reconstruction.
+// err: device word, bit 0 set if a bounded wait gave up.
+void launch3_v(const LaunchCtx &lc, const Maps3 &m, const Grid &g, const Batch &b, Fields f, int step, int mode,
+               unsigned *err);
+// lpm: maps of the adjoint fields, whose pressure the reconstruction mode
+// correlates with (mode 2 only).
+void launch3_p(const LaunchCtx &lc, const Maps3 &m, const Maps3 *lpm, const Grid &g, const Batch &b, Fields f,
+               int step, int mode, unsigned *err, float *acc, int img_mode, const float *stf, float src_scale);
+
+}  // namespace smi
