@@ -42,6 +42,8 @@ def _stale(src: str, obj: str, newest_header: float) -> bool:
 
 
 def build(verbose: bool = False, extra: list | None = None) -> str:
+    if extra is None and os.environ.get("SMI_NVCC_EXTRA"):
+        extra = os.environ["SMI_NVCC_EXTRA"].split()
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     newest = max([os.path.getmtime(h) for h in _headers()] + [0.0])

@@ -85,6 +85,7 @@ struct Setup {
     // device tables
     Stencil *d_src = nullptr, *d_rec = nullptr;
     int *d_box_src = nullptr, *d_box_rec = nullptr;
+    int *d_tab_src = nullptr, *d_tab_rec = nullptr;   // [nshot][nt+1][6] box tables
     Bands bands{};
 };
 
@@ -275,6 +276,12 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
         cudaMemcpyAsync(S.d_rec, S.rec_st.data(), sizeof(Stencil) * S.nrec_total, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(S.d_box_src, S.box_src.data(), sizeof(int) * 6 * S.nshot, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(S.d_box_rec, S.box_rec.data(), sizeof(int) * 6 * S.nshot, cudaMemcpyHostToDevice, st);
+    // the computing box of every step, evaluated once on the device
+    S.d_tab_src = ar.get<int>((size_t)S.nshot * (S.nt + 1) * 6);
+    S.d_tab_rec = ar.get<int>((size_t)S.nshot * (S.nt + 1) * 6);
+    if (!ar.ok) return fail(SMI_ERR_NOMEM, "device allocation failed");
+    launch_box_fill(lc, g, S.d_box_src, S.nshot, S.nt, S.d_tab_src);
+    launch_box_fill(lc, g, S.d_box_rec, S.nshot, S.nt, S.d_tab_rec);
     double dV = 1.0;
     for (int a = 0; a < m->ndim; a++) dV *= hh[a];
     S.src_scale = w->dt / dV;
@@ -516,6 +523,9 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             b.rec = S.d_rec + S.rec_offset[s0];
             b.rec_off = d_roff;
             b.max_rec = max_rec;
+            b.tab_src = S.d_tab_src + (size_t)s0 * (S.nt + 1) * 6;
+            b.tab_rec = S.d_tab_rec + (size_t)s0 * (S.nt + 1) * 6;
+            b.nt1 = S.nt + 1;
             launch_zero(lc, F.p, sizeof(float) * g.ntot * nb_shot);
             for (int a = 0; a < g.ndim; a++) {
                 launch_zero(lc, F.v[a], sizeof(float) * g.ntot * nb_shot);
@@ -529,7 +539,9 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 tm.begin(0);
                 if (fast3) {
                     launch3_v(lc, mF, g, b, F, it, 0, d_wait);
+                    launch_fwd_corrections(lc, g, b, F, it, true);
                     launch3_p(lc, mF, nullptr, g, b, F, it, 0, d_wait, nullptr, 0, nullptr, 0.0f);
+                    launch_fwd_corrections(lc, g, b, F, it, false);
                 } else {
                     launch_fwd_v(lc, g, b, F, it);
                     launch_fwd_p(lc, g, b, F, it);

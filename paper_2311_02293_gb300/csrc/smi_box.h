@@ -61,4 +61,16 @@ SMI_HD void box_bounds(const Grid &g, const int *ext, int n, int lo[3], int hi[3
     }
 }
 
+// Box of shot s after n steps (n >= -1) from a table filled by box_bounds.
+SMI_HD void box_at(const int *tab, int nt1, int s, int n, int lo[3], int hi[3])
+{
+    const int *e = tab + ((long long)s * nt1 + (n + 1)) * 6;
+    lo[0] = e[0];
+    lo[1] = e[1];
+    lo[2] = e[2];
+    hi[0] = e[3];
+    hi[1] = e[4];
+    hi[2] = e[5];
+}
+
 }  // namespace smi

@@ -53,6 +53,11 @@ struct Batch {
     const Stencil *rec;     // [nrec_total of the batch]
     const int *rec_off;     // [nshot+1] batch-local receiver offsets
     int max_rec;            // largest receiver count of a shot in the batch
+    // Computing-box tables, evaluated once per call on the device:
+    // [nshot][nt+1][6] (lo0,lo1,lo2,hi0,hi1,hi2) after n = -1 .. nt-1 steps.
+    const int *tab_src;     // around the source
+    const int *tab_rec;     // around the receivers
+    int nt1;                // nt + 1
 };
 
 // Wavefields of a batch; shot s of field f is at f + s * ntot, node
@@ -130,6 +135,9 @@ void launch_adj_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, 
 // Transposed CPML terms of the adjoint over the slabs (vel: velocity part,
 // else pressure part), one launch per axis; run before the interior kernels.
 void launch_adj_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, bool vel);
+// Forward CPML memory-variable updates over the slabs (vel: velocity part,
+// else pressure part); added to the interior update of the main kernels.
+void launch_fwd_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, bool vel);
 void launch_recon_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f,
                     const float *lp, float *acc, int mode, const float *stf, int it,
                     float src_scale);
@@ -144,5 +152,7 @@ void set_layout(Grid &g, const int n[3]);
 
 void launch_box_table(const LaunchCtx &lc, const Grid &g, const int *ext, int n0, int count,
                       int *lo, int *hi);
+// Fills tab[nshot][nt+1][6] with the boxes of n = -1 .. nt-1 around ext[nshot][6].
+void launch_box_fill(const LaunchCtx &lc, const Grid &g, const int *ext, int nshot, int nt, int *tab);
 
 }  // namespace smi

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_v(Grid g, Batch b, Fields f, i
 {
     const int s = blockIdx.y;
     int lo[3], hi[3];
-    box_bounds(g, b.box_src + 6 * s, it, lo, hi);
+    box_at(b.tab_src, b.nt1, s, it, lo, hi);
     BoxIter bi;
     bi.set(lo, hi);
     const float *p = f.p + s * g.ntot;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_p(Grid g, Batch b, Fields f, i
 {
     const int s = blockIdx.y;
     int lo[3], hi[3];
-    box_bounds(g, b.box_src + 6 * s, it, lo, hi);
+    box_at(b.tab_src, b.nt1, s, it, lo, hi);
     BoxIter bi;
     bi.set(lo, hi);
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < bi.vol;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_v(Grid g, Batch b, Fields f, i
 {
     const int s = blockIdx.y;
     int lo[3], hi[3];
-    box_bounds(g, b.box_rec + 6 * s, m, lo, hi);
+    box_at(b.tab_rec, b.nt1, s, m, lo, hi);
     BoxIter bi;
     bi.set(lo, hi);
     const float *lp = f.p + s * g.ntot;
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_p(Grid g, Batch b, Fields f, i
 {
     const int s = blockIdx.y;
     int lo[3], hi[3];
-    box_bounds(g, b.box_rec + 6 * s, m, lo, hi);
+    box_at(b.tab_rec, b.nt1, s, m, lo, hi);
     BoxIter bi;
     bi.set(lo, hi);
     float *lp = f.p + s * g.ntot;
@@ -289,154 +289,118 @@ __global__ void __launch_bounds__(kThreads) k_adj_p(Grid g, Batch b, Fields f, i
 //                     after the deferred chi_a <- Bv_a (chi_a + lv_a);
 //   P (lam_p update): lp -= dt kappa D_a[zeta_a], zeta_a = Av_a (lv_a + chi_a),
 //                     after phi_a <- Bp_a (phi_a + lp).
-// Region: the receiver box (m reverse steps) with axis a restricted to
-// [0, nb+N-1] and [ne_a-nb-N-1, ne_a-1].
-struct Band {
-    int lo[3], hi[3];
-    int n0, i1a, nband;   // nodes in the low interval (from lo[a]), start of the high interval, band nodes
-    long long vol;
-};
-
-__device__ __forceinline__ Band band_region(const Grid &g, const int *ext, int m, int a, int N)
+// Region: the receiver box (m reverse steps) within nb+N+1 nodes of either
+// end of axis a.
+// Thread -> node of the axis-AX band: wl = nb + N + 1 nodes at each end of
+// the axis (they cover every node whose stencil reaches that CPML layer),
+// other axes over the grid; nodes outside the receiver box are skipped.
+template <int N, int AX>
+__device__ __forceinline__ bool corr_node(const Grid &g, const Batch &b, const int *tab, int m, int &s, int i[3], int wl)
 {
-    Band r;
-    box_bounds(g, ext, m, r.lo, r.hi);
-    const int wl = g.nb + N;                  // low interval [0, wl-1]
-    const int hs = max(g.ne[a] - g.nb - N - 1, wl);
-    const int a0 = r.lo[a], a1 = min(r.hi[a], wl - 1);
-    r.n0 = max(0, a1 - a0 + 1);
-    r.i1a = max(r.lo[a], hs);
-    const int n1 = max(0, r.hi[a] - r.i1a + 1);
-    r.nband = r.n0 + n1;
-    long long v = r.nband;
-    for (int b = 0; b < 3; b++)
-        if (b != a) v *= max(0, r.hi[b] - r.lo[b] + 1);
-    r.vol = v;
-    return r;
-}
-
-__device__ __forceinline__ void band_node(const Band &r, int a, long long t, int i[3])
-{
-    // the band axis runs fastest only for a = 0; otherwise z stays fastest
-    int w[3];
-    for (int b = 0; b < 3; b++) w[b] = (b == a) ? 0 : r.hi[b] - r.lo[b] + 1;
-    const int nband = r.nband;
+    const int zdim = (AX == 2) ? 2 * wl : g.ne[2];
+    s = blockIdx.z / zdim;
+    const int tz = blockIdx.z - s * zdim;
+    const int tx = blockIdx.x * 32 + threadIdx.x, ty = blockIdx.y * 8 + threadIdx.y;
     int j;
-    if (a == 0) {
-        j = (int)(t % nband);
-        const long long u = t / nband;
-        i[1] = r.lo[1] + (int)(u % w[1]);
-        i[2] = r.lo[2] + (int)(u / w[1]);
-    } else if (a == 1) {
-        i[0] = r.lo[0] + (int)(t % w[0]);
-        const long long u = t / w[0];
-        j = (int)(u % nband);
-        i[2] = r.lo[2] + (int)(u / nband);
-    } else {
-        i[0] = r.lo[0] + (int)(t % w[0]);
-        const long long u = t / w[0];
-        i[1] = r.lo[1] + (int)(u % w[1]);
-        j = (int)(u / w[1]);
-    }
-    i[a] = j < r.n0 ? r.lo[a] + j : r.i1a + (j - r.n0);
+    if (AX == 0) { j = tx; i[1] = ty; i[2] = tz; }
+    else if (AX == 1) { i[0] = tx; j = ty; i[2] = tz; }
+    else { i[0] = tx; i[1] = ty; j = tz; }
+    if (j >= 2 * wl) return false;
+    i[AX] = j < wl ? j : g.ne[AX] - 2 * wl + j;
+    if (i[AX] < 0 || (j >= wl && i[AX] < wl)) return false;     // bands overlap on a short axis
+    int lo[3], hi[3];
+    box_at(tab, b.nt1, s, m, lo, hi);
+    return i[0] >= lo[0] && i[0] <= hi[0] && i[1] >= lo[1] && i[1] <= hi[1] && i[2] >= lo[2] && i[2] <= hi[2];
 }
 
-template <int N>
-__global__ void __launch_bounds__(kThreads) k_adjc_v(Grid g, Batch b, Fields f, int m)
+// js of node j of a CPML slab (slab arrays compress their axis to 2 nb + 1).
+__device__ __forceinline__ int slab_j(const Grid &g, int a, int j) { return j < g.nb ? j : j - (g.ne[a] - 2 * g.nb - 1); }
+
+// Offset and stride of axis AX's slab index at node i with i[AX] replaced.
+template <int AX>
+__device__ __forceinline__ void slab_base(const Grid &g, const int i[3], long long &base, long long &stride)
 {
-    const int s = blockIdx.y, a = blockIdx.z;
-    const Band r = band_region(g, b.box_rec + 6 * s, m, a, N);
-    const long long st = gstride(g, a);
+    if (AX == 0) { base = (long long)g.S * ((long long)i[1] + (long long)g.ne[1] * i[2]); stride = 1; }
+    else if (AX == 1) { base = (long long)i[0] + (long long)g.ne[0] * g.S * i[2]; stride = g.ne[0]; }
+    else { base = (long long)i[0] + (long long)g.ne[0] * i[1]; stride = (long long)g.ne[0] * g.ne[1]; }
+}
+
+template <int N, int AX>
+__global__ void __launch_bounds__(256) k_corr_v(Grid g, Batch b, Fields f, int m)
+{
+    int s, i[3];
+    if (!corr_node<N, AX>(g, b, b.tab_rec, m, s, i, g.nb + N + 1)) return;
+    const long long k = gidx(g, i[0], i[1], i[2]), st = gstride(g, AX);
+    long long sb, ss;
+    slab_base<AX>(g, i, sb, ss);
+    sb += (long long)s * g.slab_n[AX];
     const float *lp = f.p + s * g.ntot;
-    float *lv = f.v[a] + s * g.ntot;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < r.vol;
-         t += (long long)gridDim.x * blockDim.x) {
-        int i[3];
-        band_node(r, a, t, i);
-        const long long k = gidx(g, i[0], i[1], i[2]);
-        const int ia = i[a];
-        if (in_slab(g, a, ia)) {
-            float *ch = f.psip[a] + s * g.slab_n[a] + slab_index(g, a, i[0], i[1], i[2]);
-            *ch = g.cvb[a][ia] * (*ch + lv[k]);
-        }
-        float E = 0.0f;
-#pragma unroll
-        for (int l = 1; l <= N; l++) {
-            float h[2];
-            const int off[2] = {l, 1 - l};
-#pragma unroll
-            for (int e = 0; e < 2; e++) {
-                const int j = ia + off[e];
-                h[e] = 0.0f;
-                if (j >= 0 && j < g.ne[a] && in_slab(g, a, j)) {
-                    const float A = g.cpa[a][j];
-                    if (A != 0.0f) {
-                        int jj[3] = {i[0], i[1], i[2]};
-                        jj[a] = j;
-                        h[e] = A * (lp[k + off[e] * st] + f.psiv[a][s * g.slab_n[a] + slab_index(g, a, jj[0], jj[1], jj[2])]);
-                    }
-                }
-            }
-            E += g.c[a][l - 1] * (h[0] - h[1]);
-        }
-        if (E != 0.0f) lv[k] -= g.dt * buoyancy(g, a, ia, k, g.rho[k]) * E;
+    float *lv = f.v[AX] + s * g.ntot;
+    const int ia = i[AX];
+    if (in_slab(g, AX, ia)) {                  // deferred chi update with lv before this step
+        float *ch = f.psip[AX] + sb + slab_j(g, AX, ia) * ss;
+        *ch = g.cvb[AX][ia] * (*ch + lv[k]);
     }
+    float E = 0.0f;
+#pragma unroll
+    for (int l = 1; l <= N; l++) {
+        float h[2];
+        const int off[2] = {l, 1 - l};
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const int j = ia + off[e];
+            h[e] = 0.0f;
+            if (j >= 0 && j < g.ne[AX] && in_slab(g, AX, j)) {
+                const float A = __ldg(g.cpa[AX] + j);
+                if (A != 0.0f) h[e] = A * (lp[k + off[e] * st] + f.psiv[AX][sb + slab_j(g, AX, j) * ss]);
+            }
+        }
+        E += g.c[AX][l - 1] * (h[0] - h[1]);
+    }
+    if (E != 0.0f) lv[k] -= g.dt * buoyancy(g, AX, ia, k, g.rho[k]) * E;
 }
 
-// phi_a <- Bp_a (phi_a + lp) over the p-grid slab of every axis (blockIdx.z),
-// with lp before any of this step's pressure corrections.
-template <int N>
-__global__ void __launch_bounds__(kThreads) k_adjc_phi(Grid g, Batch b, Fields f, int m)
+template <int N, int AX>
+__global__ void __launch_bounds__(256) k_corr_phi(Grid g, Batch b, Fields f, int m)
 {
-    const int s = blockIdx.y, a = blockIdx.z;
-    const Band r = band_region(g, b.box_rec + 6 * s, m, a, N);
-    const float *lp = f.p + s * g.ntot;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < r.vol;
-         t += (long long)gridDim.x * blockDim.x) {
-        int i[3];
-        band_node(r, a, t, i);
-        if (!in_slab(g, a, i[a])) continue;
-        float *ph = f.psiv[a] + s * g.slab_n[a] + slab_index(g, a, i[0], i[1], i[2]);
-        *ph = g.cpb[a][i[a]] * (*ph + lp[gidx(g, i[0], i[1], i[2])]);
-    }
+    int s, i[3];
+    if (!corr_node<N, AX>(g, b, b.tab_rec, m, s, i, g.nb + N + 1)) return;
+    const int ia = i[AX];
+    if (!in_slab(g, AX, ia)) return;
+    long long sb, ss;
+    slab_base<AX>(g, i, sb, ss);
+    float *ph = f.psiv[AX] + (long long)s * g.slab_n[AX] + sb + slab_j(g, AX, ia) * ss;
+    *ph = g.cpb[AX][ia] * (*ph + f.p[s * g.ntot + gidx(g, i[0], i[1], i[2])]);
 }
 
-template <int N>
-__global__ void __launch_bounds__(kThreads) k_adjc_p(Grid g, Batch b, Fields f, int m, int a)
+template <int N, int AX>
+__global__ void __launch_bounds__(256) k_corr_p(Grid g, Batch b, Fields f, int m)
 {
-    const int s = blockIdx.y;
-    const Band r = band_region(g, b.box_rec + 6 * s, m, a, N);
-    const long long st = gstride(g, a);
-    float *lp = f.p + s * g.ntot;
-    const float *lv = f.v[a] + s * g.ntot;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < r.vol;
-         t += (long long)gridDim.x * blockDim.x) {
-        int i[3];
-        band_node(r, a, t, i);
-        const long long k = gidx(g, i[0], i[1], i[2]);
-        const int ia = i[a];
-        float F = 0.0f;
+    int s, i[3];
+    if (!corr_node<N, AX>(g, b, b.tab_rec, m, s, i, g.nb + N + 1)) return;
+    const long long k = gidx(g, i[0], i[1], i[2]), st = gstride(g, AX);
+    long long sb, ss;
+    slab_base<AX>(g, i, sb, ss);
+    sb += (long long)s * g.slab_n[AX];
+    const float *lv = f.v[AX] + s * g.ntot;
+    const int ia = i[AX];
+    float F = 0.0f;
 #pragma unroll
-        for (int l = 1; l <= N; l++) {
-            float h[2];
-            const int off[2] = {l - 1, -l};
+    for (int l = 1; l <= N; l++) {
+        float h[2];
+        const int off[2] = {l - 1, -l};
 #pragma unroll
-            for (int e = 0; e < 2; e++) {
-                const int j = ia + off[e];
-                h[e] = 0.0f;
-                if (j >= 0 && j < g.ne[a] && in_slab(g, a, j)) {
-                    const float A = g.cva[a][j];
-                    if (A != 0.0f) {
-                        int jj[3] = {i[0], i[1], i[2]};
-                        jj[a] = j;
-                        h[e] = A * (lv[k + off[e] * st] + f.psip[a][s * g.slab_n[a] + slab_index(g, a, jj[0], jj[1], jj[2])]);
-                    }
-                }
+        for (int e = 0; e < 2; e++) {
+            const int j = ia + off[e];
+            h[e] = 0.0f;
+            if (j >= 0 && j < g.ne[AX] && in_slab(g, AX, j)) {
+                const float A = __ldg(g.cva[AX] + j);
+                if (A != 0.0f) h[e] = A * (lv[k + off[e] * st] + f.psip[AX][sb + slab_j(g, AX, j) * ss]);
             }
-            F += g.c[a][l - 1] * (h[0] - h[1]);
         }
-        if (F != 0.0f) lp[k] -= g.dt * g.K[k] * F;
+        F += g.c[AX][l - 1] * (h[0] - h[1]);
     }
+    if (F != 0.0f) f.p[s * g.ntot + k] -= g.dt * g.K[k] * F;
 }
 
 // ---------------------------------------------------------------------------
@@ -455,8 +419,8 @@ k_recon_p(Grid g, Batch b, Fields f, const float *lpall, float *acc, int mode, c
 {
     const int s = blockIdx.y;
     int lo[3], hi[3], plo[3], phi[3];
-    box_bounds(g, b.box_src + 6 * s, it, lo, hi);
-    box_bounds(g, b.box_src + 6 * s, it - 1, plo, phi);
+    box_at(b.tab_src, b.nt1, s, it, lo, hi);
+    box_at(b.tab_src, b.nt1, s, it - 1, plo, phi);
     for (int a = 0; a < 3; a++) {
         lo[a] = max(lo[a], g.L[a]);
         hi[a] = min(hi[a], g.H[a]);
@@ -509,8 +473,8 @@ __global__ void __launch_bounds__(kThreads) k_recon_v(Grid g, Batch b, Fields f,
 {
     const int s = blockIdx.y;
     int lo[3], hi[3], plo[3], phi[3];
-    box_bounds(g, b.box_src + 6 * s, it, lo, hi);
-    box_bounds(g, b.box_src + 6 * s, it - 1, plo, phi);
+    box_at(b.tab_src, b.nt1, s, it, lo, hi);
+    box_at(b.tab_src, b.nt1, s, it - 1, plo, phi);
     for (int a = 0; a < 3; a++) {
         lo[a] = max(lo[a], g.L[a]);
         hi[a] = min(hi[a], g.H[a]);
@@ -778,6 +742,19 @@ __global__ void k_minmax_out(const unsigned *tmp, float *out2)
     out2[1] = __uint_as_float(tmp[1]);
 }
 
+__global__ void k_box_fill(Grid g, const int *ext, int nshot, int nt, int *tab)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nshot * (nt + 1)) return;
+    const int s = (int)(t / (nt + 1)), n = (int)(t % (nt + 1)) - 1;
+    int lo[3], hi[3];
+    box_bounds(g, ext + 6 * s, n, lo, hi);
+    for (int a = 0; a < 3; a++) {
+        tab[t * 6 + a] = lo[a];
+        tab[t * 6 + 3 + a] = hi[a];
+    }
+}
+
 __global__ void k_box_table(Grid g, const int *ext, int n0, int count, int *lo, int *hi)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -843,28 +820,107 @@ void launch_recon_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f
     SMI_DISPATCH(k_recon_v, grid, g, b, f, it);
 }
 
+// Forward CPML over the slabs only (Sec. 2.1, Komatitsch & Martin CPML),
+// added to the interior update that the main kernels apply everywhere:
+//   V: psi_a <- Bv_a psi_a + Av_a D_a p;  v_a -= dt b_a psi_a
+//   P: psi_a <- Bp_a psi_a + Ap_a D_a v_a; p -= dt kappa psi_a
+// over the forward box (step it); nodes outside the axis-AX slab skip.
+template <int N, int AX>
+__global__ void __launch_bounds__(256) k_fcorr_v(Grid g, Batch b, Fields f, int it)
+{
+    int s, i[3];
+    if (!corr_node<N, AX>(g, b, b.tab_src, it, s, i, g.nb + 1)) return;
+    const int ia = i[AX];
+    if (!in_slab(g, AX, ia)) return;
+    const long long k = gidx(g, i[0], i[1], i[2]), st = gstride(g, AX);
+    const float *p = f.p + s * g.ntot;
+    float D = 0.0f;
+#pragma unroll
+    for (int l = 1; l <= N; l++) {
+        const float pp = (ia + l < g.ne[AX]) ? p[k + l * st] : 0.0f;
+        const float pm = (ia - l + 1 >= 0) ? p[k - (l - 1) * st] : 0.0f;
+        D += g.c[AX][l - 1] * (pp - pm);
+    }
+    long long sb, ss;
+    slab_base<AX>(g, i, sb, ss);
+    float *ps = f.psip[AX] + (long long)s * g.slab_n[AX] + sb + slab_j(g, AX, ia) * ss;
+    const float psi = g.cvb[AX][ia] * *ps + g.cva[AX][ia] * D;
+    *ps = psi;
+    f.v[AX][s * g.ntot + k] -= g.dt * buoyancy(g, AX, ia, k, g.rho[k]) * psi;
+}
+
+template <int N, int AX>
+__global__ void __launch_bounds__(256) k_fcorr_p(Grid g, Batch b, Fields f, int it)
+{
+    int s, i[3];
+    if (!corr_node<N, AX>(g, b, b.tab_src, it, s, i, g.nb + 1)) return;
+    const int ia = i[AX];
+    if (!in_slab(g, AX, ia)) return;
+    const long long k = gidx(g, i[0], i[1], i[2]), st = gstride(g, AX);
+    const float *v = f.v[AX] + s * g.ntot;
+    float D = 0.0f;
+#pragma unroll
+    for (int l = 1; l <= N; l++) {
+        const float vp = (ia + l - 1 < g.ne[AX]) ? v[k + (l - 1) * st] : 0.0f;
+        const float vm = (ia - l >= 0) ? v[k - l * st] : 0.0f;
+        D += g.c[AX][l - 1] * (vp - vm);
+    }
+    long long sb, ss;
+    slab_base<AX>(g, i, sb, ss);
+    float *ps = f.psiv[AX] + (long long)s * g.slab_n[AX] + sb + slab_j(g, AX, ia) * ss;
+    const float psi = g.cpb[AX][ia] * *ps + g.cpa[AX][ia] * D;
+    *ps = psi;
+    f.p[s * g.ntot + k] -= g.dt * g.K[k] * psi;
+}
+
+template <int N, int AX>
+void corr_launch(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, int which)
+{
+    const int wl = which >= 3 ? g.nb + 1 : g.nb + N + 1;
+    dim3 grid(AX == 0 ? (2 * wl + 31) / 32 : (g.ne[0] + 31) / 32, AX == 1 ? (2 * wl + 7) / 8 : (g.ne[1] + 7) / 8,
+              (AX == 2 ? 2 * wl : g.ne[2]) * b.nshot);
+    dim3 block(32, 8);
+    if (which == 0) k_corr_v<N, AX><<<grid, block, 0, S(lc)>>>(g, b, f, m);
+    else if (which == 1) k_corr_phi<N, AX><<<grid, block, 0, S(lc)>>>(g, b, f, m);
+    else if (which == 2) k_corr_p<N, AX><<<grid, block, 0, S(lc)>>>(g, b, f, m);
+    else if (which == 3) k_fcorr_v<N, AX><<<grid, block, 0, S(lc)>>>(g, b, f, m);
+    else k_fcorr_p<N, AX><<<grid, block, 0, S(lc)>>>(g, b, f, m);
+    ++*lc.launches;
+}
+
+template <int N>
+void corr_axes(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, int which)
+{
+    corr_launch<N, 0>(lc, g, b, f, m, which);
+    corr_launch<N, 1>(lc, g, b, f, m, which);
+    if (g.ndim == 3) corr_launch<N, 2>(lc, g, b, f, m, which);
+}
+
 void launch_adj_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, bool vel)
 {
-    // a band holds at most 2 (nb + N + 1) nodes along its axis
-    long long vol = 0;
-    for (int a = 0; a < g.ndim; a++) vol = std::max(vol, g.ntot / g.ne[a] * (2LL * (g.nb + g.N + 1)));
+    // velocity part: the axes touch disjoint arrays.  Pressure part: every
+    // phi update reads lp before any axis changes it, then one launch per
+    // axis (each updates lp).
     if (vel) {
-        dim3 grid(blocks_for(vol), b.nshot, g.ndim);     // axes touch disjoint arrays
-        if (g.N == 2) k_adjc_v<2><<<grid, kThreads, 0, S(lc)>>>(g, b, f, m);
-        else k_adjc_v<4><<<grid, kThreads, 0, S(lc)>>>(g, b, f, m);
-        ++*lc.launches;
+        if (g.N == 2) corr_axes<2>(lc, g, b, f, m, 0);
+        else corr_axes<4>(lc, g, b, f, m, 0);
         return;
     }
-    dim3 gphi(blocks_for(vol), b.nshot, g.ndim);
-    if (g.N == 2) k_adjc_phi<2><<<gphi, kThreads, 0, S(lc)>>>(g, b, f, m);
-    else k_adjc_phi<4><<<gphi, kThreads, 0, S(lc)>>>(g, b, f, m);
-    ++*lc.launches;
-    for (int a = 0; a < g.ndim; a++) {          // all axes update lp: one launch each
-        dim3 grid(blocks_for(vol), b.nshot);
-        if (g.N == 2) k_adjc_p<2><<<grid, kThreads, 0, S(lc)>>>(g, b, f, m, a);
-        else k_adjc_p<4><<<grid, kThreads, 0, S(lc)>>>(g, b, f, m, a);
-        ++*lc.launches;
+    if (g.N == 2) {
+        corr_axes<2>(lc, g, b, f, m, 1);
+        corr_axes<2>(lc, g, b, f, m, 2);
+    } else {
+        corr_axes<4>(lc, g, b, f, m, 1);
+        corr_axes<4>(lc, g, b, f, m, 2);
     }
+}
+
+void launch_fwd_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, bool vel)
+{
+    // velocity: axes touch disjoint arrays; pressure: one launch per axis,
+    // each updating p in the slab of its axis
+    if (g.N == 2) corr_axes<2>(lc, g, b, f, it, vel ? 3 : 4);
+    else corr_axes<4>(lc, g, b, f, it, vel ? 3 : 4);
 }
 
 void launch_inject_source(const LaunchCtx &lc, const Grid &g, const Batch &b, float *p,
@@ -962,6 +1018,13 @@ void launch_minmax(const LaunchCtx &lc, const float *vp, long long n, float *out
 void launch_zero(const LaunchCtx &lc, void *ptr, size_t bytes)
 {
     cudaMemsetAsync(ptr, 0, bytes, S(lc));
+}
+
+void launch_box_fill(const LaunchCtx &lc, const Grid &g, const int *ext, int nshot, int nt, int *tab)
+{
+    const long long n = (long long)nshot * (nt + 1);
+    k_box_fill<<<(unsigned)((n + 127) / 128), 128, 0, S(lc)>>>(g, ext, nshot, nt, tab);
+    ++*lc.launches;
 }
 
 void launch_box_table(const LaunchCtx &lc, const Grid &g, const int *ext, int n0, int count, int *lo,

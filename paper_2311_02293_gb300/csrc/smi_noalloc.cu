@@ -96,11 +96,12 @@ struct Plan {
     float *K, *rho;
     Stencil *src, *rec;
     int *box_src, *box_rec, *rec_off;
+    int *tab;                 // [nt+1][6] source box of every step
     long long *seis_off;
     float *p, *v[3], *psip[3], *psiv[3];
 };
 
-void lay_out(Carve &c, Plan &pl, const Grid &g, int max_rec)
+void lay_out(Carve &c, Plan &pl, const Grid &g, int max_rec, int nt)
 {
     pl.mm_tmp = c.take<unsigned>(4);
     pl.mm = c.take<float>(4);
@@ -113,6 +114,7 @@ void lay_out(Carve &c, Plan &pl, const Grid &g, int max_rec)
     pl.box_src = c.take<int>(6);
     pl.box_rec = c.take<int>(6);
     pl.rec_off = c.take<int>(2);
+    pl.tab = c.take<int>(6 * ((size_t)nt + 1));
     pl.seis_off = c.take<long long>(1);
     pl.p = c.take<float>((size_t)g.ntot);
     for (int a = 0; a < 3; a++) {
@@ -197,7 +199,7 @@ int forward_noalloc(const smi_model *m, const smi_geometry *geo, const smi_wavel
     // size check before touching the device
     Carve count;
     Plan pl{};
-    lay_out(count, pl, g, max_rec);
+    lay_out(count, pl, g, max_rec, w->nt);
     if (count.off > kScratchBytes)
         return err(SMI_ERR_ARG,
                    "problem needs %zu bytes of working memory; smi_forward_noalloc holds at most %zu "
@@ -211,7 +213,7 @@ int forward_noalloc(const smi_model *m, const smi_geometry *geo, const smi_wavel
     if (rc) return rc;
     Carve c;
     c.base = static_cast<unsigned char *>(base);
-    lay_out(c, pl, g, max_rec);
+    lay_out(c, pl, g, max_rec, w->nt);
 
     cudaStream_t st = static_cast<cudaStream_t>(o->stream);
     long long launches = 0;
@@ -312,6 +314,10 @@ int forward_noalloc(const smi_model *m, const smi_geometry *geo, const smi_wavel
         b.rec = pl.rec;
         b.rec_off = pl.rec_off;
         b.max_rec = nr;
+        launch_box_fill(lc, g, pl.box_src, 1, w->nt, pl.tab);
+        b.tab_src = pl.tab;
+        b.tab_rec = pl.tab;
+        b.nt1 = w->nt + 1;
         Fields F{};
         F.p = pl.p;
         for (int a = 0; a < 3; a++) {

@@ -2,11 +2,11 @@
 //
 // Two kernels advance one half of a leap-frog step each (Sec. 2.1 update
 // equations): k3_v updates the three velocity components from p, k3_p
-// updates p from the velocities.  Each comes in three modes:
-//   FWD  forward modelling, CPML memory variables in the slabs;
-//   ADJ  the interior part of the exact discrete adjoint in "same solver"
-//        form (the forward scheme itself); the transposed CPML terms are
-//        added beforehand by slab-only correction kernels (smi_kernels.cu);
+// updates p from the velocities.  They run in two modes:
+//   FWD  the branch-free interior update, applied to every node of the box
+//        for both the forward scheme and the adjoint in "same solver" form;
+//        the CPML terms (forward, and transposed for the adjoint) are added
+//        by slab-only correction kernels (smi_kernels.cu);
 //   REC  source-field reconstruction backwards in time (Sec. 4.2) on the
 //        physical domain, with the imaging / gradient accumulation fused
 //        into the pressure kernel.
@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "smi_box.h"
 #include "smi_internal.h"
@@ -35,7 +36,22 @@
 namespace smi {
 namespace s3 {
 
-constexpr int TZ = 32, TX = 16, NTHR = 128;
+#ifndef SMI_TX
+#define SMI_TX 16
+#endif
+#ifndef SMI_PFP
+#define SMI_PFP 1
+#endif
+#ifndef SMI_MINB
+#define SMI_MINB 4
+#endif
+#ifndef SMI_WAVES
+#define SMI_WAVES 1
+#endif
+#ifdef SMI_TIMING
+#include <cstdio>
+#endif
+constexpr int TZ = 32, TX = SMI_TX, NTHR = 8 * TX;
 constexpr int ZW = 40;                 // z extent of haloed tiles: [z0-4, z0+36)
 constexpr long long kSpin = 1LL << 22; // bounded mbarrier polls
 
@@ -47,7 +63,7 @@ __host__ __device__ constexpr int rup32(int n) { return (n + 31) / 32 * 32; }
 // Haloed ring: slots resident while their plane feeds a derivative (N+1
 // planes for the velocity kernel, N for the pressure kernel) plus PFP planes
 // of lead.  Core ring: the pointwise 32 x 16 tiles of one plane, SC slots.
-constexpr int PFP = 1, SC = 3, CORE = TZ * TX;
+constexpr int PFP = SMI_PFP, SC = 3, CORE = TZ * TX;
 
 template <int N> struct VLay {
     static constexpr int PR = TX + 2 * N - 1;            // p tile rows: x0-N+1 .. x0+TX-1+N
@@ -140,12 +156,12 @@ __device__ __forceinline__ void item_box(const Grid &g, const Batch &b, int mode
                                          int hi[3], int plo[3], int phi[3])
 {
     if (mode == ADJ) {
-        box_bounds(g, b.box_rec + 6 * s, step, lo, hi);
+        box_at(b.tab_rec, b.nt1, s, step, lo, hi);
     } else {
-        box_bounds(g, b.box_src + 6 * s, step, lo, hi);
+        box_at(b.tab_src, b.nt1, s, step, lo, hi);
     }
     if (mode == REC) {
-        box_bounds(g, b.box_src + 6 * s, step - 1, plo, phi);
+        box_at(b.tab_src, b.nt1, s, step - 1, plo, phi);
         for (int a = 0; a < 3; a++) {
             lo[a] = max(lo[a], g.L[a]);
             hi[a] = min(hi[a], g.H[a]);
@@ -173,21 +189,11 @@ __device__ __forceinline__ Decomp decomp(const int lo[3], const int hi[3], int g
         return d;
     }
     const int cols = d.nzt * d.nxt;
-    float best = 1e30f;
-    int best_cy = ylen;
-    const int maxc = max(1, min(ylen / 8, 64));
-    for (int c = 1; c <= maxc; c++) {
-        const int cy = (ylen + c - 1) / c;
-        const int nyc = (ylen + cy - 1) / cy;
-        const long long items = (long long)cols * nyc;
-        const long long waves = (items + grid - 1) / grid;
-        // time ~ waves x (cy + pipeline start-up)
-        const float t = (float)waves * (float)(cy + 10);
-        if (t < best) {
-            best = t;
-            best_cy = cy;
-        }
-    }
+    // Long chunks: each chunk pays a pipeline start-up of about 2N planes.
+    // Split columns only as far as the persistent grid holds SMI_WAVES
+    // waves of items, so that no wave runs nearly empty.
+    const int chunks = max(1, min(ylen / 16, (int)((long long)SMI_WAVES * grid / cols)));
+    const int best_cy = (ylen + chunks - 1) / chunks;
     d.cy = best_cy;
     d.nyc = (ylen + best_cy - 1) / best_cy;
     return d;
@@ -256,13 +262,34 @@ __device__ __forceinline__ void ring_drain(uint64_t *bars, int nslots, int bitba
     }
 }
 
-__device__ __forceinline__ float buoy(float r0, float r1, bool last) { return last ? 1.0f / r0 : 2.0f / (r0 + r1); }
+// Buoyancy on a half node: 2 / (rho_i + rho_{i+1}), 1/rho at the last node
+// (fast reciprocal-based division: a few ulp, far below the FP32 scheme error).
+// y-loop unrolled by the queue length M = 2N: step K of a group sees logical
+// queue entry l at physical index (l + K) % M, so the queue rotates by
+// renaming registers instead of moving them.
+template <int K, int M> struct Unroll {
+    template <class F> __device__ __forceinline__ static void run(F &f, int &y, int yb, const bool &stop)
+    {
+        if (y > yb || stop) return;
+        f(std::integral_constant<int, K>{});
+        ++y;
+        Unroll<K + 1, M>::run(f, y, yb, stop);
+    }
+};
+template <int M> struct Unroll<M, M> {
+    template <class F> __device__ __forceinline__ static void run(F &, int &, int, const bool &) {}
+};
+
+__device__ __forceinline__ float buoy(float r0, float r1, bool last)
+{
+    return last ? __fdividef(1.0f, r0) : __fdividef(2.0f, r0 + r1);
+}
 
 // ===========================================================================
 // Velocity kernel.  FWD/ADJ: v_a -= dt b_a D_a p (+ CPML terms); REC:
 // v_a += dt b_a D_a p on L_a+N-1..H_a-N, zero outside the previous box.
 template <int N, int MODE>
-__global__ void __launch_bounds__(NTHR, 4)
+__global__ void __launch_bounds__(NTHR, SMI_MINB)
 k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_rho,
      const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensorMap tm_vx,
      const __grid_constant__ CUtensorMap tm_vy, Grid g, Batch b, Fields f, int step, unsigned *err)
@@ -281,6 +308,9 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
     __syncthreads();
     unsigned parity = 0;
     const float dt = g.dt;
+#ifdef SMI_TIMING
+    long long t_wait = 0, t_sync = 0, t_all = clock64(), n_planes = 0;
+#endif
 
     Item it;
     for (long long w = blockIdx.x; get_item(g, b, MODE, step, w, it); w += gridDim.x) {
@@ -293,12 +323,6 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
 #pragma unroll
         for (int r = 0; r < 4; r++) mz[r] = in_range(oz + r, it.lo[0], it.hi[0]);
         const bool mx = in_range(ox, it.lo[1], it.hi[1]);
-        // CPML memory variables (FWD only; block uniform): the tile meets a slab.
-        // The adjoint's transposed CPML terms are applied by the slab
-        // correction kernels before this one runs.
-        const int ext = 1;
-        const bool sz = (MODE == FWD) && (z0 < g.nb + ext || z0 + TZ - 1 >= g.ne[0] - g.nb - 1 - ext);
-        const bool sx = (MODE == FWD) && (x0 < g.nb + ext || x0 + TX - 1 >= g.ne[1] - g.nb - 1 - ext);
         const int own = (txi + N - 1) * ZW + 4 * tzi + 4;   // own nodes in a p tile
 
         // y queue of own p: entry l = plane y-N+1+l; planes before ya by plain loads
@@ -336,16 +360,25 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
         }
         if (__syncthreads_or(!ok)) goto timeout;
 
-        for (int y = ya; y <= yb; y++) {
+        {
+        bool stop = false;
+        int y = ya;
+        auto body = [&](auto kc) {
+            constexpr int kq = decltype(kc)::value;
+#ifdef SMI_TIMING
+            const long long tw0 = clock64();
+#endif
             ok = ring_wait(bar, S, 0, parity, hr, y + N, ya);
             ok &= ring_wait(cbar, SC, 16, parity, cr, y, ya);
+#ifdef SMI_TIMING
+            t_wait += clock64() - tw0;
+#endif
             const float *pt = sm + ((y - ya) % S) * Lay::SLOT;
             const float *rt = pt + Lay::R_OFF;
             const float *rt1 = sm + ((y + 1 - ya) % S) * Lay::SLOT + Lay::R_OFF;
-            put(q[2 * N - 1], lds4(sm + ((y + N - ya) % S) * Lay::SLOT + Lay::P_OFF + own));
+            put(q[((2 * N - 1) + kq) % (2 * N)], lds4(sm + ((y + N - ya) % S) * Lay::SLOT + Lay::P_OFF + own));
             const float *cs = cbase + ((y - ya) % SC) * Lay::CSLOT + txi * TZ + 4 * tzi;
             const bool my = in_range(y, it.lo[2], it.hi[2]);
-            const bool sy = (MODE == FWD) && (y < g.nb + ext || y >= g.ne[2] - g.nb - 1 - ext);
             bool keep[4];
             if (MODE == REC) {
                 const bool kxy = in_range(ox, it.plo[1], it.phi[1]) && in_range(y, it.plo[2], it.phi[2]);
@@ -379,17 +412,6 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
                     for (int l = 1; l <= N; l++) d += g.c[0][l - 1] * (W[4 + r + l] - W[4 + r - l + 1]);
                     D[r] = d;
                 }
-                if (MODE == FWD && sz && act) {
-#pragma unroll
-                    for (int r = 0; r < 4; r++) {
-                        const int z = oz + r;
-                        if (!mz[r] || !slab(g, 0, z)) continue;
-                        float *ps = f.psip[0] + (long long)s * g.slab_n[0] + slab_index(g, 0, z, ox, y);
-                        const float psi = g.cvb[0][z] * *ps + g.cva[0][z] * D[r];
-                        *ps = psi;
-                        D[r] += psi;
-                    }
-                }
                 float nv[4];
 #pragma unroll
                 for (int r = 0; r < 4; r++) {
@@ -422,16 +444,6 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
                     for (int l = 1; l <= N; l++) d += g.c[1][l - 1] * (Xr[N - 1 + l][r] - Xr[N - l][r]);
                     D[r] = d;
                 }
-                if (MODE == FWD && sx && act && slab(g, 1, ox)) {
-#pragma unroll
-                    for (int r = 0; r < 4; r++) {
-                        if (!mz[r]) continue;
-                        float *ps = f.psip[1] + (long long)s * g.slab_n[1] + slab_index(g, 1, oz + r, ox, y);
-                        const float psi = g.cvb[1][ox] * *ps + g.cva[1][ox] * D[r];
-                        *ps = psi;
-                        D[r] += psi;
-                    }
-                }
                 const bool lastx = ox + 1 >= g.ne[1];
                 const bool rxm = MODE == REC && in_range(ox, g.L[1] + N - 1, g.H[1] - N);
                 float nv[4];
@@ -453,18 +465,8 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
                 for (int r = 0; r < 4; r++) {
                     float d = 0.f;
 #pragma unroll
-                    for (int l = 1; l <= N; l++) d += g.c[2][l - 1] * (q[N - 1 + l][r] - q[N - l][r]);
+                    for (int l = 1; l <= N; l++) d += g.c[2][l - 1] * (q[((N - 1 + l) + kq) % (2 * N)][r] - q[((N - l) + kq) % (2 * N)][r]);
                     D[r] = d;
-                }
-                if (MODE == FWD && sy && act && slab(g, 2, y)) {
-#pragma unroll
-                    for (int r = 0; r < 4; r++) {
-                        if (!mz[r]) continue;
-                        float *ps = f.psip[2] + (long long)s * g.slab_n[2] + slab_index(g, 2, oz + r, ox, y);
-                        const float psi = g.cvb[2][y] * *ps + g.cva[2][y] * D[r];
-                        *ps = psi;
-                        D[r] += psi;
-                    }
                 }
                 const bool lasty = y + 1 >= g.ne[2];
                 const bool rym = MODE == REC && in_range(y, g.L[2] + N - 1, g.H[2] - N);
@@ -483,12 +485,18 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
                 *reinterpret_cast<float4 *>(f.v[1] + base) = nxv;
                 *reinterpret_cast<float4 *>(f.v[2] + base) = nyv;
             }
-#pragma unroll
-            for (int l = 0; l < 2 * N - 1; l++)
-#pragma unroll
-                for (int r = 0; r < 4; r++) q[l][r] = q[l + 1][r];
             // all reads of plane y's slots are done; refill them
-            if (__syncthreads_or(!ok)) goto timeout;
+#ifdef SMI_TIMING
+            const long long ts0 = clock64();
+            n_planes++;
+#endif
+            if (__syncthreads_or(!ok)) {
+                stop = true;
+                return;
+            }
+#ifdef SMI_TIMING
+            t_sync += clock64() - ts0;
+#endif
             if (tid == 0) {
                 if (hr.issued < ylast) {
                     const int yn = hr.issued + 1;
@@ -510,6 +518,9 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
             }
             if (hr.issued < ylast) hr.issued++;
             if (cr.issued < yb) cr.issued++;
+        };
+        while (y <= yb && !stop) Unroll<0, 2 * N>::run(body, y, yb, stop);
+        if (stop) goto timeout;
         }
         continue;
     timeout:
@@ -518,6 +529,11 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
         ring_drain(cbar, SC, 16, parity, cr, ya);
         return;
     }
+#ifdef SMI_TIMING
+    if (threadIdx.x == 0 && (blockIdx.x % 97) == 0 && n_planes > 0)
+        printf("T%d blk %d planes %lld all %lld wait %lld (%.0f%%) sync %lld (%.0f%%)\n", MODE, blockIdx.x, n_planes,
+               clock64() - t_all, t_wait, 100.0 * t_wait / (clock64() - t_all), t_sync, 100.0 * t_sync / (clock64() - t_all));
+#endif
 }
 
 // ===========================================================================
@@ -525,7 +541,7 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
 // REC: acc += lp * (div v | p), p += dt kappa div v - source, zero outside the
 // previous box, on the physical domain.
 template <int N, int MODE>
-__global__ void __launch_bounds__(NTHR, 4)
+__global__ void __launch_bounds__(NTHR, SMI_MINB)
 k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensorMap tm_vx,
      const __grid_constant__ CUtensorMap tm_vy, const __grid_constant__ CUtensorMap tm_pc,
      const __grid_constant__ CUtensorMap tm_K, const __grid_constant__ CUtensorMap tm_lp, Grid g, Batch b,
@@ -546,6 +562,9 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
     __syncthreads();
     unsigned parity = 0;
     const float dt = g.dt;
+#ifdef SMI_TIMING
+    long long t_wait = 0, t_sync = 0, t_all = clock64(), n_planes = 0;
+#endif
 
     Item it;
     for (long long w = blockIdx.x; get_item(g, b, MODE, step, w, it); w += gridDim.x) {
@@ -558,9 +577,6 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
 #pragma unroll
         for (int r = 0; r < 4; r++) mz[r] = in_range(oz + r, it.lo[0], it.hi[0]);
         const bool mx = in_range(ox, it.lo[1], it.hi[1]);
-        const int ext = 1;
-        const bool sz = (MODE == FWD) && (z0 < g.nb + ext || z0 + TZ - 1 >= g.ne[0] - g.nb - 1 - ext);
-        const bool sx = (MODE == FWD) && (x0 < g.nb + ext || x0 + TX - 1 >= g.ne[1] - g.nb - 1 - ext);
         const int own = txi * TZ + 4 * tzi;           // own nodes in a core tile
 
         // y queue of own vy: entry l = plane y-N+l; planes before ya by plain loads
@@ -599,14 +615,34 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
         }
         if (__syncthreads_or(!ok)) goto timeout;
 
-        for (int y = ya; y <= yb; y++) {
+        {
+        bool stop = false;
+        int y = ya;
+        auto body = [&](auto kc) {
+            constexpr int kq = decltype(kc)::value;
+            // accumulator of this plane (REC), loaded before the waits
+            float accv[4] = {0.f, 0.f, 0.f, 0.f};
+            long long accb = 0;
+            if (MODE == REC && mem && mx && in_range(y, it.lo[2], it.hi[2])) {
+                const long long n0 = g.H[0] - g.L[0] + 1, n1 = g.H[1] - g.L[1] + 1;
+                accb = (long long)s * g.nphys + (long long)(oz - g.L[0]) +
+                       n0 * ((long long)(ox - g.L[1]) + n1 * (long long)(y - g.L[2]));
+#pragma unroll
+                for (int r = 0; r < 4; r++)
+                    if (mz[r]) accv[r] = acc[accb + r];
+            }
+#ifdef SMI_TIMING
+            const long long tw0 = clock64();
+#endif
             ok = ring_wait(bar, S, 0, parity, hr, y + N - 1, ya);
             ok &= ring_wait(cbar, SC, 16, parity, cr, y, ya);
-            put(q[2 * N - 1], lds4(sm + ((y + N - 1 - ya) % S) * Lay::SLOT + Lay::Y_OFF + own));
+#ifdef SMI_TIMING
+            t_wait += clock64() - tw0;
+#endif
+            put(q[((2 * N - 1) + kq) % (2 * N)], lds4(sm + ((y + N - 1 - ya) % S) * Lay::SLOT + Lay::Y_OFF + own));
             const float *slot = sm + ((y - ya) % S) * Lay::SLOT;
             const float *cs = cbase + ((y - ya) % SC) * Lay::CSLOT + own;
             const bool my = in_range(y, it.lo[2], it.hi[2]);
-            const bool sy = (MODE == FWD) && (y < g.nb + ext || y >= g.ne[2] - g.nb - 1 - ext);
             const bool act = mem && mx && my;
             float pv[4], Kv[4];
             put(pv, lds4(cs));
@@ -629,18 +665,6 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
                     for (int l = 1; l <= N; l++) d += g.c[0][l - 1] * (W[4 + r + l - 1] - W[4 + r - l]);
                     div[r] = d;
                 }
-                if (MODE == FWD && sz && act) {
-#pragma unroll
-                    for (int r = 0; r < 4; r++) {
-                        const int z = oz + r;
-                        if (!mz[r] || !slab(g, 0, z)) continue;
-                        float *ps = f.psiv[0] + (long long)s * g.slab_n[0] + slab_index(g, 0, z, ox, y);
-                        const float d = div[r];
-                        const float psi = g.cpb[0][z] * *ps + g.cpa[0][z] * d;
-                        *ps = psi;
-                        div[r] = d + psi;
-                    }
-                }
             }
             // ---- x ----
             {
@@ -658,16 +682,6 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
                     for (int l = 1; l <= N; l++) d += g.c[1][l - 1] * (Xr[N + l - 1][r] - Xr[N - l][r]);
                     D[r] = d;
                 }
-                if (MODE == FWD && sx && act && slab(g, 1, ox)) {
-#pragma unroll
-                    for (int r = 0; r < 4; r++) {
-                        if (!mz[r]) continue;
-                        float *ps = f.psiv[1] + (long long)s * g.slab_n[1] + slab_index(g, 1, oz + r, ox, y);
-                        const float psi = g.cpb[1][ox] * *ps + g.cpa[1][ox] * D[r];
-                        *ps = psi;
-                        D[r] += psi;
-                    }
-                }
 #pragma unroll
                 for (int r = 0; r < 4; r++) div[r] += D[r];
             }
@@ -678,18 +692,8 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
                 for (int r = 0; r < 4; r++) {
                     float d = 0.f;
 #pragma unroll
-                    for (int l = 1; l <= N; l++) d += g.c[2][l - 1] * (q[N + l - 1][r] - q[N - l][r]);
+                    for (int l = 1; l <= N; l++) d += g.c[2][l - 1] * (q[((N + l - 1) + kq) % (2 * N)][r] - q[((N - l) + kq) % (2 * N)][r]);
                     D[r] = d;
-                }
-                if (MODE == FWD && sy && act && slab(g, 2, y)) {
-#pragma unroll
-                    for (int r = 0; r < 4; r++) {
-                        if (!mz[r]) continue;
-                        float *ps = f.psiv[2] + (long long)s * g.slab_n[2] + slab_index(g, 2, oz + r, ox, y);
-                        const float psi = g.cpb[2][y] * *ps + g.cpa[2][y] * D[r];
-                        *ps = psi;
-                        D[r] += psi;
-                    }
                 }
 #pragma unroll
                 for (int r = 0; r < 4; r++) div[r] += D[r];
@@ -701,16 +705,13 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
                     const float amp = src_scale * stf[step];
                     float lpv[4];
                     put(lpv, lds4(cs + 2 * CORE));
-                    const long long n0 = g.H[0] - g.L[0] + 1, n1 = g.H[1] - g.L[1] + 1;
                     const bool kxy = in_range(ox, it.plo[1], it.phi[1]) && in_range(y, it.plo[2], it.phi[2]);
 #pragma unroll
                     for (int r = 0; r < 4; r++) {
                         const int z = oz + r;
                         np[r] = pv[r];
                         if (!mz[r]) continue;
-                        const long long kp = (long long)(z - g.L[0]) +
-                                             n0 * ((long long)(ox - g.L[1]) + n1 * (long long)(y - g.L[2]));
-                        acc[(long long)s * g.nphys + kp] += lpv[r] * (img_mode == 0 ? div[r] : pv[r]);
+                        acc[accb + r] = accv[r] + lpv[r] * (img_mode == 0 ? div[r] : pv[r]);
                         float pn = pv[r] + dt * Kv[r] * div[r];
                         const int t0 = z - st.first[0], t1 = ox - st.first[1], t2 = y - st.first[2];
                         if (t0 >= 0 && t0 < st.cnt[0] && t1 >= 0 && t1 < st.cnt[1] && t2 >= 0 && t2 < st.cnt[2])
@@ -723,11 +724,17 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
                 }
                 *reinterpret_cast<float4 *>(f.p + sh + gidx(g, oz, ox, y)) = make_float4(np[0], np[1], np[2], np[3]);
             }
-#pragma unroll
-            for (int l = 0; l < 2 * N - 1; l++)
-#pragma unroll
-                for (int r = 0; r < 4; r++) q[l][r] = q[l + 1][r];
-            if (__syncthreads_or(!ok)) goto timeout;
+#ifdef SMI_TIMING
+            const long long ts0 = clock64();
+            n_planes++;
+#endif
+            if (__syncthreads_or(!ok)) {
+                stop = true;
+                return;
+            }
+#ifdef SMI_TIMING
+            t_sync += clock64() - ts0;
+#endif
             if (tid == 0) {
                 if (hr.issued < ylast) {
                     const int yn = hr.issued + 1;
@@ -750,6 +757,9 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
             }
             if (hr.issued < ylast) hr.issued++;
             if (cr.issued < yb) cr.issued++;
+        };
+        while (y <= yb && !stop) Unroll<0, 2 * N>::run(body, y, yb, stop);
+        if (stop) goto timeout;
         }
         continue;
     timeout:
@@ -758,6 +768,11 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
         ring_drain(cbar, SC, 16, parity, cr, ya);
         return;
     }
+#ifdef SMI_TIMING
+    if (threadIdx.x == 0 && (blockIdx.x % 97) == 0 && n_planes > 0)
+        printf("T%d blk %d planes %lld all %lld wait %lld (%.0f%%) sync %lld (%.0f%%)\n", MODE, blockIdx.x, n_planes,
+               clock64() - t_all, t_wait, 100.0 * t_wait / (clock64() - t_all), t_sync, 100.0 * t_sync / (clock64() - t_all));
+#endif
 }
 
 }  // namespace s3
@@ -858,6 +873,7 @@ bool make_maps3(Maps3 &m, const Grid &g, const Fields &f, int nshot)
 void launch3_v(const LaunchCtx &lc, const Maps3 &m, const Grid &g, const Batch &b, Fields f, int step, int mode,
                unsigned *err)
 {
+    // the adjoint's interior update is the forward scheme; only its box differs
     if (g.N == 2) {
         if (mode == 0) run_v<2, 0>(lc, m, g, b, f, step, err);
         else if (mode == 1) run_v<2, 1>(lc, m, g, b, f, step, err);
