@@ -59,6 +59,25 @@ def dist_env():
     return world, rank, local
 
 
+def shard_shots(nshot: int, world: int, rank: int, nsteps: int) -> list:
+    """Shots of this rank, cycled over nsteps steps: rank r owns shots
+    r, r+world, ... (replicas; no exchange on the data path)."""
+    mine = list(range(rank % nshot, nshot, world)) or [rank % nshot]
+    return [mine[k % len(mine)] for k in range(nsteps)]
+
+
+def aggregate(t_ms: float, units: float, world: int, device):
+    """(max time over ranks in ms, sum of units over ranks)."""
+    import torch
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -189,8 +208,7 @@ def run_ours(args):
     vp = torch.from_numpy(w.vp).to(dev)
     rho = torch.from_numpy(w.rho).to(dev)
     stf = torch.from_numpy(w.stf).to(dev)
-    my_shots = list(range(rank % w.nshot, w.nshot, world)) or [rank % w.nshot]
-    order = [my_shots[k % len(my_shots)] for k in range(args.warmup + args.steps)]
+    order = shard_shots(w.nshot, world, rank, args.warmup + args.steps)
     # observed data: forward modelling in the true model (untimed set-up)
     gen = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb)
     dobs = {}
@@ -225,13 +243,8 @@ def run_ours(args):
     clk = clocks.stop()
     t_ms = e0.elapsed_time(e1)
     units = sum(s["point_updates"] for s in stats)
-    t_all = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-    u_all = torch.tensor([units], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t_all, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(u_all, op=torch.distributed.ReduceOp.SUM)
-    t_max = float(t_all.item())
-    value = float(u_all.item()) / (t_max / 1e3) / 1e9
+    t_max, u_sum = aggregate(t_ms, units, world, dev)
+    value = u_sum / (t_max / 1e3) / 1e9
 
     # roofline of the dominant stencil class (forward / adjoint / reconstruction)
     ms = np.sum([s["ms"] for s in stats], axis=0)

@@ -152,9 +152,20 @@ int smi_rtm(const smi_model *model, const smi_geometry *geom, const smi_wavelet 
 int smi_fwi_gradient(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
                      const smi_opts *opts, const float *dobs, double *misfit, float *grad_vp);
 
+/* Vector-Jacobian product of smi_forward with respect to Vp: for an upstream
+ * gradient g = dL/dseis (adj_src, seis layout, host or device), writes
+ * dL/dVp = sum over shots, receivers and samples of g * d seis / d Vp on the
+ * physical grid (grad_vp, n1*n2*n3 floats, host or device).  It is the FWI
+ * gradient computation (Eq. gradrhokappa, Algorithm 2) with g in place of
+ * the residual: forward modelling saving the boundaries (Sec. 4.2), then the
+ * exact discrete adjoint with g as its source.  The saved boundaries are the
+ * checkpoint; no wavefield history is kept. */
+int smi_forward_vjp(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                    const smi_opts *opts, const float *adj_src, float *grad_vp);
+
 /* Sizes a caller needs before a call: seismogram floats, image floats and
  * the device bytes the call will allocate (kind: 0 forward, 1 rtm, 2
- * gradient).  Validates like the calls themselves (CFL, dispersion,
+ * gradient, 3 vector-Jacobian product).  Validates like the calls themselves (CFL, dispersion,
  * positions) and launches one small reduction to find vmin/vmax.  Any
  * output pointer may be NULL. */
 int smi_query(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,

@@ -409,7 +409,8 @@ int finish_stream(cudaStream_t st)
     return SMI_OK;
 }
 
-// kind: 0 forward, 1 rtm, 2 gradient
+// kind: 0 forward, 1 rtm, 2 gradient, 3 vector-Jacobian product of the
+// forward map with respect to vp (adjoint source given)
 int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet *w, const smi_opts *o,
         const float *dobs, float *seis_out, float *img_out, double *misfit_out)
 {
@@ -431,7 +432,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         LaunchCtx lc{st, &launches};
         const size_t nseis = (size_t)S.nt * S.nrec_total;
         if (kind == 0 && !seis_out) return fail(SMI_ERR_ARG, "seis is null");
-        if (kind != 0 && !dobs) return fail(SMI_ERR_ARG, "dobs is null");
+        if (kind != 0 && !dobs) return fail(SMI_ERR_ARG, kind == 3 ? "adj_src is null" : "dobs is null");
 
         // outputs and observed data on the device
         float *d_seis_out = nullptr, *d_img = nullptr;
@@ -573,7 +574,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 launch_zero(lc, A.psiv[a], sizeof(float) * g.slab_n[a] * nb_shot);
             }
             launch_zero(lc, acc, sizeof(float) * g.nphys * nb_shot);
-            const int mode = kind == 2 ? 0 : 1;
+            const int mode = (kind == 2 || kind == 3) ? 0 : 1;     // 0: gradient, 1: image
             for (int it = S.nt - 1; it >= 0; it--) {
                 const int mrev = S.nt - 1 - it;
                 if (max_rec > 0) launch_adj_inject(lc, g, b, A.p, res, d_soff, S.nt, it);
@@ -614,7 +615,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             launch_reduce_shots(lc, g, acc, nb_shot, d_img, s0 > 0);
             // batch buffers are released (stream-ordered) when `ba` goes out of scope
         }
-        if (kind == 2) launch_finalize_grad(lc, g.nphys, S.vp, g.dt, d_img);
+        if (kind == 2 || kind == 3) launch_finalize_grad(lc, g.nphys, S.vp, g.dt, d_img);
 
         // outputs back to the host where needed
         if (kind == 0 && d_seis_out != seis_out)
@@ -688,13 +689,20 @@ int smi_fwi_gradient(const smi_model *model, const smi_geometry *geom, const smi
     return run(2, model, geom, wav, opts, dobs, nullptr, grad_vp, misfit);
 }
 
+int smi_forward_vjp(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                    const smi_opts *opts, const float *adj_src, float *grad_vp)
+{
+    if (!grad_vp) return fail(SMI_ERR_ARG, "grad_vp is null");
+    return run(3, model, geom, wav, opts, adj_src, nullptr, grad_vp, nullptr);
+}
+
 int smi_query(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
               const smi_opts *opts, int kind, size_t *seis_elems, size_t *image_elems,
               size_t *device_bytes)
 {
     t_err.clear();
     if (!opts) return fail(SMI_ERR_ARG, "null options");
-    if (kind < 0 || kind > 2) return fail(SMI_ERR_ARG, "kind must be 0, 1 or 2");
+    if (kind < 0 || kind > 3) return fail(SMI_ERR_ARG, "kind must be 0, 1, 2 or 3");
     cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
     long long launches = 0;
     Setup S;

@@ -79,7 +79,8 @@ class smi_stats(ctypes.Structure):
 
 # C functions exported by libsmi (the names of include/smi.h)
 EXPORTS = ["smi_opts_default", "smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query",
-           "smi_box_table", "smi_last_stats", "smi_last_error", "smi_version", "smi_forward_noalloc"]
+           "smi_box_table", "smi_last_stats", "smi_last_error", "smi_version", "smi_forward_noalloc",
+           "smi_forward_vjp"]
 
 
 def _load():
@@ -95,13 +96,14 @@ def _load():
     L.smi_forward_noalloc.argtypes = common + [vp]
     L.smi_rtm.argtypes = common + [vp, vp]
     L.smi_fwi_gradient.argtypes = common + [vp, vp, vp]
+    L.smi_forward_vjp.argtypes = common + [vp, vp]
     L.smi_query.argtypes = common + [c_int, P(ctypes.c_size_t), P(ctypes.c_size_t), P(ctypes.c_size_t)]
     L.smi_box_table.argtypes = common + [c_int, c_int, c_int, c_int, vp, vp]
     L.smi_last_stats.argtypes = [P(smi_stats)]
     L.smi_last_error.restype = ctypes.c_char_p
     L.smi_version.restype = ctypes.c_char_p
     for name in ("smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query", "smi_box_table",
-                 "smi_last_stats", "smi_forward_noalloc"):
+                 "smi_last_stats", "smi_forward_noalloc", "smi_forward_vjp"):
         getattr(L, name).restype = c_int
     return L
 
@@ -298,6 +300,19 @@ def smi_fwi_gradient(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None,
     return J, g.reshape(shape)
 
 
+def smi_forward_vjp(vp, rho, prob: Problem, srcs, recs, stf, adj_src, stream=None, out=None):
+    """dL/dVp for an upstream gradient adj_src = dL/dseis (seismogram layout)."""
+    m, keep_m, cuda, shape = _model(vp, rho, prob.d)
+    geo, keep_g, off = _geometry(srcs, recs)
+    ks, ps, _ = _as_f32(stf)
+    kd, pd, _ = _dobs_flat(adj_src, cuda, None)
+    w = smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
+    o = _opts(prob, stream)
+    g, pg = _out(out, int(np.prod(shape)), cuda, vp.device if cuda else None)
+    _check(_lib.smi_forward_vjp(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w), ctypes.byref(o), pd, pg))
+    return g.reshape(shape)
+
+
 def smi_query(vp, rho, prob: Problem, srcs, recs, stf, kind: str = "forward", stream=None):
     """(seis_elems, image_elems, device_bytes) of a call."""
     m, keep_m, cuda, shape = _model(vp, rho, prob.d)
@@ -306,7 +321,7 @@ def smi_query(vp, rho, prob: Problem, srcs, recs, stf, kind: str = "forward", st
     w = smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
     o = _opts(prob, stream)
     a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
-    k = {"forward": 0, "rtm": 1, "gradient": 2}[kind]
+    k = {"forward": 0, "rtm": 1, "gradient": 2, "vjp": 3}[kind]
     _check(_lib.smi_query(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w), ctypes.byref(o), k,
                           ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
