@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nt", type=int, default=2500, help="time steps (full workload: 2500)")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving mix instead: throughput and p50/p99 latency of the request server")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-scale", type=float, default=0.5,
+                    help="grid sizes and nt of the serving mix relative to the full mix")
     return ap.parse_args()
 
 
@@ -302,9 +307,47 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_serve(args):
+    """Serving mix: one-at-a-time plain FP32 calls vs the request server (FP16
+    boundaries, 4 slots) under Poisson arrivals at 1.2x and 0.5x the measured
+    one-at-a-time service rate."""
+    import torch
+    from paper_2311_02293_gb300 import build
+    if not os.path.exists(os.path.join(ROOT, "paper_2311_02293_gb300", "libsmi.so")):
+        build.build()
+    from paper_2311_02293_gb300 import serve, smi
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    reqs = serve.make_mix(args.serve_requests, scale=args.serve_scale, shell="f16")
+    plain = serve.make_mix(args.serve_requests, scale=args.serve_scale, shell="f32")
+    serve._prepare(reqs, dev)
+    serve._prepare(plain, dev)
+    serve.run_alone(plain[:4], dev)                        # warm-up
+    _, t_alone = serve.run_alone(plain, dev)
+    rate1 = len(plain) / t_alone
+    out = {}
+    for name, factor in (("rate_1.2x", 1.2), ("rate_0.5x", 0.5)):
+        m = serve.run_mix(reqs, dev, slots=4, rate=factor * rate1)
+        out[name] = {"requests_per_s": m["requests_per_s"], "gradient_shots_per_s": m["gradient_shots_per_s"],
+                     "p50_s": m["p50_s"], "p99_s": m["p99_s"], "failed": m["failed"], "seconds": m["seconds"]}
+    ngrad = sum(1 for r in plain if r.kind == "gradient")
+    kinds = {k: sum(1 for r in reqs if r.kind == k) for k in ("gradient", "forward", "rtm")}
+    line = {"metric": "served gradient shots/s (request server, FP16 boundaries)",
+            "value": out["rate_1.2x"]["gradient_shots_per_s"], "unit": "gradient shots/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving_mix_{len(reqs)}req_scale{args.serve_scale}", "kinds": kinds,
+                       "slots": 4, "arrivals": "poisson"},
+            "one_at_a_time_fp32": {"requests_per_s": rate1, "gradient_shots_per_s": ngrad / t_alone,
+                                   "seconds": t_alone},
+            "served": out}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.serve:
+        run_serve(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

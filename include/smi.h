@@ -201,6 +201,55 @@ int smi_box_table(const smi_model *model, const smi_geometry *geom, const smi_wa
 int smi_forward_noalloc(const smi_model *model, const smi_geometry *geom,
                         const smi_wavelet *wav, const smi_opts *opts, float *seis);
 
+/* ---------------------------------------------------------------------------
+ * Request server (continuous batching of modelling jobs on one GPU).  The
+ * GPU counterpart of the paper's shot-per-process parallelism (Sec. 3.2) and
+ * batchwise job scheduling (Sec. 4.3): requests of any size, dimension and
+ * nt are queued in arrival order and admitted into one of `slots` worker
+ * slots (each with its own CUDA stream and host thread) as soon as a slot is
+ * free and the request's device footprint (smi_query) fits in the remaining
+ * memory budget; admitted requests run concurrently.  Among queued requests
+ * the oldest one that fits is admitted first.  A request whose footprint
+ * exceeds the whole budget fails at submission with SMI_ERR_NOMEM. */
+typedef struct smi_server smi_server;
+
+typedef struct {
+    int kind;                 /* 0 forward (out = seismograms), 1 RTM (out = image),
+                                 2 FWI gradient (out = grad_vp, misfit) */
+    smi_model model;
+    smi_geometry geom;
+    smi_wavelet wav;
+    smi_opts opts;            /* opts.stream is replaced by the slot's stream */
+    const float *dobs;        /* observed data (kinds 1, 2) */
+    float *out;               /* output array, as for the direct calls */
+    double *misfit;           /* kind 2, may be NULL */
+} smi_request;                /* every pointer stays owned by the caller and must
+                                 stay valid until the request has finished */
+
+typedef struct {
+    int status;               /* SMI_OK or the request's SMI_ERR_* code */
+    size_t device_bytes;      /* admitted footprint */
+    double t_submit, t_start, t_end;   /* seconds since the server was created */
+    char error[256];
+} smi_result;
+
+/* budget_bytes = 0: 80 % of the device's free memory at creation. */
+smi_server *smi_server_create(size_t budget_bytes, int slots);
+/* Queues *req (copied); *ticket identifies it.  Returns SMI_ERR_ARG only for
+ * a malformed call; request errors are reported by smi_wait. */
+int smi_submit(smi_server *s, const smi_request *req, long long *ticket);
+/* Waits for the request to finish (timeout_s < 0: no limit); SMI_ERR_TIMEOUT
+ * if it is still queued or running after timeout_s. */
+int smi_wait(smi_server *s, long long ticket, double timeout_s, smi_result *res);
+/* *state: 0 queued, 1 running, 2 finished. */
+int smi_poll(smi_server *s, long long ticket, int *state);
+/* Removes a request that has not started yet (its status becomes SMI_ERR_ARG). */
+int smi_cancel(smi_server *s, long long ticket);
+int smi_server_info(smi_server *s, size_t *budget, size_t *in_use, long long *queued,
+                    long long *completed, long long *failed);
+/* Finishes running requests, drops queued ones, joins the workers. */
+void smi_server_destroy(smi_server *s);
+
 /* Measurements of the calling thread's last smi_forward / smi_rtm /
  * smi_fwi_gradient call. */
 int smi_last_stats(smi_stats *st);

@@ -80,7 +80,8 @@ class smi_stats(ctypes.Structure):
 # C functions exported by libsmi (the names of include/smi.h)
 EXPORTS = ["smi_opts_default", "smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query",
            "smi_box_table", "smi_last_stats", "smi_last_error", "smi_version", "smi_forward_noalloc",
-           "smi_forward_vjp"]
+           "smi_forward_vjp", "smi_server_create", "smi_submit", "smi_wait", "smi_poll", "smi_cancel",
+           "smi_server_info", "smi_server_destroy"]
 
 
 def _load():

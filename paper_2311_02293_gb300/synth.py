@@ -108,7 +108,7 @@ def layered_fault_2d(nz=301, nx=1001, h=12.5, nt=3000, dt=1e-3, fm=8.0, order=8,
     model).  40 shots at x = 400 + 300 k m, z = 25 m; 1001 receivers at
     z = 25 m on every node."""
     rng = np.random.default_rng(seed)
-    nl = int(rng.integers(8, 16))
+    nl = min(int(rng.integers(8, 16)), max(2, (nz - 6) // 4))   # small grids hold fewer layers
     # interface depths (cells): sorted uniform with >= 3 cells between them
     while True:
         tops = np.sort(rng.integers(3, nz - 3, size=nl - 1))
