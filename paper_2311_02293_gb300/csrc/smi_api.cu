@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -527,6 +528,21 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             b.tab_src = S.d_tab_src + (size_t)s0 * (S.nt + 1) * 6;
             b.tab_rec = S.d_tab_rec + (size_t)s0 * (S.nt + 1) * 6;
             b.nt1 = S.nt + 1;
+            // union of the batch's boxes after n steps (bounds the CPML launches)
+            auto batch_box = [&](const std::vector<int> &ext, int n, int lo[3], int hi[3]) {
+                for (int a = 0; a < 3; a++) {
+                    lo[a] = INT_MAX;
+                    hi[a] = INT_MIN;
+                }
+                for (int s = 0; s < nb_shot; s++) {
+                    int l[3], h[3];
+                    box_bounds(g, ext.data() + 6 * (s0 + s), n, l, h);
+                    for (int a = 0; a < 3; a++) {
+                        lo[a] = std::min(lo[a], l[a]);
+                        hi[a] = std::max(hi[a], h[a]);
+                    }
+                }
+            };
             launch_zero(lc, F.p, sizeof(float) * g.ntot * nb_shot);
             for (int a = 0; a < g.ndim; a++) {
                 launch_zero(lc, F.v[a], sizeof(float) * g.ntot * nb_shot);
@@ -539,10 +555,12 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 if (kind != 0) launch_save_bands(lc, g, b, F, bd, it, d_absmax);
                 tm.begin(0);
                 if (fast3) {
+                    int blo[3], bhi[3];
+                    batch_box(S.box_src, it, blo, bhi);
                     launch3_v(lc, mF, g, b, F, it, 0, d_wait);
-                    launch_fwd_corrections(lc, g, b, F, it, true);
+                    launch_fwd_corrections(lc, g, b, F, it, true, blo, bhi);
                     launch3_p(lc, mF, nullptr, g, b, F, it, 0, d_wait, nullptr, 0, nullptr, 0.0f);
-                    launch_fwd_corrections(lc, g, b, F, it, false);
+                    launch_fwd_corrections(lc, g, b, F, it, false, blo, bhi);
                 } else {
                     launch_fwd_v(lc, g, b, F, it);
                     launch_fwd_p(lc, g, b, F, it);
@@ -590,9 +608,11 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 launch_restore_bands(lc, g, b, F, bd, it);
                 tm.begin(1);
                 if (fast3) {
-                    launch_adj_corrections(lc, g, b, A, mrev, true);
+                    int blo[3], bhi[3];
+                    batch_box(S.box_rec, mrev, blo, bhi);
+                    launch_adj_corrections(lc, g, b, A, mrev, true, blo, bhi);
                     launch3_v(lc, mA, g, b, A, mrev, 1, d_wait);
-                    launch_adj_corrections(lc, g, b, A, mrev, false);
+                    launch_adj_corrections(lc, g, b, A, mrev, false, blo, bhi);
                     launch3_p(lc, mA, nullptr, g, b, A, mrev, 1, d_wait, nullptr, 0, nullptr, 0.0f);
                 } else {
                     launch_adj_v(lc, g, b, A, mrev);

@@ -132,12 +132,35 @@ void launch_adj_inject(const LaunchCtx &lc, const Grid &g, const Batch &b, float
                        const float *res, const long long *seis_off, int nt, int it);
 void launch_adj_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m);
 void launch_adj_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m);
+// One piece of the union of the CPML bands: per axis up to two index
+// intervals {start0, len0, start1, len1}; nodes = product of the counts.
+struct Piece {
+    int iv[3][4];
+    int cnt[3];
+    int axis;              // the axis whose band defines the piece
+    int blocks;            // 256-thread blocks of this piece (per shot); 0: empty
+};
+// Disjoint pieces covering the nodes within w_lo of the low end or w_hi of
+// the high end of some axis, clipped to a box (make_pieces); q[a] is the
+// piece of axis a.
+struct Pieces {
+    int n;                 // non-empty pieces
+    int w_lo, w_hi;
+    Piece q[3];
+};
+Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, int w_hi);
 // Transposed CPML terms of the adjoint over the slabs (vel: velocity part,
-// else pressure part), one launch per axis; run before the interior kernels.
-void launch_adj_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, bool vel);
+// else pressure part), one launch over the union of the axes' bands within
+// the box [lo, hi] (union of the batch's receiver boxes after m reverse
+// steps); run before the interior kernels.
+void launch_adj_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, bool vel,
+                            const int lo[3], const int hi[3]);
 // Forward CPML memory-variable updates over the slabs (vel: velocity part,
-// else pressure part); added to the interior update of the main kernels.
-void launch_fwd_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, bool vel);
+// else pressure part), one launch within the box [lo, hi] (union of the
+// batch's source boxes at step it); added to the interior update of the
+// main kernels.
+void launch_fwd_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, bool vel,
+                            const int lo[3], const int hi[3]);
 void launch_recon_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f,
                     const float *lp, float *acc, int mode, const float *stf, int it,
                     float src_scale);

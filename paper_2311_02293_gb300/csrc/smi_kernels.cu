@@ -21,6 +21,8 @@ namespace smi {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kCpmlChunk = 4;      // nodes per thread along x / y, CPML kernels of the x / y pieces
+constexpr int kCpmlChunkZ = 2;     // nodes per lane along y (x in 2D), CPML kernel of the z piece
 constexpr int kMaxBlocksX = 152 * 16;
 
 __device__ __forceinline__ long long gidx(const Grid &g, int i1, int i2, int i3)
@@ -282,125 +284,380 @@ __global__ void __launch_bounds__(kThreads) k_adj_p(Grid g, Batch b, Fields f, i
 }
 
 // ---------------------------------------------------------------------------
-// Transposed CPML terms of the adjoint, applied over the slabs only, before
-// the interior adjoint kernels (which then run the plain forward scheme).
-// Axis a, band of nodes whose stencil reaches the axis-a CPML layer:
-//   V (lam_v update): lv_a -= dt b_a D_a[eta_a],  eta_a = Ap_a (lp + phi_a),
-//                     after the deferred chi_a <- Bv_a (chi_a + lv_a);
-//   P (lam_p update): lp -= dt kappa D_a[zeta_a], zeta_a = Av_a (lv_a + chi_a),
-//                     after phi_a <- Bp_a (phi_a + lp).
-// Region: the receiver box (m reverse steps) within nb+N+1 nodes of either
-// end of axis a.
-// Thread -> node of the axis-AX band: wl = nb + N + 1 nodes at each end of
-// the axis (they cover every node whose stencil reaches that CPML layer),
-// other axes over the grid; nodes outside the receiver box are skipped.
-template <int N, int AX>
-__device__ __forceinline__ bool corr_node(const Grid &g, const Batch &b, const int *tab, int m, int &s, int i[3], int wl)
+// ---------------------------------------------------------------------------
+// CPML terms over the slabs only (Sec. 2.1), added to the interior update of
+// the main 3D kernels, which apply the plain scheme everywhere.
+//
+// Forward (the CPML of Komatitsch & Martin):
+//   FV: psi_a <- Bv_a psi_a + Av_a D_a p;    v_a -= dt b_a psi_a
+//   FP: psi_a <- Bp_a psi_a + Ap_a D_a v_a;  p -= dt kappa sum_a psi_a
+// Adjoint (transpose of one forward step; runs before the interior adjoint
+// kernels; chi / phi are the adjoint memory variables, kept in the psip /
+// psiv slabs):
+//   AV: chi_a <- Bv_a (chi_a + lv_a);  lv_a -= dt b_a D_a[Ap_a (lp + phi_a)]
+//   AP: phi_a <- Bp_a (phi_a + lp);    lp -= dt kappa sum_a D_a[Av_a (lv_a + chi_a)]
+//
+// Every D_a above is sum_l c_l (h(j + o + l) - h(j + o + 1 - l)) over a
+// field h along axis a (o = 0 for the V kinds, -1 for the P kinds), with
+// h = p, v_a, Ap_a (lp + phi_a) or Av_a (lv_a + chi_a), zero outside the
+// grid (and, for the adjoint kinds, outside the slab).
+//
+// One launch per kind covers the union of the axes' bands (nodes within
+// w_lo of the low end or w_hi of the high end of an axis; forward: the
+// slabs; adjoint: every node whose stencil reaches a slab node), cut into
+// disjoint pieces clipped to the union of the batch's computing boxes (see
+// Pieces).  Each node belongs to one thread, which applies the terms of
+// every axis whose band holds it, so the kinds that update p / lp (read at
+// the node only) need no ordering between axes.  A thread takes a chunk of
+// consecutive nodes along x or y and issues all the chunk's loads before
+// its first store (the kernels are bound by memory latency, not bytes); a
+// warp holds consecutive z indices, so branches on the x and y bands are
+// warp-uniform.
+enum CpmlKind { kFV = 0, kFP = 1, kAV = 2, kAP = 3 };
+
+__device__ __forceinline__ bool in_band(const Grid &g, const Pieces &P, int a, int j)
 {
-    const int zdim = (AX == 2) ? 2 * wl : g.ne[2];
-    s = blockIdx.z / zdim;
-    const int tz = blockIdx.z - s * zdim;
-    const int tx = blockIdx.x * 32 + threadIdx.x, ty = blockIdx.y * 8 + threadIdx.y;
-    int j;
-    if (AX == 0) { j = tx; i[1] = ty; i[2] = tz; }
-    else if (AX == 1) { i[0] = tx; j = ty; i[2] = tz; }
-    else { i[0] = tx; i[1] = ty; j = tz; }
-    if (j >= 2 * wl) return false;
-    i[AX] = j < wl ? j : g.ne[AX] - 2 * wl + j;
-    if (i[AX] < 0 || (j >= wl && i[AX] < wl)) return false;     // bands overlap on a short axis
-    int lo[3], hi[3];
-    box_at(tab, b.nt1, s, m, lo, hi);
-    return i[0] >= lo[0] && i[0] <= hi[0] && i[1] >= lo[1] && i[1] <= hi[1] && i[2] >= lo[2] && i[2] <= hi[2];
+    return j < P.w_lo || j >= g.ne[a] - P.w_hi;
 }
 
 // js of node j of a CPML slab (slab arrays compress their axis to 2 nb + 1).
 __device__ __forceinline__ int slab_j(const Grid &g, int a, int j) { return j < g.nb ? j : j - (g.ne[a] - 2 * g.nb - 1); }
 
-// Offset and stride of axis AX's slab index at node i with i[AX] replaced.
-template <int AX>
-__device__ __forceinline__ void slab_base(const Grid &g, const int i[3], long long &base, long long &stride)
+// Offsets inside one shot's arrays are 32-bit: the 3D path requires a
+// field of one shot to hold fewer than 2^31 points.
+__device__ __forceinline__ int gidx32(const Grid &g, int i0, int i1, int i2) { return i0 + g.px * (i1 + g.ne[1] * i2); }
+__device__ __forceinline__ int gstride32(const Grid &g, int a) { return a == 0 ? 1 : (a == 1 ? g.px : g.px * g.ne[1]); }
+
+// Offset and stride of axis a's slab index at node i with i[a] replaced.
+__device__ __forceinline__ void slab_base(const Grid &g, int a, const int i[3], int &base, int &stride)
 {
-    if (AX == 0) { base = (long long)g.S * ((long long)i[1] + (long long)g.ne[1] * i[2]); stride = 1; }
-    else if (AX == 1) { base = (long long)i[0] + (long long)g.ne[0] * g.S * i[2]; stride = g.ne[0]; }
-    else { base = (long long)i[0] + (long long)g.ne[0] * i[1]; stride = (long long)g.ne[0] * g.ne[1]; }
+    if (a == 0) { base = g.S * (i[1] + g.ne[1] * i[2]); stride = 1; }
+    else if (a == 1) { base = i[0] + g.ne[0] * g.S * i[2]; stride = g.ne[0]; }
+    else { base = i[0] + g.ne[0] * i[1]; stride = g.ne[0] * g.ne[1]; }
 }
 
-template <int N, int AX>
-__global__ void __launch_bounds__(256) k_corr_v(Grid g, Batch b, Fields f, int m)
-{
-    int s, i[3];
-    if (!corr_node<N, AX>(g, b, b.tab_rec, m, s, i, g.nb + N + 1)) return;
-    const long long k = gidx(g, i[0], i[1], i[2]), st = gstride(g, AX);
-    long long sb, ss;
-    slab_base<AX>(g, i, sb, ss);
-    sb += (long long)s * g.slab_n[AX];
-    const float *lp = f.p + s * g.ntot;
-    float *lv = f.v[AX] + s * g.ntot;
-    const int ia = i[AX];
-    if (in_slab(g, AX, ia)) {                  // deferred chi update with lv before this step
-        float *ch = f.psip[AX] + sb + slab_j(g, AX, ia) * ss;
-        *ch = g.cvb[AX][ia] * (*ch + lv[k]);
+// Arrays of kind KIND along axis A for one shot.
+template <int KIND, int A>
+struct CpmlAxis {
+    static constexpr bool VK = KIND == kFV || KIND == kAV;
+    const float *src;      // h's field: p (FV, AV) or v_a (FP, AP)
+    const float *hmem;     // adjoint kinds: phi_a (AV) or chi_a (AP), the memory variable in h
+    float *mem;            // memory variable updated at the node: psi / chi (V kinds), psi / phi (P kinds)
+    float *fld;            // V kinds: v_a / lv_a
+    int st, ne, sb, ss;    // flat stride, axis length; slab base of the line and slab stride
+    __device__ __forceinline__ CpmlAxis(const Grid &g, const Fields &f, int s, const int i[3])
+    {
+        const long long so = (long long)s * g.ntot, ms = (long long)s * g.slab_n[A];
+        src = VK ? f.p + so : f.v[A] + so;
+        hmem = (KIND == kAV ? f.psiv[A] : f.psip[A]) + ms;
+        mem = (VK ? f.psip[A] : f.psiv[A]) + ms;
+        fld = f.v[A] + so;
+        st = gstride32(g, A);
+        ne = g.ne[A];
+        slab_base(g, A, i, sb, ss);
     }
-    float E = 0.0f;
-#pragma unroll
-    for (int l = 1; l <= N; l++) {
-        float h[2];
-        const int off[2] = {l, 1 - l};
-#pragma unroll
-        for (int e = 0; e < 2; e++) {
-            const int j = ia + off[e];
-            h[e] = 0.0f;
-            if (j >= 0 && j < g.ne[AX] && in_slab(g, AX, j)) {
-                const float A = __ldg(g.cpa[AX] + j);
-                if (A != 0.0f) h[e] = A * (lp[k + off[e] * st] + f.psiv[AX][sb + slab_j(g, AX, j) * ss]);
-            }
+    __device__ __forceinline__ bool slab(const Grid &g, int j) const { return j < g.nb || j >= ne - g.nb - 1; }
+    __device__ __forceinline__ int msi(const Grid &g, int j) const   // slab index of node j (j in the slab)
+    {
+        return sb + (j < g.nb ? j : j - (ne - 2 * g.nb - 1)) * ss;
+    }
+    // h at index j of the line through node k (index ia); zero where the
+    // scheme has none.  Loads depend only on index arithmetic.
+    __device__ __forceinline__ float h(const Grid &g, int k, int ia, int j) const
+    {
+        bool valid = (unsigned)j < (unsigned)ne;
+        if (KIND == kAV || KIND == kAP) valid = valid && slab(g, j);
+        float x = 0.0f;
+        if (valid) {
+            const int kk = k + (j - ia) * st;
+            if (KIND == kFV || KIND == kFP) x = src[kk];
+            else x = __ldg((KIND == kAV ? g.cpa[A] : g.cva[A]) + j) * (src[kk] + hmem[msi(g, j)]);
         }
-        E += g.c[AX][l - 1] * (h[0] - h[1]);
+        return x;
     }
-    if (E != 0.0f) lv[k] -= g.dt * buoyancy(g, AX, ia, k, g.rho[k]) * E;
+};
+
+// D_a at a node from its 2N values of h: w[t] = h(ia + o - N + 1 + t).
+template <int N>
+__device__ __forceinline__ float cpml_d(const Grid &g, int a, const float *w)
+{
+    float D = 0.0f;
+#pragma unroll
+    for (int l = 1; l <= N; l++) D += g.c[a][l - 1] * (w[N - 1 + l] - w[N - l]);
+    return D;
 }
 
-template <int N, int AX>
-__global__ void __launch_bounds__(256) k_corr_phi(Grid g, Batch b, Fields f, int m)
+// Values of one axis at one node, loaded before any store of the chunk:
+// mem = memory variable (if the node is in the slab), fld = v_a / lv_a (V
+// kinds), rho1 = rho one node up the axis (buoyancy).
+struct CpmlOwn {
+    float mem, fld, rho1;
+};
+
+template <int KIND, int A>
+__device__ __forceinline__ CpmlOwn cpml_own(const Grid &g, const CpmlAxis<KIND, A> &x, int ia, int k, bool sl)
 {
-    int s, i[3];
-    if (!corr_node<N, AX>(g, b, b.tab_rec, m, s, i, g.nb + N + 1)) return;
-    const int ia = i[AX];
-    if (!in_slab(g, AX, ia)) return;
-    long long sb, ss;
-    slab_base<AX>(g, i, sb, ss);
-    float *ph = f.psiv[AX] + (long long)s * g.slab_n[AX] + sb + slab_j(g, AX, ia) * ss;
-    *ph = g.cpb[AX][ia] * (*ph + f.p[s * g.ntot + gidx(g, i[0], i[1], i[2])]);
+    CpmlOwn o{0.0f, 0.0f, 0.0f};
+    if (sl) o.mem = x.mem[x.msi(g, ia)];
+    if (CpmlAxis<KIND, A>::VK) {
+        o.fld = x.fld[k];
+        if (ia + 1 < x.ne) o.rho1 = g.rho[k + x.st];
+    }
+    return o;
 }
 
-template <int N, int AX>
-__global__ void __launch_bounds__(256) k_corr_p(Grid g, Batch b, Fields f, int m)
+// Applies the axis-A terms of one node from its preloaded values; the P
+// kinds add their term to acc (p / lp is written once per node).
+template <int KIND, int A>
+__device__ __forceinline__ void cpml_apply(const Grid &g, const CpmlAxis<KIND, A> &x, int ia, int k, bool sl,
+                                           const CpmlOwn &o, float rho0, float lp0, float D, float &acc)
 {
-    int s, i[3];
-    if (!corr_node<N, AX>(g, b, b.tab_rec, m, s, i, g.nb + N + 1)) return;
-    const long long k = gidx(g, i[0], i[1], i[2]), st = gstride(g, AX);
-    long long sb, ss;
-    slab_base<AX>(g, i, sb, ss);
-    sb += (long long)s * g.slab_n[AX];
-    const float *lv = f.v[AX] + s * g.ntot;
-    const int ia = i[AX];
-    float F = 0.0f;
-#pragma unroll
-    for (int l = 1; l <= N; l++) {
-        float h[2];
-        const int off[2] = {l - 1, -l};
-#pragma unroll
-        for (int e = 0; e < 2; e++) {
-            const int j = ia + off[e];
-            h[e] = 0.0f;
-            if (j >= 0 && j < g.ne[AX] && in_slab(g, AX, j)) {
-                const float A = __ldg(g.cva[AX] + j);
-                if (A != 0.0f) h[e] = A * (lv[k + off[e] * st] + f.psip[AX][sb + slab_j(g, AX, j) * ss]);
-            }
+    if (KIND == kFV || KIND == kAV) {
+        const float b = (ia + 1 < x.ne) ? __fdividef(2.0f, rho0 + o.rho1) : __fdividef(1.0f, rho0);
+        if (KIND == kFV) {
+            const float psi = g.cvb[A][ia] * o.mem + g.cva[A][ia] * D;
+            x.mem[x.msi(g, ia)] = psi;
+            x.fld[k] = o.fld - g.dt * b * psi;
+        } else {
+            if (sl) x.mem[x.msi(g, ia)] = g.cvb[A][ia] * (o.mem + o.fld);   // deferred chi update, lv before this step
+            if (D != 0.0f) x.fld[k] = o.fld - g.dt * b * D;
         }
-        F += g.c[AX][l - 1] * (h[0] - h[1]);
+    } else if (KIND == kFP) {
+        const float psi = g.cpb[A][ia] * o.mem + g.cpa[A][ia] * D;
+        x.mem[x.msi(g, ia)] = psi;
+        acc += psi;
+    } else {
+        if (sl) x.mem[x.msi(g, ia)] = g.cpb[A][ia] * (o.mem + lp0);         // phi update, lp before this step
+        acc += D;
     }
-    if (F != 0.0f) f.p[s * g.ntot + k] -= g.dt * g.K[k] * F;
+}
+
+// Band membership of index j on axis a for kind KIND (forward: the slab).
+template <int KIND>
+__device__ __forceinline__ bool cpml_in(const Grid &g, const Pieces &P, int a, int j)
+{
+    return (KIND == kFV || KIND == kFP) ? in_slab(g, a, j) : in_band(g, P, a, j);
+}
+
+__device__ __forceinline__ int iv_map(const int *iv, int c) { return c < iv[1] ? iv[0] + c : iv[2] + c - iv[1]; }
+
+// The axis-A terms of node i (flat k) from 2N gathered h values (corner
+// nodes whose other terms come from a window or from shuffles).
+template <int N, int KIND, int A>
+__device__ __forceinline__ void cpml_gather_term(const Grid &g, const Fields &f, int s, const int i[3], int k,
+                                                 float rho0, float lp0, float &acc)
+{
+    constexpr int O = CpmlAxis<KIND, A>::VK ? 0 : -1;
+    const CpmlAxis<KIND, A> x(g, f, s, i);
+    const int ia = i[A];
+    float w[2 * N];
+#pragma unroll
+    for (int q = 0; q < 2 * N; q++) w[q] = x.h(g, k, ia, ia + O - N + 1 + q);
+    const bool sl = x.slab(g, ia);
+    const CpmlOwn o = cpml_own(g, x, ia, k, sl);
+    cpml_apply(g, x, ia, k, sl, o, rho0, lp0, cpml_d<N>(g, A, w), acc);
+}
+
+// x / y pieces: a thread takes up to U consecutive nodes along the strided
+// axis W of one line (fixed z index i0 and index iR on the remaining axis
+// R); z is inner there, so no node has a z term.  Phase 1 issues every load
+// of the chunk: the window of h along W shared by the U nodes (U + 2N - 1
+// values instead of 2N per node) and the nodes' own values.  Phase 2
+// computes and stores.  Terms of axis R (corner nodes of the x piece) gather
+// their h in phase 2.
+template <int N, int KIND, int U, int W>
+__device__ __forceinline__ void cpml_chunk(const Grid &g, const Fields &f, const Pieces &P, const Piece &p, int s,
+                                           int t, const int lo[3], const int hi[3])
+{
+    constexpr bool VK = KIND == kFV || KIND == kAV;
+    constexpr int O = VK ? 0 : -1;
+    constexpr int R = 3 - W;
+    const int n0 = p.cnt[0], nR = p.cnt[R];
+    int i[3];
+    i[0] = iv_map(p.iv[0], t % n0);
+    t /= n0;
+    i[R] = iv_map(p.iv[R], t % nR);
+    int ch = t / nR;
+    const int c0 = (p.iv[W][1] + U - 1) / U, c1 = (p.iv[W][3] + U - 1) / U;
+    if (ch >= c0 + c1) return;
+    if (i[0] < lo[0] || i[0] > hi[0] || i[R] < lo[R] || i[R] > hi[R]) return;
+    const int seg = ch < c0 ? 0 : 1;
+    ch -= seg ? c0 : 0;
+    const int j0 = p.iv[W][2 * seg] + ch * U;
+    const int jend = min(p.iv[W][2 * seg] + p.iv[W][2 * seg + 1] - 1, hi[W]);
+    i[W] = j0;
+    const int k0 = gidx32(g, i[0], i[1], i[2]);
+    const CpmlAxis<KIND, W> x(g, f, s, i);
+    float *ps = f.p + (long long)s * g.ntot;
+
+    // ---- phase 1: loads ----
+    float win[U + 2 * N - 1];
+#pragma unroll
+    for (int q = 0; q < U + 2 * N - 1; q++) win[q] = x.h(g, k0, j0, j0 + O - N + 1 + q);
+    CpmlOwn oW[U];
+    float rho0[U], own_p[U], kap[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int j = j0 + u, k = k0 + u * x.st;
+        const bool ok = j <= jend && j >= lo[W];
+        rho0[u] = (VK && ok) ? g.rho[k] : 1.0f;
+        own_p[u] = (!VK && ok) ? ps[k] : 0.0f;
+        kap[u] = (!VK && ok) ? g.K[k] : 0.0f;
+        oW[u] = CpmlOwn{0.0f, 0.0f, 0.0f};
+        if (ok) oW[u] = cpml_own(g, x, j, k, x.slab(g, j));
+    }
+
+    // ---- phase 2: compute and store ----
+    const bool inR = R < g.ndim && cpml_in<KIND>(g, P, R, i[R]);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int j = j0 + u, k = k0 + u * x.st;
+        if (!(j <= jend && j >= lo[W])) continue;
+        float acc = 0.0f;
+        cpml_apply(g, x, j, k, x.slab(g, j), oW[u], rho0[u], own_p[u], cpml_d<N>(g, W, win + u), acc);
+        if (inR) {
+            int iu[3] = {i[0], i[1], i[2]};
+            iu[W] = j;
+            cpml_gather_term<N, KIND, R>(g, f, s, iu, k, rho0[u], own_p[u], acc);
+        }
+        if (KIND == kFP) ps[k] = own_p[u] - g.dt * kap[u] * acc;
+        if (KIND == kAP && acc != 0.0f) ps[k] = own_p[u] - g.dt * kap[u] * acc;
+    }
+}
+
+// z piece: a warp takes one line segment along z (32 lanes = BW owned nodes
+// plus the 2N - 1 halo nodes of their stencils) times up to U consecutive
+// nodes along the strided axis W.  Each lane loads h along z at its own
+// position and the z derivatives come from warp shuffles; the W terms
+// (chunks that reach the W band) use a per-lane window along W, and the
+// terms of axis R (x in 3D) gather their h.  Control flow is warp-uniform
+// up to the shuffles.
+template <int N, int KIND, int U, int W>
+__device__ __forceinline__ void cpml_zwarp(const Grid &g, const Fields &f, const Pieces &P, const Piece &p, int s,
+                                           int t, const int lo[3], const int hi[3])
+{
+    constexpr bool VK = KIND == kFV || KIND == kAV;
+    constexpr int O = VK ? 0 : -1;
+    constexpr int R = 3 - W;
+    constexpr int HL = N - 1 - O, HR = N + O, BW = 32 - HL - HR;
+    const int lane = t & 31;
+    int gw = t >> 5;
+    const int nz0 = (p.iv[0][1] + BW - 1) / BW, nz1 = (p.iv[0][3] + BW - 1) / BW;
+    const int nR = p.cnt[R];
+    const int cw0 = (p.iv[W][1] + U - 1) / U, cw1 = (p.iv[W][3] + U - 1) / U;
+    int zw = gw % (nz0 + nz1);
+    gw /= nz0 + nz1;
+    const int cr = gw % nR;
+    int ch = gw / nR;
+    if (ch >= cw0 + cw1) return;                                   // warp-uniform from here to the shuffles
+    int i[3];
+    i[R] = iv_map(p.iv[R], cr);
+    if (i[R] < lo[R] || i[R] > hi[R]) return;
+    const int zseg = zw < nz0 ? 0 : 1;
+    zw -= zseg ? nz0 : 0;
+    const int zs = p.iv[0][2 * zseg], ze = min(zs + p.iv[0][2 * zseg + 1] - 1, hi[0]);
+    const int z = zs + zw * BW + lane - HL;
+    const bool zown = lane >= HL && lane < 32 - HR && z <= ze && z >= lo[0];
+    const int wseg = ch < cw0 ? 0 : 1;
+    ch -= wseg ? cw0 : 0;
+    const int j0 = p.iv[W][2 * wseg] + ch * U;
+    const int jend = min(p.iv[W][2 * wseg] + p.iv[W][2 * wseg + 1] - 1, hi[W]);
+    const int zc = min(max(z, 0), g.ne[0] - 1);
+    i[0] = zc;
+    i[W] = j0;
+    const int k0 = gidx32(g, i[0], i[1], i[2]);
+    const CpmlAxis<KIND, W> xw(g, f, s, i);
+    float *ps = f.p + (long long)s * g.ntot;
+    // axis-0 arrays: the slab base moves with the node along W
+    const CpmlAxis<KIND, 0> xz(g, f, s, i);
+    const int sb0_step = W == 1 ? g.S : g.S * g.ne[1];
+    const bool s0 = xz.slab(g, zc);
+    const bool wband = cpml_in<KIND>(g, P, W, j0) || cpml_in<KIND>(g, P, W, j0 + U - 1);   // warp-uniform
+
+    // ---- phase 1: loads ----
+    float hz[U], win[U + 2 * N - 1];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        CpmlAxis<KIND, 0> xu = xz;
+        xu.sb += u * sb0_step;
+        hz[u] = xu.h(g, k0 + u * xw.st, zc, z);
+    }
+#pragma unroll
+    for (int q = 0; q < U + 2 * N - 1; q++) win[q] = (zown && wband) ? xw.h(g, k0, j0, j0 + O - N + 1 + q) : 0.0f;
+    CpmlOwn o0[U], oW[U];
+    float rho0[U], own_p[U], kap[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int j = j0 + u, k = k0 + u * xw.st;
+        const bool ok = zown && j <= jend && j >= lo[W];
+        rho0[u] = (VK && ok) ? g.rho[k] : 1.0f;
+        own_p[u] = (!VK && ok) ? ps[k] : 0.0f;
+        kap[u] = (!VK && ok) ? g.K[k] : 0.0f;
+        o0[u] = CpmlOwn{0.0f, 0.0f, 0.0f};
+        oW[u] = CpmlOwn{0.0f, 0.0f, 0.0f};
+        CpmlAxis<KIND, 0> xu = xz;
+        xu.sb += u * sb0_step;
+        if (ok) o0[u] = cpml_own(g, xu, zc, k, s0);
+        if (ok && wband && cpml_in<KIND>(g, P, W, j)) oW[u] = cpml_own(g, xw, j, k, xw.slab(g, j));
+    }
+
+    // ---- phase 2: compute and store ----
+    const bool inR = R < g.ndim && cpml_in<KIND>(g, P, R, i[R]);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int j = j0 + u, k = k0 + u * xw.st;
+        if (!(j <= jend && j >= lo[W])) continue;                 // warp-uniform
+        float Dz = 0.0f;
+#pragma unroll
+        for (int l = 1; l <= N; l++)
+            Dz += g.c[0][l - 1] * (__shfl_sync(0xffffffffu, hz[u], lane + O + l) -
+                                   __shfl_sync(0xffffffffu, hz[u], lane + O + 1 - l));
+        if (!zown) continue;
+        float acc = 0.0f;
+        CpmlAxis<KIND, 0> xu = xz;
+        xu.sb += u * sb0_step;
+        cpml_apply(g, xu, zc, k, s0, o0[u], rho0[u], own_p[u], Dz, acc);
+        if (wband && cpml_in<KIND>(g, P, W, j))
+            cpml_apply(g, xw, j, k, xw.slab(g, j), oW[u], rho0[u], own_p[u], cpml_d<N>(g, W, win + u), acc);
+        if (inR) {
+            int iu[3] = {i[0], i[1], i[2]};
+            iu[W] = j;
+            cpml_gather_term<N, KIND, R>(g, f, s, iu, k, rho0[u], own_p[u], acc);
+        }
+        if (KIND == kFP) ps[k] = own_p[u] - g.dt * kap[u] * acc;
+        if (KIND == kAP && acc != 0.0f) ps[k] = own_p[u] - g.dt * kap[u] * acc;
+    }
+}
+
+// Pieces of axis x and y (blockIdx.x over their blocks), one chunk a thread.
+template <int N, int KIND>
+__global__ void __launch_bounds__(256) k_cpml_xy(Grid g, Batch b, Fields f, Pieces P, int m)
+{
+    int blk = blockIdx.x;
+    int q = 1;
+    if (blk >= P.q[1].blocks) {
+        blk -= P.q[1].blocks;
+        q = 2;
+    }
+    const Piece &p = P.q[q];
+    const int s = blockIdx.y;
+    int lo[3], hi[3];
+    box_at((KIND == kFV || KIND == kFP) ? b.tab_src : b.tab_rec, b.nt1, s, m, lo, hi);
+    const int t = blk * 256 + (int)threadIdx.x;
+    if (q == 2) cpml_chunk<N, KIND, kCpmlChunk, 2>(g, f, P, p, s, t, lo, hi);
+    else cpml_chunk<N, KIND, kCpmlChunk, 1>(g, f, P, p, s, t, lo, hi);
+}
+
+// The z piece, one warp a line segment (W = y in 3D, x in 2D).
+template <int N, int KIND>
+__global__ void __launch_bounds__(256) k_cpml_z(Grid g, Batch b, Fields f, Pieces P, int m)
+{
+    const int s = blockIdx.y;
+    int lo[3], hi[3];
+    box_at((KIND == kFV || KIND == kFP) ? b.tab_src : b.tab_rec, b.nt1, s, m, lo, hi);
+    const int t = blockIdx.x * 256 + (int)threadIdx.x;
+    if (g.ndim == 3) cpml_zwarp<N, KIND, kCpmlChunkZ, 2>(g, f, P, P.q[0], s, t, lo, hi);
+    else cpml_zwarp<N, KIND, kCpmlChunkZ, 1>(g, f, P, P.q[0], s, t, lo, hi);
 }
 
 // ---------------------------------------------------------------------------
@@ -820,107 +1077,113 @@ void launch_recon_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f
     SMI_DISPATCH(k_recon_v, grid, g, b, f, it);
 }
 
-// Forward CPML over the slabs only (Sec. 2.1, Komatitsch & Martin CPML),
-// added to the interior update that the main kernels apply everywhere:
-//   V: psi_a <- Bv_a psi_a + Av_a D_a p;  v_a -= dt b_a psi_a
-//   P: psi_a <- Bp_a psi_a + Ap_a D_a v_a; p -= dt kappa psi_a
-// over the forward box (step it); nodes outside the axis-AX slab skip.
-template <int N, int AX>
-__global__ void __launch_bounds__(256) k_fcorr_v(Grid g, Batch b, Fields f, int it)
+// Pieces of the union of the bands (Sec. 2.1 CPML terms), clipped to the
+// box [lo, hi].  Axis a: band = [0, w_lo) u [ne - w_hi, ne), the rest is
+// "inner"; piece a = band of a x inner of every lower axis x box of every
+// higher axis.  Inactive axes hold the single node 0.
+Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, int w_hi)
 {
-    int s, i[3];
-    if (!corr_node<N, AX>(g, b, b.tab_src, it, s, i, g.nb + 1)) return;
-    const int ia = i[AX];
-    if (!in_slab(g, AX, ia)) return;
-    const long long k = gidx(g, i[0], i[1], i[2]), st = gstride(g, AX);
-    const float *p = f.p + s * g.ntot;
-    float D = 0.0f;
-#pragma unroll
-    for (int l = 1; l <= N; l++) {
-        const float pp = (ia + l < g.ne[AX]) ? p[k + l * st] : 0.0f;
-        const float pm = (ia - l + 1 >= 0) ? p[k - (l - 1) * st] : 0.0f;
-        D += g.c[AX][l - 1] * (pp - pm);
+    Pieces P{};
+    P.w_lo = w_lo;
+    P.w_hi = w_hi;
+    int band[3][4], inner[3][4], full[3][4];
+    auto clip = [](int x0, int x1, int l, int h, int *out) {
+        const int s = std::max(x0, l), e = std::min(x1, h);
+        out[0] = s;
+        out[1] = e >= s ? e - s + 1 : 0;
+    };
+    for (int a = 0; a < 3; a++) {
+        for (int k = 0; k < 4; k++) band[a][k] = inner[a][k] = full[a][k] = 0;
+        if (a >= g.ndim) {
+            inner[a][1] = full[a][1] = 1;
+            continue;
+        }
+        const int ne = g.ne[a];
+        clip(0, ne - 1, lo[a], hi[a], full[a]);
+        if (ne - w_hi <= w_lo) {              // the two bands meet: the whole axis
+            clip(0, ne - 1, lo[a], hi[a], band[a]);
+        } else {
+            clip(0, w_lo - 1, lo[a], hi[a], band[a]);
+            clip(ne - w_hi, ne - 1, lo[a], hi[a], band[a] + 2);
+            clip(w_lo, ne - w_hi - 1, lo[a], hi[a], inner[a]);
+        }
     }
-    long long sb, ss;
-    slab_base<AX>(g, i, sb, ss);
-    float *ps = f.psip[AX] + (long long)s * g.slab_n[AX] + sb + slab_j(g, AX, ia) * ss;
-    const float psi = g.cvb[AX][ia] * *ps + g.cva[AX][ia] * D;
-    *ps = psi;
-    f.v[AX][s * g.ntot + k] -= g.dt * buoyancy(g, AX, ia, k, g.rho[k]) * psi;
+    for (int a = 0; a < 3; a++) {
+        Piece &p = P.q[a];
+        p.axis = a;
+        long long cnt = a < g.ndim ? 1 : 0;
+        for (int b = 0; b < 3; b++) {
+            const int *src = b == a ? band[b] : (b < a ? inner[b] : full[b]);
+            for (int k = 0; k < 4; k++) p.iv[b][k] = src[k];
+            p.cnt[b] = src[1] + src[3];
+            cnt *= p.cnt[b];
+        }
+        if (cnt == 0) continue;
+        P.n++;
+        // threads: z piece one warp per line segment of BW nodes along z and
+        // kCpmlChunk nodes along W; x / y pieces one per chunk along x / y
+        const int w = (a == 1 || g.ndim == 2) ? 1 : 2, r = 3 - w, u = a == 0 ? kCpmlChunkZ : kCpmlChunk;
+        const long long chunks = (p.iv[w][1] + u - 1) / u + (p.iv[w][3] + u - 1) / u;
+        long long threads;
+        if (a == 0) {
+            const int bw = 32 - (2 * g.N - 1);
+            const long long zsegs = (p.iv[0][1] + bw - 1) / bw + (p.iv[0][3] + bw - 1) / bw;
+            threads = 32LL * zsegs * p.cnt[r] * chunks;
+        } else {
+            threads = (long long)p.cnt[0] * p.cnt[r] * chunks;
+        }
+        p.blocks = (int)((threads + 255) / 256);
+    }
+    return P;
 }
 
-template <int N, int AX>
-__global__ void __launch_bounds__(256) k_fcorr_p(Grid g, Batch b, Fields f, int it)
-{
-    int s, i[3];
-    if (!corr_node<N, AX>(g, b, b.tab_src, it, s, i, g.nb + 1)) return;
-    const int ia = i[AX];
-    if (!in_slab(g, AX, ia)) return;
-    const long long k = gidx(g, i[0], i[1], i[2]), st = gstride(g, AX);
-    const float *v = f.v[AX] + s * g.ntot;
-    float D = 0.0f;
-#pragma unroll
-    for (int l = 1; l <= N; l++) {
-        const float vp = (ia + l - 1 < g.ne[AX]) ? v[k + (l - 1) * st] : 0.0f;
-        const float vm = (ia - l >= 0) ? v[k - l * st] : 0.0f;
-        D += g.c[AX][l - 1] * (vp - vm);
-    }
-    long long sb, ss;
-    slab_base<AX>(g, i, sb, ss);
-    float *ps = f.psiv[AX] + (long long)s * g.slab_n[AX] + sb + slab_j(g, AX, ia) * ss;
-    const float psi = g.cpb[AX][ia] * *ps + g.cpa[AX][ia] * D;
-    *ps = psi;
-    f.p[s * g.ntot + k] -= g.dt * g.K[k] * psi;
-}
-
-template <int N, int AX>
-void corr_launch(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, int which)
-{
-    const int wl = which >= 3 ? g.nb + 1 : g.nb + N + 1;
-    dim3 grid(AX == 0 ? (2 * wl + 31) / 32 : (g.ne[0] + 31) / 32, AX == 1 ? (2 * wl + 7) / 8 : (g.ne[1] + 7) / 8,
-              (AX == 2 ? 2 * wl : g.ne[2]) * b.nshot);
-    dim3 block(32, 8);
-    if (which == 0) k_corr_v<N, AX><<<grid, block, 0, S(lc)>>>(g, b, f, m);
-    else if (which == 1) k_corr_phi<N, AX><<<grid, block, 0, S(lc)>>>(g, b, f, m);
-    else if (which == 2) k_corr_p<N, AX><<<grid, block, 0, S(lc)>>>(g, b, f, m);
-    else if (which == 3) k_fcorr_v<N, AX><<<grid, block, 0, S(lc)>>>(g, b, f, m);
-    else k_fcorr_p<N, AX><<<grid, block, 0, S(lc)>>>(g, b, f, m);
-    ++*lc.launches;
-}
+namespace {
 
 template <int N>
-void corr_axes(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, int which)
+void corr_launch(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, int kind,
+                 const int lo[3], const int hi[3])
 {
-    corr_launch<N, 0>(lc, g, b, f, m, which);
-    corr_launch<N, 1>(lc, g, b, f, m, which);
-    if (g.ndim == 3) corr_launch<N, 2>(lc, g, b, f, m, which);
+    // adjoint bands: nodes whose stencil reaches a slab node; forward: the slabs
+    const Pieces P = kind >= kAV ? make_pieces(g, lo, hi, g.nb + N, g.nb + N + 1) : make_pieces(g, lo, hi, g.nb, g.nb + 1);
+    // the z piece and the x / y pieces hold disjoint nodes: two launches in any order
+    const int bz = P.q[0].blocks, bxy = P.q[1].blocks + P.q[2].blocks;
+    if (bz > 0) {
+        dim3 grid(bz, b.nshot);
+        if (kind == kFV) k_cpml_z<N, kFV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+        else if (kind == kFP) k_cpml_z<N, kFP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+        else if (kind == kAV) k_cpml_z<N, kAV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+        else k_cpml_z<N, kAP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+        ++*lc.launches;
+    }
+    if (bxy > 0) {
+        dim3 grid(bxy, b.nshot);
+        if (kind == kFV) k_cpml_xy<N, kFV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+        else if (kind == kFP) k_cpml_xy<N, kFP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+        else if (kind == kAV) k_cpml_xy<N, kAV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+        else k_cpml_xy<N, kAP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+        ++*lc.launches;
+    }
 }
 
-void launch_adj_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, bool vel)
+void corr_dispatch(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, int kind,
+                   const int lo[3], const int hi[3])
 {
-    // velocity part: the axes touch disjoint arrays.  Pressure part: every
-    // phi update reads lp before any axis changes it, then one launch per
-    // axis (each updates lp).
-    if (vel) {
-        if (g.N == 2) corr_axes<2>(lc, g, b, f, m, 0);
-        else corr_axes<4>(lc, g, b, f, m, 0);
-        return;
-    }
-    if (g.N == 2) {
-        corr_axes<2>(lc, g, b, f, m, 1);
-        corr_axes<2>(lc, g, b, f, m, 2);
-    } else {
-        corr_axes<4>(lc, g, b, f, m, 1);
-        corr_axes<4>(lc, g, b, f, m, 2);
-    }
+    if (g.N == 2) corr_launch<2>(lc, g, b, f, m, kind, lo, hi);
+    else corr_launch<4>(lc, g, b, f, m, kind, lo, hi);
 }
 
-void launch_fwd_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, bool vel)
+}  // namespace
+
+void launch_adj_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, bool vel,
+                            const int lo[3], const int hi[3])
 {
-    // velocity: axes touch disjoint arrays; pressure: one launch per axis,
-    // each updating p in the slab of its axis
-    if (g.N == 2) corr_axes<2>(lc, g, b, f, it, vel ? 3 : 4);
-    else corr_axes<4>(lc, g, b, f, it, vel ? 3 : 4);
+    corr_dispatch(lc, g, b, f, m, vel ? kAV : kAP, lo, hi);
+}
+
+void launch_fwd_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, bool vel,
+                            const int lo[3], const int hi[3])
+{
+    corr_dispatch(lc, g, b, f, it, vel ? kFV : kFP, lo, hi);
 }
 
 void launch_inject_source(const LaunchCtx &lc, const Grid &g, const Batch &b, float *p,

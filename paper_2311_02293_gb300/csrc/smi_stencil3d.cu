@@ -856,7 +856,11 @@ void run_p(const LaunchCtx &lc, const Maps3 &m, const Maps3 *lpm, const Grid &g,
 
 }  // namespace
 
-bool stencil3d_supported(const Grid &g) { return g.ndim == 3 && (g.N == 2 || g.N == 4) && encoder() != nullptr; }
+// The 3D path indexes one shot's arrays with 32-bit offsets.
+bool stencil3d_supported(const Grid &g)
+{
+    return g.ndim == 3 && (g.N == 2 || g.N == 4) && g.ntot < (1LL << 31) && encoder() != nullptr;
+}
 
 bool make_maps3(Maps3 &m, const Grid &g, const Fields &f, int nshot)
 {
