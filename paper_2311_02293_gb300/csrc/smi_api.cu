@@ -315,6 +315,7 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
             for (int b = 0; b < 3; b++) c *= bd.hi[a][sd][b] - bd.lo[a][sd][b] + 1;
             bd.count += c;
         }
+    if (bd.count >= (1LL << 31)) return fail(SMI_ERR_UNSUPPORTED, "boundary bands of one step exceed 2^31 values");
     return SMI_OK;
 }
 

@@ -21,8 +21,14 @@ namespace smi {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kCpmlChunk = 4;      // nodes per thread along x / y, CPML kernels of the x / y pieces
-constexpr int kCpmlChunkZ = 2;     // nodes per lane along y (x in 2D), CPML kernel of the z piece
+#ifndef SMI_CPML_U
+#define SMI_CPML_U 4
+#endif
+#ifndef SMI_CPML_UZ
+#define SMI_CPML_UZ 2
+#endif
+constexpr int kCpmlChunk = SMI_CPML_U;     // nodes per thread along x / y, CPML kernels of the x / y pieces
+constexpr int kCpmlChunkZ = SMI_CPML_UZ;   // nodes per lane along y (x in 2D), CPML kernel of the z piece
 constexpr int kMaxBlocksX = 152 * 16;
 
 __device__ __forceinline__ long long gidx(const Grid &g, int i1, int i2, int i3)
@@ -812,80 +818,110 @@ __global__ void k_adj_inject(Grid g, Batch b, float *lp, const float *res, const
 }
 
 // ---------------------------------------------------------------------------
-// Boundary bands: value t of a step maps to (axis, side, node).
-__device__ __forceinline__ bool band_node(const Bands &bd, int ndim, long long t, int &a, int &sd,
-                                          int i[3])
-{
-    for (a = 0; a < ndim; a++)
-        for (sd = 0; sd < 2; sd++) {
-            const long long o = bd.off[a][sd];
-            const int *lo = bd.lo[a][sd], *hi = bd.hi[a][sd];
-            const long long w0 = hi[0] - lo[0] + 1, w1 = hi[1] - lo[1] + 1, w2 = hi[2] - lo[2] + 1;
-            const long long n = w0 * w1 * w2;
-            if (t >= o && t < o + n) {
-                const long long u = t - o;
-                i[0] = lo[0] + (int)(u % w0);
-                i[1] = lo[1] + (int)((u / w0) % w1);
-                i[2] = lo[2] + (int)(u / (w0 * w1));
-                return true;
-            }
-        }
-    return false;
-}
+// Boundary bands.  blockIdx.y = region r = 2 axis + side, blockIdx.z =
+// shot; a thread moves kBandVals values of the region (stride 256, all
+// loads issued before the stores).  One step of one shot holds fewer than
+// 2^31 values (checked at set-up), so offsets are 32-bit.
+constexpr int kBandVals = 4;
+
+struct BandRegion {
+    int a, sd, w0, w1, n, off;
+    const int *lo;
+    __device__ __forceinline__ BandRegion(const Bands &bd, int r)
+    {
+        a = r >> 1;
+        sd = r & 1;
+        lo = bd.lo[a][sd];
+        const int *hi = bd.hi[a][sd];
+        w0 = hi[0] - lo[0] + 1;
+        w1 = hi[1] - lo[1] + 1;
+        n = w0 * w1 * (hi[2] - lo[2] + 1);
+        off = (int)bd.off[a][sd];
+    }
+    // flat field index of value u of the region
+    __device__ __forceinline__ int node(const Grid &g, int u) const
+    {
+        const int q = u / w0;
+        return (lo[0] + u - q * w0) + g.px * ((lo[1] + q % w1) + g.ne[1] * (lo[2] + q / w1));
+    }
+};
 
 __global__ void k_band_absmax(Grid g, Fields f, Bands bd, unsigned *amax)
 {
-    const int s = blockIdx.y;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= bd.count) return;
-    int a, sd, i[3];
-    if (!band_node(bd, g.ndim, t, a, sd, i)) return;
-    const float v = fabsf(f.v[a][s * g.ntot + gidx(g, i[0], i[1], i[2])]);
-    atomicMax(amax + s * 6 + a * 2 + sd, __float_as_uint(v));
+    const BandRegion R(bd, blockIdx.y);
+    if (R.a >= g.ndim || R.n <= 0) return;
+    const int s = blockIdx.z;
+    const float *v = f.v[R.a] + (long long)s * g.ntot;
+    float m = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kBandVals; q++) {
+        const int u = (blockIdx.x * kBandVals + q) * blockDim.x + threadIdx.x;
+        if (u < R.n) m = fmaxf(m, fabsf(v[R.node(g, u)]));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(amax + s * 6 + blockIdx.y, __float_as_uint(m));
 }
 
 __global__ void k_band_save(Grid g, Fields f, Bands bd, int it, const unsigned *amax)
 {
-    const int s = blockIdx.y;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= bd.count) return;
-    int a, sd, i[3];
-    if (!band_node(bd, g.ndim, t, a, sd, i)) return;
-    const float v = f.v[a][s * g.ntot + gidx(g, i[0], i[1], i[2])];
-    const long long o = ((long long)s * bd.nt + it) * bd.count + t;
-    if (bd.prec == SMI_PREC_F32) {
-        static_cast<float *>(bd.data)[o] = v;
-        return;
+    const BandRegion R(bd, blockIdx.y);
+    if (R.a >= g.ndim || R.n <= 0) return;
+    const int s = blockIdx.z;
+    const float *v = f.v[R.a] + (long long)s * g.ntot;
+    const long long o0 = ((long long)s * bd.nt + it) * bd.count + R.off;
+    float x[kBandVals];
+#pragma unroll
+    for (int q = 0; q < kBandVals; q++) {
+        const int u = (blockIdx.x * kBandVals + q) * blockDim.x + threadIdx.x;
+        x[q] = u < R.n ? v[R.node(g, u)] : 0.0f;
     }
     // 16-bit storage scaled per (step, axis, side): the largest magnitude
     // maps to 2^14 (FP16) or 1 (BF16).
-    const float m = __uint_as_float(amax[s * 6 + a * 2 + sd]);
-    const float target = bd.prec == SMI_PREC_F16 ? 16384.0f : 1.0f;
-    const float scale = m > 0.0f ? m / target : 0.0f;
-    if (t == bd.off[a][sd]) bd.scale[((long long)s * bd.nt + it) * 6 + a * 2 + sd] = scale;
-    const float x = scale > 0.0f ? v / scale : 0.0f;
-    if (bd.prec == SMI_PREC_F16) static_cast<__half *>(bd.data)[o] = __float2half_rn(x);
-    else static_cast<__nv_bfloat16 *>(bd.data)[o] = __float2bfloat16_rn(x);
+    float inv = 1.0f;
+    if (bd.prec != SMI_PREC_F32) {
+        const float m = __uint_as_float(amax[s * 6 + blockIdx.y]);
+        const float scale = m > 0.0f ? m / (bd.prec == SMI_PREC_F16 ? 16384.0f : 1.0f) : 0.0f;
+        if (blockIdx.x == 0 && threadIdx.x == 0) bd.scale[((long long)s * bd.nt + it) * 6 + blockIdx.y] = scale;
+        inv = scale;
+    }
+#pragma unroll
+    for (int q = 0; q < kBandVals; q++) {
+        const int u = (blockIdx.x * kBandVals + q) * blockDim.x + threadIdx.x;
+        if (u >= R.n) continue;
+        if (bd.prec == SMI_PREC_F32) {
+            static_cast<float *>(bd.data)[o0 + u] = x[q];
+        } else {
+            const float y = inv > 0.0f ? x[q] / inv : 0.0f;
+            if (bd.prec == SMI_PREC_F16) static_cast<__half *>(bd.data)[o0 + u] = __float2half_rn(y);
+            else static_cast<__nv_bfloat16 *>(bd.data)[o0 + u] = __float2bfloat16_rn(y);
+        }
+    }
 }
 
 __global__ void k_band_restore(Grid g, Fields f, Bands bd, int it)
 {
-    const int s = blockIdx.y;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= bd.count) return;
-    int a, sd, i[3];
-    if (!band_node(bd, g.ndim, t, a, sd, i)) return;
-    const long long o = ((long long)s * bd.nt + it) * bd.count + t;
-    float v;
-    if (bd.prec == SMI_PREC_F32) {
-        v = static_cast<const float *>(bd.data)[o];
-    } else {
-        const float scale = bd.scale[((long long)s * bd.nt + it) * 6 + a * 2 + sd];
-        const float x = bd.prec == SMI_PREC_F16 ? __half2float(static_cast<const __half *>(bd.data)[o])
-                                                : __bfloat162float(static_cast<const __nv_bfloat16 *>(bd.data)[o]);
-        v = x * scale;
+    const BandRegion R(bd, blockIdx.y);
+    if (R.a >= g.ndim || R.n <= 0) return;
+    const int s = blockIdx.z;
+    float *v = f.v[R.a] + (long long)s * g.ntot;
+    const long long o0 = ((long long)s * bd.nt + it) * bd.count + R.off;
+    const float scale = bd.prec == SMI_PREC_F32 ? 1.0f : bd.scale[((long long)s * bd.nt + it) * 6 + blockIdx.y];
+    float x[kBandVals];
+#pragma unroll
+    for (int q = 0; q < kBandVals; q++) {
+        const int u = (blockIdx.x * kBandVals + q) * blockDim.x + threadIdx.x;
+        x[q] = 0.0f;
+        if (u < R.n) {
+            if (bd.prec == SMI_PREC_F32) x[q] = static_cast<const float *>(bd.data)[o0 + u];
+            else if (bd.prec == SMI_PREC_F16) x[q] = __half2float(static_cast<const __half *>(bd.data)[o0 + u]) * scale;
+            else x[q] = __bfloat162float(static_cast<const __nv_bfloat16 *>(bd.data)[o0 + u]) * scale;
+        }
     }
-    f.v[a][s * g.ntot + gidx(g, i[0], i[1], i[2])] = v;
+#pragma unroll
+    for (int q = 0; q < kBandVals; q++) {
+        const int u = (blockIdx.x * kBandVals + q) * blockDim.x + threadIdx.x;
+        if (u < R.n) v[R.node(g, u)] = x[q];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1211,10 +1247,23 @@ void launch_adj_inject(const LaunchCtx &lc, const Grid &g, const Batch &b, float
     ++*lc.launches;
 }
 
+// Band kernels: x = chunks of the largest region, y = region, z = shot.
+static dim3 band_grid(const Bands &bd, int nshot)
+{
+    long long nmax = 0;
+    for (int a = 0; a < 3; a++)
+        for (int sd = 0; sd < 2; sd++) {
+            long long n = 1;
+            for (int b = 0; b < 3; b++) n *= std::max(0, bd.hi[a][sd][b] - bd.lo[a][sd][b] + 1);
+            nmax = std::max(nmax, n);
+        }
+    return dim3((unsigned)std::max<long long>(1, (nmax + kThreads * kBandVals - 1) / (kThreads * kBandVals)), 6, nshot);
+}
+
 void launch_save_bands(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, Bands bd, int it,
                        unsigned *absmax_tmp)
 {
-    dim3 grid((unsigned)((bd.count + kThreads - 1) / kThreads), b.nshot);
+    const dim3 grid = band_grid(bd, b.nshot);
     if (bd.prec != SMI_PREC_F32) {
         cudaMemsetAsync(absmax_tmp, 0, sizeof(unsigned) * 6 * b.nshot, S(lc));
         k_band_absmax<<<grid, kThreads, 0, S(lc)>>>(g, f, bd, absmax_tmp);
@@ -1226,7 +1275,7 @@ void launch_save_bands(const LaunchCtx &lc, const Grid &g, const Batch &b, Field
 
 void launch_restore_bands(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, Bands bd, int it)
 {
-    dim3 grid((unsigned)((bd.count + kThreads - 1) / kThreads), b.nshot);
+    const dim3 grid = band_grid(bd, b.nshot);
     k_band_restore<<<grid, kThreads, 0, S(lc)>>>(g, f, bd, it);
     ++*lc.launches;
 }
