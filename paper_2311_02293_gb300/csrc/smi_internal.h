@@ -138,27 +138,29 @@ struct Piece {
     int iv[3][4];
     int cnt[3];
     int axis;              // the axis whose band defines the piece
-    int blocks;            // 256-thread blocks of this piece (per shot); 0: empty
+    int blocks;            // 256-thread blocks of this piece per chunk and shot; 0: empty
+    int chunks;            // chunks along the piece's walk axis
 };
 // Disjoint pieces covering the nodes within w_lo of the low end or w_hi of
-// the high end of some axis, clipped to a box (make_pieces); q[a] is the
-// piece of axis a.
+// the high end of axis z or x, clipped to a box (make_pieces); q[a] is the
+// piece of axis a (q[2] unused).
 struct Pieces {
     int n;                 // non-empty pieces
     int w_lo, w_hi;
     Piece q[3];
 };
 Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, int w_hi);
-// Transposed CPML terms of the adjoint over the slabs (vel: velocity part,
-// else pressure part), one launch over the union of the axes' bands within
-// the box [lo, hi] (union of the batch's receiver boxes after m reverse
-// steps); run before the interior kernels.
+// 3D only.  Transposed z and x CPML terms of the adjoint (vel: velocity
+// part, else pressure part, which also updates phi_y at its own nodes) over
+// the union of the z and x bands within the box [lo, hi] (union of the
+// batch's receiver boxes after m reverse steps); run before the main 3D
+// kernels, which apply the y terms.
 void launch_adj_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, bool vel,
                             const int lo[3], const int hi[3]);
-// Forward CPML memory-variable updates over the slabs (vel: velocity part,
-// else pressure part), one launch within the box [lo, hi] (union of the
-// batch's source boxes at step it); added to the interior update of the
-// main kernels.
+// 3D only.  Forward z and x CPML memory-variable updates over the slabs
+// (vel: velocity part, else pressure part) within the box [lo, hi] (union
+// of the batch's source boxes at step it); added to the update of the main
+// 3D kernels, which apply the y terms.
 void launch_fwd_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, bool vel,
                             const int lo[3], const int hi[3]);
 void launch_recon_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f,

@@ -27,8 +27,8 @@ constexpr int kThreads = 256;
 #ifndef SMI_CPML_UZ
 #define SMI_CPML_UZ 2
 #endif
-constexpr int kCpmlChunk = SMI_CPML_U;     // nodes per thread along x / y, CPML kernels of the x / y pieces
-constexpr int kCpmlChunkZ = SMI_CPML_UZ;   // nodes per lane along y (x in 2D), CPML kernel of the z piece
+constexpr int kCpmlChunk = SMI_CPML_U;     // nodes per thread along x, CPML kernel of the x piece
+constexpr int kCpmlChunkZ = SMI_CPML_UZ;   // nodes per lane along x, CPML kernel of the z piece
 constexpr int kMaxBlocksX = 152 * 16;
 
 __device__ __forceinline__ long long gidx(const Grid &g, int i1, int i2, int i3)
@@ -60,7 +60,7 @@ __device__ __forceinline__ long long slab_index(const Grid &g, int a, int i1, in
         return (long long)i1 + (long long)g.ne[0] * ((long long)js + (long long)g.S * i3);
     }
     int js = i3 < g.nb ? i3 : i3 - (g.ne[2] - 2 * g.nb - 1);
-    return (long long)i1 + (long long)g.ne[0] * ((long long)i2 + (long long)g.ne[1] * js);
+    return (long long)i1 + (long long)g.px * ((long long)i2 + (long long)g.ne[1] * js);
 }
 
 __device__ __forceinline__ float buoyancy(const Grid &g, int a, int ia, long long k, float rho0)
@@ -308,26 +308,25 @@ __global__ void __launch_bounds__(kThreads) k_adj_p(Grid g, Batch b, Fields f, i
 // h = p, v_a, Ap_a (lp + phi_a) or Av_a (lv_a + chi_a), zero outside the
 // grid (and, for the adjoint kinds, outside the slab).
 //
-// One launch per kind covers the union of the axes' bands (nodes within
-// w_lo of the low end or w_hi of the high end of an axis; forward: the
+// The main 3D kernels apply the y terms themselves (their register queue
+// along y holds the operand of D_y; see smi_stencil3d.cu).  The kernels here
+// cover the z and x terms over the union of the z and x bands (nodes within
+// w_lo of the low end or w_hi of the high end of the axis; forward: the
 // slabs; adjoint: every node whose stencil reaches a slab node), cut into
-// disjoint pieces clipped to the union of the batch's computing boxes (see
-// Pieces).  Each node belongs to one thread, which applies the terms of
-// every axis whose band holds it, so the kinds that update p / lp (read at
-// the node only) need no ordering between axes.  A thread takes a chunk of
-// consecutive nodes along x or y and issues all the chunk's loads before
-// its first store (the kernels are bound by memory latency, not bytes); a
-// warp holds consecutive z indices, so branches on the x and y bands are
-// warp-uniform.
+// two disjoint pieces clipped to the union of the batch's computing boxes
+// (see Pieces).  Each node belongs to one thread, which applies the terms of
+// both axes where both bands hold it, so the kinds that update p / lp (read
+// at the node only) need no ordering between axes.  A thread takes a chunk
+// of consecutive nodes along x and issues all the chunk's loads before its
+// first store (these kernels are bound by memory latency, not bytes).  The
+// adjoint phi_y update needs lp before the step, so the AP kernel makes it
+// at its own nodes of the y slab and the main pressure kernel at the rest.
 enum CpmlKind { kFV = 0, kFP = 1, kAV = 2, kAP = 3 };
 
 __device__ __forceinline__ bool in_band(const Grid &g, const Pieces &P, int a, int j)
 {
     return j < P.w_lo || j >= g.ne[a] - P.w_hi;
 }
-
-// js of node j of a CPML slab (slab arrays compress their axis to 2 nb + 1).
-__device__ __forceinline__ int slab_j(const Grid &g, int a, int j) { return j < g.nb ? j : j - (g.ne[a] - 2 * g.nb - 1); }
 
 // Offsets inside one shot's arrays are 32-bit: the 3D path requires a
 // field of one shot to hold fewer than 2^31 points.
@@ -339,7 +338,7 @@ __device__ __forceinline__ void slab_base(const Grid &g, int a, const int i[3], 
 {
     if (a == 0) { base = g.S * (i[1] + g.ne[1] * i[2]); stride = 1; }
     else if (a == 1) { base = i[0] + g.ne[0] * g.S * i[2]; stride = g.ne[0]; }
-    else { base = i[0] + g.ne[0] * i[1]; stride = g.ne[0] * g.ne[1]; }
+    else { base = i[0] + g.px * i[1]; stride = g.px * g.ne[1]; }
 }
 
 // Arrays of kind KIND along axis A for one shot.
@@ -447,61 +446,60 @@ __device__ __forceinline__ bool cpml_in(const Grid &g, const Pieces &P, int a, i
 
 __device__ __forceinline__ int iv_map(const int *iv, int c) { return c < iv[1] ? iv[0] + c : iv[2] + c - iv[1]; }
 
-// The axis-A terms of node i (flat k) from 2N gathered h values (corner
-// nodes whose other terms come from a window or from shuffles).
-template <int N, int KIND, int A>
-__device__ __forceinline__ void cpml_gather_term(const Grid &g, const Fields &f, int s, const int i[3], int k,
-                                                 float rho0, float lp0, float &acc)
-{
-    constexpr int O = CpmlAxis<KIND, A>::VK ? 0 : -1;
-    const CpmlAxis<KIND, A> x(g, f, s, i);
-    const int ia = i[A];
-    float w[2 * N];
-#pragma unroll
-    for (int q = 0; q < 2 * N; q++) w[q] = x.h(g, k, ia, ia + O - N + 1 + q);
-    const bool sl = x.slab(g, ia);
-    const CpmlOwn o = cpml_own(g, x, ia, k, sl);
-    cpml_apply(g, x, ia, k, sl, o, rho0, lp0, cpml_d<N>(g, A, w), acc);
-}
+// AP only: phi_y <- Bp_y (phi_y + lp) at nodes of the y slab, with lp
+// before this step (these kernels run before the main pressure kernel,
+// which makes the update at the y-slab nodes outside the z and x bands).
+struct CpmlPhiY {
+    float *ph;             // shot's phi_y slab array at node 0 of the chunk, or null
+    float B;
+    int step;              // offset between consecutive nodes of the chunk
+    __device__ __forceinline__ CpmlPhiY(const Grid &g, const Fields &f, int s, const int i[3], int step_)
+    {
+        ph = nullptr;
+        B = 0.0f;
+        step = step_;
+        const int y = i[2];
+        if (y < g.nb || y >= g.ne[2] - g.nb - 1) {
+            const int js = y < g.nb ? y : y - (g.ne[2] - 2 * g.nb - 1);
+            ph = f.psiv[2] + (long long)s * g.slab_n[2] + i[0] + g.px * (i[1] + g.ne[1] * js);
+            B = g.cpb[2][y];
+        }
+    }
+};
 
-// x / y pieces: a thread takes up to U consecutive nodes along the strided
-// axis W of one line (fixed z index i0 and index iR on the remaining axis
-// R); z is inner there, so no node has a z term.  Phase 1 issues every load
-// of the chunk: the window of h along W shared by the U nodes (U + 2N - 1
-// values instead of 2N per node) and the nodes' own values.  Phase 2
-// computes and stores.  Terms of axis R (corner nodes of the x piece) gather
-// their h in phase 2.
-template <int N, int KIND, int U, int W>
-__device__ __forceinline__ void cpml_chunk(const Grid &g, const Fields &f, const Pieces &P, const Piece &p, int s,
-                                           int t, const int lo[3], const int hi[3])
+// x piece: a thread takes up to U consecutive nodes along x of one line
+// (fixed z index i0 and y index i2); z is inner there, so the nodes have x
+// terms only.  Phase 1 issues every load of the chunk: the window of h
+// along x shared by the U nodes (U + 2N - 1 values instead of 2N per node)
+// and the nodes' own values.  Phase 2 computes and stores.
+template <int N, int KIND, int U>
+__device__ __forceinline__ void cpml_chunk(const Grid &g, const Fields &f, const Piece &p, int s, int c0, int cr,
+                                           int ch, const int lo[3], const int hi[3])
 {
+    constexpr int W = 1;
     constexpr bool VK = KIND == kFV || KIND == kAV;
     constexpr int O = VK ? 0 : -1;
-    constexpr int R = 3 - W;
-    const int n0 = p.cnt[0], nR = p.cnt[R];
     int i[3];
-    i[0] = iv_map(p.iv[0], t % n0);
-    t /= n0;
-    i[R] = iv_map(p.iv[R], t % nR);
-    int ch = t / nR;
-    const int c0 = (p.iv[W][1] + U - 1) / U, c1 = (p.iv[W][3] + U - 1) / U;
-    if (ch >= c0 + c1) return;
-    if (i[0] < lo[0] || i[0] > hi[0] || i[R] < lo[R] || i[R] > hi[R]) return;
-    const int seg = ch < c0 ? 0 : 1;
-    ch -= seg ? c0 : 0;
+    i[0] = iv_map(p.iv[0], c0);
+    i[2] = iv_map(p.iv[2], cr);
+    if (i[0] < lo[0] || i[0] > hi[0] || i[2] < lo[2] || i[2] > hi[2]) return;
+    const int nc0 = (p.iv[W][1] + U - 1) / U;
+    const int seg = ch < nc0 ? 0 : 1;
+    ch -= seg ? nc0 : 0;
     const int j0 = p.iv[W][2 * seg] + ch * U;
     const int jend = min(p.iv[W][2 * seg] + p.iv[W][2 * seg + 1] - 1, hi[W]);
     i[W] = j0;
     const int k0 = gidx32(g, i[0], i[1], i[2]);
     const CpmlAxis<KIND, W> x(g, f, s, i);
     float *ps = f.p + (long long)s * g.ntot;
+    const CpmlPhiY py(g, f, s, i, g.px);
 
     // ---- phase 1: loads ----
     float win[U + 2 * N - 1];
 #pragma unroll
     for (int q = 0; q < U + 2 * N - 1; q++) win[q] = x.h(g, k0, j0, j0 + O - N + 1 + q);
     CpmlOwn oW[U];
-    float rho0[U], own_p[U], kap[U];
+    float rho0[U], own_p[U], kap[U], phy[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
         const int j = j0 + u, k = k0 + u * x.st;
@@ -509,56 +507,45 @@ __device__ __forceinline__ void cpml_chunk(const Grid &g, const Fields &f, const
         rho0[u] = (VK && ok) ? g.rho[k] : 1.0f;
         own_p[u] = (!VK && ok) ? ps[k] : 0.0f;
         kap[u] = (!VK && ok) ? g.K[k] : 0.0f;
+        phy[u] = (KIND == kAP && ok && py.ph) ? py.ph[u * py.step] : 0.0f;
         oW[u] = CpmlOwn{0.0f, 0.0f, 0.0f};
         if (ok) oW[u] = cpml_own(g, x, j, k, x.slab(g, j));
     }
 
     // ---- phase 2: compute and store ----
-    const bool inR = R < g.ndim && cpml_in<KIND>(g, P, R, i[R]);
 #pragma unroll
     for (int u = 0; u < U; u++) {
         const int j = j0 + u, k = k0 + u * x.st;
         if (!(j <= jend && j >= lo[W])) continue;
         float acc = 0.0f;
         cpml_apply(g, x, j, k, x.slab(g, j), oW[u], rho0[u], own_p[u], cpml_d<N>(g, W, win + u), acc);
-        if (inR) {
-            int iu[3] = {i[0], i[1], i[2]};
-            iu[W] = j;
-            cpml_gather_term<N, KIND, R>(g, f, s, iu, k, rho0[u], own_p[u], acc);
-        }
         if (KIND == kFP) ps[k] = own_p[u] - g.dt * kap[u] * acc;
-        if (KIND == kAP && acc != 0.0f) ps[k] = own_p[u] - g.dt * kap[u] * acc;
+        if (KIND == kAP) {
+            if (py.ph) py.ph[u * py.step] = py.B * (phy[u] + own_p[u]);
+            if (acc != 0.0f) ps[k] = own_p[u] - g.dt * kap[u] * acc;
+        }
     }
 }
 
 // z piece: a warp takes one line segment along z (32 lanes = BW owned nodes
 // plus the 2N - 1 halo nodes of their stencils) times up to U consecutive
-// nodes along the strided axis W.  Each lane loads h along z at its own
-// position and the z derivatives come from warp shuffles; the W terms
-// (chunks that reach the W band) use a per-lane window along W, and the
-// terms of axis R (x in 3D) gather their h.  Control flow is warp-uniform
-// up to the shuffles.
-template <int N, int KIND, int U, int W>
+// nodes along x.  Each lane loads h along z at its own position and the z
+// derivatives come from warp shuffles; chunks that reach the x band also
+// load a per-lane window of h along x for the x terms.  Control flow is
+// warp-uniform up to the shuffles.
+template <int N, int KIND, int U>
 __device__ __forceinline__ void cpml_zwarp(const Grid &g, const Fields &f, const Pieces &P, const Piece &p, int s,
-                                           int t, const int lo[3], const int hi[3])
+                                           int lane, int zw, int cr, int ch, const int lo[3], const int hi[3])
 {
+    constexpr int W = 1;
     constexpr bool VK = KIND == kFV || KIND == kAV;
     constexpr int O = VK ? 0 : -1;
-    constexpr int R = 3 - W;
     constexpr int HL = N - 1 - O, HR = N + O, BW = 32 - HL - HR;
-    const int lane = t & 31;
-    int gw = t >> 5;
-    const int nz0 = (p.iv[0][1] + BW - 1) / BW, nz1 = (p.iv[0][3] + BW - 1) / BW;
-    const int nR = p.cnt[R];
-    const int cw0 = (p.iv[W][1] + U - 1) / U, cw1 = (p.iv[W][3] + U - 1) / U;
-    int zw = gw % (nz0 + nz1);
-    gw /= nz0 + nz1;
-    const int cr = gw % nR;
-    int ch = gw / nR;
-    if (ch >= cw0 + cw1) return;                                   // warp-uniform from here to the shuffles
-    int i[3];
-    i[R] = iv_map(p.iv[R], cr);
-    if (i[R] < lo[R] || i[R] > hi[R]) return;
+    const int nz0 = (p.iv[0][1] + BW - 1) / BW;
+    const int cw0 = (p.iv[W][1] + U - 1) / U;
+    int i[3];                                                      // warp-uniform from here to the shuffles
+    i[2] = iv_map(p.iv[2], cr);
+    if (i[2] < lo[2] || i[2] > hi[2]) return;
     const int zseg = zw < nz0 ? 0 : 1;
     zw -= zseg ? nz0 : 0;
     const int zs = p.iv[0][2 * zseg], ze = min(zs + p.iv[0][2 * zseg + 1] - 1, hi[0]);
@@ -574,24 +561,24 @@ __device__ __forceinline__ void cpml_zwarp(const Grid &g, const Fields &f, const
     const int k0 = gidx32(g, i[0], i[1], i[2]);
     const CpmlAxis<KIND, W> xw(g, f, s, i);
     float *ps = f.p + (long long)s * g.ntot;
-    // axis-0 arrays: the slab base moves with the node along W
+    // axis-0 arrays: the slab base moves by S per node along x
     const CpmlAxis<KIND, 0> xz(g, f, s, i);
-    const int sb0_step = W == 1 ? g.S : g.S * g.ne[1];
     const bool s0 = xz.slab(g, zc);
     const bool wband = cpml_in<KIND>(g, P, W, j0) || cpml_in<KIND>(g, P, W, j0 + U - 1);   // warp-uniform
+    const CpmlPhiY py(g, f, s, i, g.px);
 
     // ---- phase 1: loads ----
     float hz[U], win[U + 2 * N - 1];
 #pragma unroll
     for (int u = 0; u < U; u++) {
         CpmlAxis<KIND, 0> xu = xz;
-        xu.sb += u * sb0_step;
+        xu.sb += u * g.S;
         hz[u] = xu.h(g, k0 + u * xw.st, zc, z);
     }
 #pragma unroll
     for (int q = 0; q < U + 2 * N - 1; q++) win[q] = (zown && wband) ? xw.h(g, k0, j0, j0 + O - N + 1 + q) : 0.0f;
     CpmlOwn o0[U], oW[U];
-    float rho0[U], own_p[U], kap[U];
+    float rho0[U], own_p[U], kap[U], phy[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
         const int j = j0 + u, k = k0 + u * xw.st;
@@ -599,16 +586,16 @@ __device__ __forceinline__ void cpml_zwarp(const Grid &g, const Fields &f, const
         rho0[u] = (VK && ok) ? g.rho[k] : 1.0f;
         own_p[u] = (!VK && ok) ? ps[k] : 0.0f;
         kap[u] = (!VK && ok) ? g.K[k] : 0.0f;
+        phy[u] = (KIND == kAP && ok && py.ph) ? py.ph[u * py.step] : 0.0f;
         o0[u] = CpmlOwn{0.0f, 0.0f, 0.0f};
         oW[u] = CpmlOwn{0.0f, 0.0f, 0.0f};
         CpmlAxis<KIND, 0> xu = xz;
-        xu.sb += u * sb0_step;
+        xu.sb += u * g.S;
         if (ok) o0[u] = cpml_own(g, xu, zc, k, s0);
         if (ok && wband && cpml_in<KIND>(g, P, W, j)) oW[u] = cpml_own(g, xw, j, k, xw.slab(g, j));
     }
 
     // ---- phase 2: compute and store ----
-    const bool inR = R < g.ndim && cpml_in<KIND>(g, P, R, i[R]);
 #pragma unroll
     for (int u = 0; u < U; u++) {
         const int j = j0 + u, k = k0 + u * xw.st;
@@ -621,49 +608,49 @@ __device__ __forceinline__ void cpml_zwarp(const Grid &g, const Fields &f, const
         if (!zown) continue;
         float acc = 0.0f;
         CpmlAxis<KIND, 0> xu = xz;
-        xu.sb += u * sb0_step;
+        xu.sb += u * g.S;
         cpml_apply(g, xu, zc, k, s0, o0[u], rho0[u], own_p[u], Dz, acc);
         if (wband && cpml_in<KIND>(g, P, W, j))
             cpml_apply(g, xw, j, k, xw.slab(g, j), oW[u], rho0[u], own_p[u], cpml_d<N>(g, W, win + u), acc);
-        if (inR) {
-            int iu[3] = {i[0], i[1], i[2]};
-            iu[W] = j;
-            cpml_gather_term<N, KIND, R>(g, f, s, iu, k, rho0[u], own_p[u], acc);
-        }
         if (KIND == kFP) ps[k] = own_p[u] - g.dt * kap[u] * acc;
-        if (KIND == kAP && acc != 0.0f) ps[k] = own_p[u] - g.dt * kap[u] * acc;
+        if (KIND == kAP) {
+            if (py.ph) py.ph[u * py.step] = py.B * (phy[u] + own_p[u]);
+            if (acc != 0.0f) ps[k] = own_p[u] - g.dt * kap[u] * acc;
+        }
     }
 }
 
-// Pieces of axis x and y (blockIdx.x over their blocks), one chunk a thread.
+// x piece: block = 64 z indices x 4 y indices; blockIdx.y = chunk along x,
+// blockIdx.z = shot.
 template <int N, int KIND>
-__global__ void __launch_bounds__(256) k_cpml_xy(Grid g, Batch b, Fields f, Pieces P, int m)
+__global__ void __launch_bounds__(256) k_cpml_x(Grid g, Batch b, Fields f, Pieces P, int m)
 {
-    int blk = blockIdx.x;
-    int q = 1;
-    if (blk >= P.q[1].blocks) {
-        blk -= P.q[1].blocks;
-        q = 2;
-    }
-    const Piece &p = P.q[q];
-    const int s = blockIdx.y;
+    const Piece &p = P.q[1];
+    const int nbz = (p.cnt[0] + 63) >> 6;
+    const int bz = blockIdx.x % nbz, br = blockIdx.x / nbz;
+    const int c0 = bz * 64 + (threadIdx.x & 63), cr = br * 4 + (threadIdx.x >> 6);
+    if (c0 >= p.cnt[0] || cr >= p.cnt[2]) return;
+    const int s = blockIdx.z;
     int lo[3], hi[3];
     box_at((KIND == kFV || KIND == kFP) ? b.tab_src : b.tab_rec, b.nt1, s, m, lo, hi);
-    const int t = blk * 256 + (int)threadIdx.x;
-    if (q == 2) cpml_chunk<N, KIND, kCpmlChunk, 2>(g, f, P, p, s, t, lo, hi);
-    else cpml_chunk<N, KIND, kCpmlChunk, 1>(g, f, P, p, s, t, lo, hi);
+    cpml_chunk<N, KIND, kCpmlChunk>(g, f, p, s, c0, cr, blockIdx.y, lo, hi);
 }
 
-// The z piece, one warp a line segment (W = y in 3D, x in 2D).
+// z piece: 8 warps a block, warp -> (z segment, y index); blockIdx.y =
+// chunk along x, blockIdx.z = shot.
 template <int N, int KIND>
 __global__ void __launch_bounds__(256) k_cpml_z(Grid g, Batch b, Fields f, Pieces P, int m)
 {
-    const int s = blockIdx.y;
+    constexpr int BW = 32 - (2 * N - 1);     // owned lanes of a warp
+    const Piece &p = P.q[0];
+    const int nzw = (p.iv[0][1] + BW - 1) / BW + (p.iv[0][3] + BW - 1) / BW;
+    const int gw = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int zw = gw % nzw, cr = gw / nzw;
+    if (cr >= p.cnt[2]) return;                                   // warp-uniform
+    const int s = blockIdx.z;
     int lo[3], hi[3];
     box_at((KIND == kFV || KIND == kFP) ? b.tab_src : b.tab_rec, b.nt1, s, m, lo, hi);
-    const int t = blockIdx.x * 256 + (int)threadIdx.x;
-    if (g.ndim == 3) cpml_zwarp<N, KIND, kCpmlChunkZ, 2>(g, f, P, P.q[0], s, t, lo, hi);
-    else cpml_zwarp<N, KIND, kCpmlChunkZ, 1>(g, f, P, P.q[0], s, t, lo, hi);
+    cpml_zwarp<N, KIND, kCpmlChunkZ>(g, f, P, p, s, threadIdx.x & 31, zw, cr, blockIdx.y, lo, hi);
 }
 
 // ---------------------------------------------------------------------------
@@ -1130,10 +1117,6 @@ Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, in
     };
     for (int a = 0; a < 3; a++) {
         for (int k = 0; k < 4; k++) band[a][k] = inner[a][k] = full[a][k] = 0;
-        if (a >= g.ndim) {
-            inner[a][1] = full[a][1] = 1;
-            continue;
-        }
         const int ne = g.ne[a];
         clip(0, ne - 1, lo[a], hi[a], full[a]);
         if (ne - w_hi <= w_lo) {              // the two bands meet: the whole axis
@@ -1144,10 +1127,11 @@ Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, in
             clip(w_lo, ne - w_hi - 1, lo[a], hi[a], inner[a]);
         }
     }
-    for (int a = 0; a < 3; a++) {
+    // piece 0: z band x all x x all y; piece 1: x band x inner z x all y
+    for (int a = 0; a < 2; a++) {
         Piece &p = P.q[a];
         p.axis = a;
-        long long cnt = a < g.ndim ? 1 : 0;
+        long long cnt = 1;
         for (int b = 0; b < 3; b++) {
             const int *src = b == a ? band[b] : (b < a ? inner[b] : full[b]);
             for (int k = 0; k < 4; k++) p.iv[b][k] = src[k];
@@ -1156,19 +1140,17 @@ Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, in
         }
         if (cnt == 0) continue;
         P.n++;
-        // threads: z piece one warp per line segment of BW nodes along z and
-        // kCpmlChunk nodes along W; x / y pieces one per chunk along x / y
-        const int w = (a == 1 || g.ndim == 2) ? 1 : 2, r = 3 - w, u = a == 0 ? kCpmlChunkZ : kCpmlChunk;
-        const long long chunks = (p.iv[w][1] + u - 1) / u + (p.iv[w][3] + u - 1) / u;
-        long long threads;
+        // launch shape (k_cpml_z / k_cpml_x): y = chunks along x, x = z warps
+        // x y lines (z piece) or blocks of 64 z x 4 y lines (x piece)
+        const int u = a == 0 ? kCpmlChunkZ : kCpmlChunk;
+        p.chunks = (p.iv[1][1] + u - 1) / u + (p.iv[1][3] + u - 1) / u;
         if (a == 0) {
             const int bw = 32 - (2 * g.N - 1);
-            const long long zsegs = (p.iv[0][1] + bw - 1) / bw + (p.iv[0][3] + bw - 1) / bw;
-            threads = 32LL * zsegs * p.cnt[r] * chunks;
+            const long long zw = (p.iv[0][1] + bw - 1) / bw + (p.iv[0][3] + bw - 1) / bw;
+            p.blocks = (int)((zw * p.cnt[2] + 7) / 8);
         } else {
-            threads = (long long)p.cnt[0] * p.cnt[r] * chunks;
+            p.blocks = ((p.cnt[0] + 63) / 64) * ((p.cnt[2] + 3) / 4);
         }
-        p.blocks = (int)((threads + 255) / 256);
     }
     return P;
 }
@@ -1181,22 +1163,22 @@ void corr_launch(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, i
 {
     // adjoint bands: nodes whose stencil reaches a slab node; forward: the slabs
     const Pieces P = kind >= kAV ? make_pieces(g, lo, hi, g.nb + N, g.nb + N + 1) : make_pieces(g, lo, hi, g.nb, g.nb + 1);
-    // the z piece and the x / y pieces hold disjoint nodes: two launches in any order
-    const int bz = P.q[0].blocks, bxy = P.q[1].blocks + P.q[2].blocks;
-    if (bz > 0) {
-        dim3 grid(bz, b.nshot);
-        if (kind == kFV) k_cpml_z<N, kFV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-        else if (kind == kFP) k_cpml_z<N, kFP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-        else if (kind == kAV) k_cpml_z<N, kAV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-        else k_cpml_z<N, kAP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-        ++*lc.launches;
-    }
-    if (bxy > 0) {
-        dim3 grid(bxy, b.nshot);
-        if (kind == kFV) k_cpml_xy<N, kFV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-        else if (kind == kFP) k_cpml_xy<N, kFP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-        else if (kind == kAV) k_cpml_xy<N, kAV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-        else k_cpml_xy<N, kAP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+    // the two pieces hold disjoint nodes: launches in any order
+    for (int a = 0; a < 2; a++) {
+        const Piece &p = P.q[a];
+        if (p.blocks == 0 || p.chunks == 0) continue;
+        const dim3 grid(p.blocks, p.chunks, b.nshot);
+        if (a == 0) {
+            if (kind == kFV) k_cpml_z<N, kFV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+            else if (kind == kFP) k_cpml_z<N, kFP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+            else if (kind == kAV) k_cpml_z<N, kAV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+            else k_cpml_z<N, kAP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+        } else {
+            if (kind == kFV) k_cpml_x<N, kFV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+            else if (kind == kFP) k_cpml_x<N, kFP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+            else if (kind == kAV) k_cpml_x<N, kAV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+            else k_cpml_x<N, kAP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+        }
         ++*lc.launches;
     }
 }

@@ -128,8 +128,11 @@ void set_layout(Grid &g, const int n[3])
     g.ntot = (long long)g.px * g.ne[1] * g.ne[2];
     g.nphys = (long long)n[0] * n[1] * n[2];
     g.S = 2 * g.nb + 1;
-    const long long plane = (long long)g.ne[0] * g.ne[1] * g.ne[2];
-    for (int a = 0; a < 3; a++) g.slab_n[a] = a < g.ndim ? plane / g.ne[a] * g.S : 0;
+    // slab arrays compress their axis to S; the y slab (3D) keeps the padded
+    // row pitch px so that 4 consecutive z nodes form an aligned float4
+    g.slab_n[0] = (long long)g.S * g.ne[1] * g.ne[2];
+    g.slab_n[1] = (long long)g.ne[0] * g.S * g.ne[2];
+    g.slab_n[2] = g.ndim == 3 ? (long long)g.px * g.ne[1] * g.S : 0;
 }
 
 }  // namespace smi

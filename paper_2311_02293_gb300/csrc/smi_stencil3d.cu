@@ -45,6 +45,9 @@ namespace s3 {
 #ifndef SMI_MINB
 #define SMI_MINB 4
 #endif
+#ifndef SMI_YUNROLL
+#define SMI_YUNROLL 2        // y planes per unrolled group (divides 2N)
+#endif
 #ifndef SMI_WAVES
 #define SMI_WAVES 1
 #endif
@@ -129,19 +132,19 @@ __device__ __forceinline__ long long gidx(const Grid &g, int i1, int i2, int i3)
 {
     return (long long)i1 + (long long)g.px * ((long long)i2 + (long long)g.ne[1] * i3);
 }
-__device__ __forceinline__ bool slab(const Grid &g, int a, int j) { return j < g.nb || j >= g.ne[a] - g.nb - 1; }
-__device__ __forceinline__ long long slab_index(const Grid &g, int a, int i1, int i2, int i3)
+// y slab (Sec. 2.1 CPML): membership of plane y, and the offset of node
+// (oz, ox, y) in the y-slab arrays (row pitch px, so 4 consecutive z nodes
+// from a multiple of 4 form an aligned float4).
+__device__ __forceinline__ bool yslab(const Grid &g, int y) { return y < g.nb || y >= g.ne[2] - g.nb - 1; }
+__device__ __forceinline__ long long yslab_off(const Grid &g, int s, int oz, int ox, int y)
 {
-    if (a == 0) {
-        const int js = i1 < g.nb ? i1 : i1 - (g.ne[0] - 2 * g.nb - 1);
-        return (long long)js + (long long)g.S * ((long long)i2 + (long long)g.ne[1] * i3);
-    }
-    if (a == 1) {
-        const int js = i2 < g.nb ? i2 : i2 - (g.ne[1] - 2 * g.nb - 1);
-        return (long long)i1 + (long long)g.ne[0] * ((long long)js + (long long)g.S * i3);
-    }
-    const int js = i3 < g.nb ? i3 : i3 - (g.ne[2] - 2 * g.nb - 1);
-    return (long long)i1 + (long long)g.ne[0] * ((long long)i2 + (long long)g.ne[1] * js);
+    const int js = y < g.nb ? y : y - (g.ne[2] - 2 * g.nb - 1);
+    return (long long)s * g.slab_n[2] + oz + (long long)g.px * (ox + (long long)g.ne[1] * js);
+}
+__device__ __forceinline__ float4 ldg4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void stg4(float *p, const float (&a)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(a[0], a[1], a[2], a[3]);
 }
 
 // --- work decomposition ---------------------------------------------------
@@ -264,9 +267,9 @@ __device__ __forceinline__ void ring_drain(uint64_t *bars, int nslots, int bitba
 
 // Buoyancy on a half node: 2 / (rho_i + rho_{i+1}), 1/rho at the last node
 // (fast reciprocal-based division: a few ulp, far below the FP32 scheme error).
-// y-loop unrolled by the queue length M = 2N: step K of a group sees logical
-// queue entry l at physical index (l + K) % M, so the queue rotates by
-// renaming registers instead of moving them.
+// y-loop unrolled in groups of G planes: step K of a group sees logical
+// queue entry l at physical index (l + K) % 2N, so inside a group the queue
+// rotates by renaming registers; rotate_queue moves it back between groups.
 template <int K, int M> struct Unroll {
     template <class F> __device__ __forceinline__ static void run(F &f, int &y, int yb, const bool &stop)
     {
@@ -279,6 +282,24 @@ template <int K, int M> struct Unroll {
 template <int M> struct Unroll<M, M> {
     template <class F> __device__ __forceinline__ static void run(F &, int &, int, const bool &) {}
 };
+
+// After a group of G planes the logical entry l sits at (l + G) % L: move
+// it back to l so the next group starts at step 0 (fewer unrolled copies of
+// the loop body keep the code inside the instruction cache).
+template <int G, int L>
+__device__ __forceinline__ void rotate_queue(float (&q)[L][4])
+{
+    if (G % L == 0) return;
+    float t[L][4];
+#pragma unroll
+    for (int l = 0; l < L; l++)
+#pragma unroll
+        for (int r = 0; r < 4; r++) t[l][r] = q[(l + G) % L][r];
+#pragma unroll
+    for (int l = 0; l < L; l++)
+#pragma unroll
+        for (int r = 0; r < 4; r++) q[l][r] = t[l][r];
+}
 
 __device__ __forceinline__ float buoy(float r0, float r1, bool last)
 {
@@ -358,6 +379,19 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
             ok &= ring_wait(bar, S, 0, parity, hr, ya + l, ya);
             put(q[N - 1 + l], lds4(sm + ((l) % S) * Lay::SLOT + Lay::P_OFF + own));
         }
+        if (MODE == ADJ && mem && mx) {
+            // transposed y CPML: the queue holds lp + Ap_y (lp + phi_y) on y-slab planes
+#pragma unroll
+            for (int l = 0; l < 2 * N - 1; l++) {
+                const int yq = ya - N + 1 + l;
+                if (yq < 0 || yq >= g.ne[2] || !yslab(g, yq)) continue;
+                float ph[4];
+                put(ph, ldg4(f.psiv[2] + yslab_off(g, s, oz, ox, yq)));
+                const float A = g.cpa[2][yq];
+#pragma unroll
+                for (int r = 0; r < 4; r++) q[l][r] += A * (q[l][r] + ph[r]);
+            }
+        }
         if (__syncthreads_or(!ok)) goto timeout;
 
         {
@@ -368,6 +402,15 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
 #ifdef SMI_TIMING
             const long long tw0 = clock64();
 #endif
+            // y CPML operands, loaded before the waits: FWD psi_y, ADJ chi_y
+            // of plane y; ADJ phi_y of the plane entering the queue
+            const bool my = in_range(y, it.lo[2], it.hi[2]);
+            const bool ysl = MODE != REC && mem && mx && my && yslab(g, y);
+            const int ye = y + N;
+            const bool yent = MODE == ADJ && mem && mx && ye < g.ne[2] && yslab(g, ye);
+            float ym[4] = {0.f, 0.f, 0.f, 0.f}, yp[4] = {0.f, 0.f, 0.f, 0.f};
+            if (ysl) put(ym, ldg4(f.psip[2] + yslab_off(g, s, oz, ox, y)));
+            if (yent) put(yp, ldg4(f.psiv[2] + yslab_off(g, s, oz, ox, ye)));
             ok = ring_wait(bar, S, 0, parity, hr, y + N, ya);
             ok &= ring_wait(cbar, SC, 16, parity, cr, y, ya);
 #ifdef SMI_TIMING
@@ -378,7 +421,6 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
             const float *rt1 = sm + ((y + 1 - ya) % S) * Lay::SLOT + Lay::R_OFF;
             put(q[((2 * N - 1) + kq) % (2 * N)], lds4(sm + ((y + N - ya) % S) * Lay::SLOT + Lay::P_OFF + own));
             const float *cs = cbase + ((y - ya) % SC) * Lay::CSLOT + txi * TZ + 4 * tzi;
-            const bool my = in_range(y, it.lo[2], it.hi[2]);
             bool keep[4];
             if (MODE == REC) {
                 const bool kxy = in_range(ox, it.plo[1], it.phi[1]) && in_range(y, it.plo[2], it.phi[2]);
@@ -457,6 +499,14 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
             }
             // ---- y component ----
             {
+                if (yent) {                       // entering plane: lp + Ap_y (lp + phi_y)
+                    const float A = g.cpa[2][ye];
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        float &e = q[((2 * N - 1) + kq) % (2 * N)][r];
+                        e += A * (e + yp[r]);
+                    }
+                }
                 float ry[4], v[4];
                 put(ry, lds4(rt1 + txi * 36 + 4 * tzi));
                 put(v, lds4(cs + 2 * CORE));
@@ -467,6 +517,26 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
 #pragma unroll
                     for (int l = 1; l <= N; l++) d += g.c[2][l - 1] * (q[((N - 1 + l) + kq) % (2 * N)][r] - q[((N - l) + kq) % (2 * N)][r]);
                     D[r] = d;
+                }
+                if (ysl) {
+                    const long long yo = yslab_off(g, s, oz, ox, y);
+                    if (MODE == FWD) {            // psi_y <- Bv psi_y + Av D_y p;  v_y -= dt b (D_y p + psi_y)
+                        const float B = g.cvb[2][y], A = g.cva[2][y];
+#pragma unroll
+                        for (int r = 0; r < 4; r++) {
+                            const float ps = B * ym[r] + A * D[r];
+                            if (mz[r]) {
+                                ym[r] = ps;
+                                D[r] += ps;
+                            }
+                        }
+                    } else {                      // deferred chi_y <- Bv (chi_y + lv_y), lv_y before this step
+                        const float B = g.cvb[2][y];
+#pragma unroll
+                        for (int r = 0; r < 4; r++)
+                            if (mz[r]) ym[r] = B * (ym[r] + v[r]);
+                    }
+                    stg4(f.psip[2] + yo, ym);
                 }
                 const bool lasty = y + 1 >= g.ne[2];
                 const bool rym = MODE == REC && in_range(y, g.L[2] + N - 1, g.H[2] - N);
@@ -519,7 +589,11 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
             if (hr.issued < ylast) hr.issued++;
             if (cr.issued < yb) cr.issued++;
         };
-        while (y <= yb && !stop) Unroll<0, 2 * N>::run(body, y, yb, stop);
+        constexpr int G = (2 * N) % SMI_YUNROLL == 0 ? SMI_YUNROLL : 2 * N;
+        while (y <= yb && !stop) {
+            Unroll<0, G>::run(body, y, yb, stop);
+            rotate_queue<G>(q);
+        }
         if (stop) goto timeout;
         }
         continue;
@@ -613,6 +687,25 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
             ok &= ring_wait(bar, S, 0, parity, hr, ya + l, ya);
             put(q[N + l], lds4(sm + (l % S) * Lay::SLOT + Lay::Y_OFF + own));
         }
+        if (MODE == ADJ && mem && mx) {
+            // transposed y CPML: the queue holds lv_y + Av_y (lv_y + chi_y) on y-slab planes
+#pragma unroll
+            for (int l = 0; l < 2 * N - 1; l++) {
+                const int yq = ya - N + l;
+                if (yq < 0 || yq >= g.ne[2] || !yslab(g, yq)) continue;
+                float ch[4];
+                put(ch, ldg4(f.psip[2] + yslab_off(g, s, oz, ox, yq)));
+                const float A = g.cva[2][yq];
+#pragma unroll
+                for (int r = 0; r < 4; r++) q[l][r] += A * (q[l][r] + ch[r]);
+            }
+        }
+        // ADJ: nodes whose phi_y update the z / x CPML kernel makes (it reads
+        // lp before that kernel changes it): the adjoint z and x bands
+        bool zxb[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+            zxb[r] = oz + r < g.nb + N || oz + r >= g.ne[0] - g.nb - N - 1 || ox < g.nb + N || ox >= g.ne[1] - g.nb - N - 1;
         if (__syncthreads_or(!ok)) goto timeout;
 
         {
@@ -634,6 +727,15 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
 #ifdef SMI_TIMING
             const long long tw0 = clock64();
 #endif
+            // y CPML operands, loaded before the waits: FWD psi_vy, ADJ phi_y
+            // of plane y; ADJ chi_y of the plane entering the queue
+            const bool my = in_range(y, it.lo[2], it.hi[2]);
+            const bool ysl = MODE != REC && mem && mx && my && yslab(g, y);
+            const int ye = y + N - 1;
+            const bool yent = MODE == ADJ && mem && mx && ye < g.ne[2] && yslab(g, ye);
+            float ym[4] = {0.f, 0.f, 0.f, 0.f}, yc[4] = {0.f, 0.f, 0.f, 0.f};
+            if (ysl) put(ym, ldg4(f.psiv[2] + yslab_off(g, s, oz, ox, y)));
+            if (yent) put(yc, ldg4(f.psip[2] + yslab_off(g, s, oz, ox, ye)));
             ok = ring_wait(bar, S, 0, parity, hr, y + N - 1, ya);
             ok &= ring_wait(cbar, SC, 16, parity, cr, y, ya);
 #ifdef SMI_TIMING
@@ -642,7 +744,6 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
             put(q[((2 * N - 1) + kq) % (2 * N)], lds4(sm + ((y + N - 1 - ya) % S) * Lay::SLOT + Lay::Y_OFF + own));
             const float *slot = sm + ((y - ya) % S) * Lay::SLOT;
             const float *cs = cbase + ((y - ya) % SC) * Lay::CSLOT + own;
-            const bool my = in_range(y, it.lo[2], it.hi[2]);
             const bool act = mem && mx && my;
             float pv[4], Kv[4];
             put(pv, lds4(cs));
@@ -687,6 +788,14 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
             }
             // ---- y ----
             {
+                if (yent) {                       // entering plane: lv_y + Av_y (lv_y + chi_y)
+                    const float A = g.cva[2][ye];
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        float &e = q[((2 * N - 1) + kq) % (2 * N)][r];
+                        e += A * (e + yc[r]);
+                    }
+                }
                 float D[4];
 #pragma unroll
                 for (int r = 0; r < 4; r++) {
@@ -694,6 +803,25 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
 #pragma unroll
                     for (int l = 1; l <= N; l++) d += g.c[2][l - 1] * (q[((N + l - 1) + kq) % (2 * N)][r] - q[((N - l) + kq) % (2 * N)][r]);
                     D[r] = d;
+                }
+                if (ysl) {
+                    if (MODE == FWD) {            // psi_vy <- Bp psi_vy + Ap D_y v_y, added to div v
+                        const float B = g.cpb[2][y], A = g.cpa[2][y];
+#pragma unroll
+                        for (int r = 0; r < 4; r++) {
+                            const float ps = B * ym[r] + A * D[r];
+                            if (mz[r]) {
+                                ym[r] = ps;
+                                D[r] += ps;
+                            }
+                        }
+                    } else {                      // phi_y <- Bp (phi_y + lp), lp before this step
+                        const float B = g.cpb[2][y];
+#pragma unroll
+                        for (int r = 0; r < 4; r++)
+                            if (mz[r] && !zxb[r]) ym[r] = B * (ym[r] + pv[r]);
+                    }
+                    stg4(f.psiv[2] + yslab_off(g, s, oz, ox, y), ym);
                 }
 #pragma unroll
                 for (int r = 0; r < 4; r++) div[r] += D[r];
@@ -758,7 +886,11 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
             if (hr.issued < ylast) hr.issued++;
             if (cr.issued < yb) cr.issued++;
         };
-        while (y <= yb && !stop) Unroll<0, 2 * N>::run(body, y, yb, stop);
+        constexpr int G = (2 * N) % SMI_YUNROLL == 0 ? SMI_YUNROLL : 2 * N;
+        while (y <= yb && !stop) {
+            Unroll<0, G>::run(body, y, yb, stop);
+            rotate_queue<G>(q);
+        }
         if (stop) goto timeout;
         }
         continue;
