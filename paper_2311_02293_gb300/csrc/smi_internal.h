@@ -149,7 +149,8 @@ struct Pieces {
     int w_lo, w_hi;
     Piece q[3];
 };
-Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, int w_hi);
+// uz: nodes per lane along x in the z piece's kernel.
+Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, int w_hi, int uz);
 // 3D only.  Transposed z and x CPML terms of the adjoint (vel: velocity
 // part, else pressure part, which also updates phi_y at its own nodes) over
 // the union of the z and x bands within the box [lo, hi] (union of the

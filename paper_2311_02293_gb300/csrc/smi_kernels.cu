@@ -25,10 +25,10 @@ constexpr int kThreads = 256;
 #define SMI_CPML_U 4
 #endif
 #ifndef SMI_CPML_UZ
-#define SMI_CPML_UZ 2
+#define SMI_CPML_UZ 2        // adjoint kinds; the forward kinds take twice as many
 #endif
 constexpr int kCpmlChunk = SMI_CPML_U;     // nodes per thread along x, CPML kernel of the x piece
-constexpr int kCpmlChunkZ = SMI_CPML_UZ;   // nodes per lane along x, CPML kernel of the z piece
+constexpr int kCpmlChunkZ = SMI_CPML_UZ;   // nodes per lane along x, CPML kernel of the z piece (adjoint)
 constexpr int kMaxBlocksX = 152 * 16;
 
 __device__ __forceinline__ long long gidx(const Grid &g, int i1, int i2, int i3)
@@ -650,7 +650,8 @@ __global__ void __launch_bounds__(256) k_cpml_z(Grid g, Batch b, Fields f, Piece
     const int s = blockIdx.z;
     int lo[3], hi[3];
     box_at((KIND == kFV || KIND == kFP) ? b.tab_src : b.tab_rec, b.nt1, s, m, lo, hi);
-    cpml_zwarp<N, KIND, kCpmlChunkZ>(g, f, P, p, s, threadIdx.x & 31, zw, cr, blockIdx.y, lo, hi);
+    constexpr int UZ = (KIND == kFV || KIND == kFP) ? 2 * kCpmlChunkZ : kCpmlChunkZ;
+    cpml_zwarp<N, KIND, UZ>(g, f, P, p, s, threadIdx.x & 31, zw, cr, blockIdx.y, lo, hi);
 }
 
 // ---------------------------------------------------------------------------
@@ -1104,7 +1105,7 @@ void launch_recon_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f
 // box [lo, hi].  Axis a: band = [0, w_lo) u [ne - w_hi, ne), the rest is
 // "inner"; piece a = band of a x inner of every lower axis x box of every
 // higher axis.  Inactive axes hold the single node 0.
-Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, int w_hi)
+Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, int w_hi, int uz)
 {
     Pieces P{};
     P.w_lo = w_lo;
@@ -1142,7 +1143,7 @@ Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, in
         P.n++;
         // launch shape (k_cpml_z / k_cpml_x): y = chunks along x, x = z warps
         // x y lines (z piece) or blocks of 64 z x 4 y lines (x piece)
-        const int u = a == 0 ? kCpmlChunkZ : kCpmlChunk;
+        const int u = a == 0 ? uz : kCpmlChunk;
         p.chunks = (p.iv[1][1] + u - 1) / u + (p.iv[1][3] + u - 1) / u;
         if (a == 0) {
             const int bw = 32 - (2 * g.N - 1);
@@ -1162,7 +1163,8 @@ void corr_launch(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, i
                  const int lo[3], const int hi[3])
 {
     // adjoint bands: nodes whose stencil reaches a slab node; forward: the slabs
-    const Pieces P = kind >= kAV ? make_pieces(g, lo, hi, g.nb + N, g.nb + N + 1) : make_pieces(g, lo, hi, g.nb, g.nb + 1);
+    const Pieces P = kind >= kAV ? make_pieces(g, lo, hi, g.nb + N, g.nb + N + 1, kCpmlChunkZ)
+                                 : make_pieces(g, lo, hi, g.nb, g.nb + 1, 2 * kCpmlChunkZ);
     // the two pieces hold disjoint nodes: launches in any order
     for (int a = 0; a < 2; a++) {
         const Piece &p = P.q[a];
