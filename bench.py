@@ -35,6 +35,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "3D RTM grid-point updates/s (forward + adjoint + reconstruction, computing box)"
+# DRAM bytes moved per algorithmic byte of each stencil class (forward,
+# adjoint, reconstruction): ncu dram__bytes_read.sum + dram__bytes_write.sum
+# over the kernels of one forward and one reverse step of the 340^3 salt
+# case with the box off (`bench.py --profile rtm --nt 30 --no-box`).  A
+# bench launch's traffic is this ratio times its algorithmic bytes.
+TRAFFIC_PER_ALGO_BYTE = (1.509, 1.580, 1.441)
 UNIT = "Gpt-updates/s"
 WORKLOAD = "3d_rtm_salt_300^3_order8_nt2500_8shots_150x150rec"
 
@@ -54,6 +60,11 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-scale", type=float, default=0.5,
                     help="grid sizes and nt of the serving mix relative to the full mix")
+    ap.add_argument("--profile", choices=["fwd", "rtm"],
+                    help="profiling case instead: one untimed forward call (observed data), then one forward "
+                         "or RTM call of a one-shot salt model, printing per-class times")
+    ap.add_argument("--n", type=int, default=300, help="physical grid size of the profiling case (n^3)")
+    ap.add_argument("--no-box", action="store_true", help="profiling case without the computing box")
     return ap.parse_args()
 
 
@@ -260,7 +271,8 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = by[dom] / (ms[dom] / 1e3) / 1e9 if ms[dom] > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak if achieved else None, "traffic": None,
+            "frac": achieved / peak if achieved else None,
+            "traffic": float(TRAFFIC_PER_ALGO_BYTE[dom] * by[dom] / max(steps_cls[dom], 1)),
             "kernel": names[dom], "peak_source": peak_kind,
             "per_class_gbs": {names[c]: (by[c] / (ms[c] / 1e3) / 1e9 if ms[c] > 0 else None) for c in range(3)},
             "per_class_share": {names[c]: float(ms[c] / max(ms.sum(), 1e-9)) for c in range(3)},
@@ -307,6 +319,36 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile(args):
+    """The case the ncu summaries under profiles/ capture: one shot of the
+    salt model at n^3, one untimed forward call to make the observed data,
+    then one forward (fwd) or RTM (rtm) call; prints per-class times and
+    algorithmic bandwidths from the library's own CUDA events."""
+    import torch
+    from paper_2311_02293_gb300 import build, synth
+    if not os.path.exists(os.path.join(ROOT, "paper_2311_02293_gb300", "libsmi.so")):
+        build.build()
+    from paper_2311_02293_gb300 import smi
+    dev = torch.device("cuda:0")
+    w = synth.salt_3d(n=args.n, nt=args.nt, nshot=1)
+    vp, rho, stf = (torch.from_numpy(a).to(dev) for a in (w.vp, w.rho, w.stf))
+    prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, profile=True, use_box=not args.no_box)
+    seis = smi.smi_forward(vp, rho, prob, w.srcs, w.recs, stf)
+    torch.cuda.synchronize()
+    if args.profile == "fwd":
+        smi.smi_forward(vp, rho, prob, w.srcs, w.recs, stf)
+    else:
+        smi.smi_rtm(vp, rho, prob, w.srcs, w.recs, stf, seis[0])
+    torch.cuda.synchronize()
+    st = smi.smi_last_stats()
+    names = ["forward", "adjoint", "reconstruction"]
+    print(json.dumps({"profile": args.profile, "n": args.n, "nt": args.nt, "box": not args.no_box,
+                      "ms": dict(zip(names, st["ms"])),
+                      "algorithmic_gbs": {c: (b / (m * 1e6) if m else None)
+                                          for c, b, m in zip(names, st["bytes"], st["ms"])},
+                      "kernel_launches": st["kernel_launches"]}), flush=True)
+
+
 def run_serve(args):
     """Serving mix: one-at-a-time plain FP32 calls vs the request server (FP16
     boundaries, 4 slots) under Poisson arrivals at 1.2x and 0.5x the measured
@@ -345,7 +387,9 @@ def run_serve(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.serve:
+    if a.profile:
+        run_profile(a)
+    elif a.serve:
         run_serve(a)
     elif a.impl == "reference":
         run_reference(a)
