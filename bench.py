@@ -338,15 +338,22 @@ def run_profile(args):
     if args.profile == "fwd":
         smi.smi_forward(vp, rho, prob, w.srcs, w.recs, stf)
     else:
-        smi.smi_rtm(vp, rho, prob, w.srcs, w.recs, stf, seis[0])
+        img = smi.smi_rtm(vp, rho, prob, w.srcs, w.recs, stf, seis[0])
     torch.cuda.synchronize()
     st = smi.smi_last_stats()
     names = ["forward", "adjoint", "reconstruction"]
-    print(json.dumps({"profile": args.profile, "n": args.n, "nt": args.nt, "box": not args.no_box,
-                      "ms": dict(zip(names, st["ms"])),
-                      "algorithmic_gbs": {c: (b / (m * 1e6) if m else None)
-                                          for c, b, m in zip(names, st["bytes"], st["ms"])},
-                      "kernel_launches": st["kernel_launches"]}), flush=True)
+    line = {"profile": args.profile, "n": args.n, "nt": args.nt, "box": not args.no_box,
+            "ms": dict(zip(names, st["ms"])),
+            "algorithmic_gbs": {c: (b / (m * 1e6) if m else None) for c, b, m in zip(names, st["bytes"], st["ms"])},
+            "kernel_launches": st["kernel_launches"]}
+    if args.profile == "rtm" and args.shell != "f32":
+        # the image with 16-bit boundary storage against FP32 storage
+        p16 = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, use_box=not args.no_box,
+                          shell_prec=args.shell)
+        i16 = smi.smi_rtm(vp, rho, p16, w.srcs, w.recs, stf, seis[0])
+        line["shell"] = args.shell
+        line["image_rel_l2_vs_f32_shells"] = float(torch.linalg.norm(i16 - img) / torch.linalg.norm(img))
+    print(json.dumps(line), flush=True)
 
 
 def run_serve(args):
