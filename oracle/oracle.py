@@ -63,6 +63,7 @@ class _Par(ctypes.Structure):
         ("use_box", ctypes.c_int),
         ("periodic", ctypes.c_int),
         ("nthreads", ctypes.c_int),
+        ("dr", ctypes.c_int),
     ]
 
 
@@ -81,6 +82,7 @@ class Problem:
     use_box: bool = True
     periodic: bool = False
     nthreads: int = 0
+    dr: int = 1         # boundary decimation ratio (Sec. 4.2)
 
     @property
     def ndim(self) -> int:
@@ -100,7 +102,7 @@ class Problem:
         d = list(self.d) + [1.0] * (3 - len(self.d))
         return _Par(self.ndim, n[0], n[1], n[2], d[0], d[1], d[2], self.order, self.nb,
                     self.nt, self.dt, self.fm, self.kaiser_b, self.cpml_R, int(self.use_box),
-                    int(self.periodic), self.nthreads)
+                    int(self.periodic), self.nthreads, self.dr)
 
 
 _lib = None

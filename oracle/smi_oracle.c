@@ -58,6 +58,7 @@ typedef struct {
     int use_box;          /* dynamic computing box on/off (Sec. 4.1) */
     int periodic;         /* tests only: periodic wrap instead of zero reads */
     int nthreads;         /* OpenMP threads, 0 = library default */
+    int dr;               /* boundary decimation ratio (Sec. 4.2); 1 = every step */
 } orc_par;
 
 #define MAXN 8
@@ -70,7 +71,7 @@ typedef struct {
     long ntot;
     double d[3], dt, dV;
     double a[MAXN];       /* FD coefficients a_1..a_N stored at a[0..N-1] */
-    int periodic, use_box, nt;
+    int periodic, use_box, nt, dr;
     double vmax, vmin;
     double *K;            /* bulk modulus at p nodes */
     double *bu[3];        /* buoyancy at v_a nodes */
@@ -225,6 +226,8 @@ static int grid_init(grid_t *g, const orc_par *par, const double *vp, const doub
     g->use_box = par->use_box;
     g->nt = par->nt;
     g->dt = par->dt;
+    if (par->dr < 0) return ORC_ERR_ARG;
+    g->dr = par->dr > 1 ? par->dr : 1;
     int n[3] = {par->n1, par->n2, par->ndim == 3 ? par->n3 : 1};
     double d[3] = {par->d1, par->d2, par->ndim == 3 ? par->d3 : 1.0};
     g->dV = 1.0;
@@ -253,6 +256,10 @@ static int grid_init(grid_t *g, const orc_par *par, const double *vp, const doub
     for (int a = 0; a < g->ndim; a++) s2 += 1.0 / (d[a] * d[a]);
     for (int l = 0; l < g->N; l++) sa += fabs(g->a[l]);
     if (g->dt * g->vmax * sqrt(s2) * sa > 1.0) return ORC_ERR_CFL;
+    /* Boundary decimation (Sec. 4.2): the paper's dr = 5 vmax / vmin, read
+     * as the largest ratio that keeps the stored boundary above its Nyquist
+     * rate. */
+    if (g->dr > 1 && (double)g->dr > 5.0 * g->vmax / g->vmin) return ORC_ERR_ARG;
     /* Dispersion (Sec. 3.8; threshold is a reading): shortest wavelength
      * vmin / (2.5 fm) must span >= 5 cells at order 4, >= 4 cells at order 8. */
     if (par->fm > 0.0 && g->N >= 2) {
@@ -595,7 +602,7 @@ static void stencil_extent(const stencil_t *st, int n, int lo[3], int hi[3])
 }
 
 /* ---------------------------------------------------------------------- */
-/* Boundary bands for source-field reconstruction (Sec. 4.2, dr = 1).
+/* Boundary bands for source-field reconstruction (Sec. 4.2).
  * Reading of the band layout: for each axis a, the face-normal velocity v_a
  * on the 2N-1 half nodes straddling each face of the physical domain,
  * [L-N, L+N-2] and [H-N+1, H+N-1] along a, over the physical cross-section.
@@ -630,6 +637,67 @@ static void band_copy(const grid_t *g, double *const v[3], double *buf, int rest
             }
         }
     }
+}
+
+/* Decimated boundary saving (Sec. 4.2).  The band of step k*dr is stored
+ * for k = 0..nsamp-1 and the band of any step is interpolated from the
+ * stored samples in time with a Kaiser-windowed sinc (the window family the
+ * paper uses for sources and receivers, Hicks 2002) of radius TIME_R = 8
+ * samples and shape TIME_B = 8.  Readings: the interpolator (the paper
+ * names none; this one keeps the error of a sinusoid at or below 1.5e-4 up to
+ * 0.3 cycles a sample, the band that the dr rule below admits), and a
+ * forward run that continues past nt-1 without a source up to step
+ * (nsamp-1)*dr, so that every step it < nt has all 2 TIME_R samples of its
+ * window.  A step on a stored sample gets it exactly (sinc vanishes at the
+ * other samples), so dr = 1 stores every step and needs no continuation. */
+#define TIME_R 8
+#define TIME_B 8.0
+static int band_samples(const grid_t *g)
+{
+    return g->dr == 1 ? g->nt : (g->nt - 1) / g->dr + TIME_R + 1;
+}
+
+/* Band of step it from the stored samples into out[nband]. */
+static void band_at(const grid_t *g, const double *bands, long nband, int nsamp, int it, double *out)
+{
+    if (g->dr == 1) {
+        memcpy(out, bands + nband * (long)it, sizeof(double) * nband);
+        return;
+    }
+    int first;
+    double w[2 * TIME_R];
+    orc_kaiser_1d((double)it / (double)g->dr, TIME_R, TIME_B, &first, w);
+    for (long c = 0; c < nband; c++) out[c] = 0.0;
+    for (int q = 0; q < 2 * TIME_R; q++) {
+        int k = first + q;
+        if (k < 0 || k >= nsamp || w[q] == 0.0) continue;   /* before step 0 the field is zero */
+        const double *b = bands + nband * (long)k;
+        for (long c = 0; c < nband; c++) out[c] += w[q] * b[c];
+    }
+}
+
+/* dr > 1: continue the forward run (no source) from step nt to step
+ * (nsamp-1)*dr, storing the bands of the multiples of dr, then put p and v
+ * back to their state after step nt-1. */
+static int forward_continue(const grid_t *g, state_t *s, const int slo[3], const int shi[3], double *bands,
+                            long nband, int nsamp)
+{
+    if (g->dr == 1) return ORC_OK;
+    double *keep = malloc(sizeof(double) * g->ntot * (1 + g->ndim));
+    if (!keep) return ORC_ERR_NOMEM;
+    memcpy(keep, s->p, sizeof(double) * g->ntot);
+    for (int a = 0; a < g->ndim; a++) memcpy(keep + g->ntot * (1 + a), s->v[a], sizeof(double) * g->ntot);
+    for (int it = g->nt; it <= (nsamp - 1) * g->dr; it++) {
+        if (it % g->dr == 0) band_copy(g, s->v, bands + nband * (long)(it / g->dr), 0);
+        int lo[3], hi[3];
+        box_at(g, slo, shi, it, lo, hi);
+        update_v(g, s, lo, hi);
+        update_p(g, s, lo, hi);
+    }
+    memcpy(s->p, keep, sizeof(double) * g->ntot);
+    for (int a = 0; a < g->ndim; a++) memcpy(s->v[a], keep + g->ntot * (1 + a), sizeof(double) * g->ntot);
+    free(keep);
+    return ORC_OK;
 }
 
 /* One reverse step of the source field (Algorithm 2: remove source,
@@ -807,7 +875,8 @@ int orc_adjoint(const orc_par *par, const double *vp, const double *rho, const d
  *           (Eq. rtmimage).
  * pbar(it) is the adjoint of p^{it+1} after the receivers of step it have
  * been injected.  recon = 1 rebuilds the source field backwards from the
- * saved boundary bands (Sec. 4.2, dr = 1); recon = 0 keeps every forward
+ * saved boundary bands (Sec. 4.2, every dr-th step, interpolated in time
+ * when dr > 1); recon = 0 keeps every forward
  * state in memory (small grids only; tests).  The adjoint field uses the
  * receiver box when use_box is set (Sec. 4.1).
  * seis (optional): the forward seismograms [nt][nrec]. */
@@ -831,10 +900,12 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
     if (!rc) rc = state_alloc(&g, &s);
     if (!rc) rc = state_alloc(&g, &ad);
     long nband = band_count(&g);
-    double *bands = NULL, *store_p = NULL, *store_v[3] = {0};
+    const int nsamp = band_samples(&g);
+    double *bands = NULL, *bandt = NULL, *store_p = NULL, *store_v[3] = {0};
     if (!rc && recon) {
-        bands = malloc(sizeof(double) * (nband * (long)g.nt + 1));
-        if (!bands) rc = ORC_ERR_NOMEM;
+        bands = malloc(sizeof(double) * (nband * (long)nsamp + 1));
+        bandt = malloc(sizeof(double) * (nband + 1));
+        if (!bands || !bandt) rc = ORC_ERR_NOMEM;
     }
     if (!rc && !recon) {
         store_p = malloc(sizeof(double) * g.ntot * (long)g.nt);
@@ -851,7 +922,7 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
     stencil_extent(rst, nrec, rlo, rhi);
     /* forward loop */
     for (int it = 0; it < g.nt; it++) {
-        if (recon) band_copy(&g, s.v, bands + nband * (long)it, 0);
+        if (recon && it % g.dr == 0) band_copy(&g, s.v, bands + nband * (long)(it / g.dr), 0);
         int lo[3], hi[3];
         box_at(&g, slo, shi, it, lo, hi);
         update_v(&g, &s, lo, hi);
@@ -864,6 +935,7 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
                 memcpy(store_v[a] + g.ntot * (long)it, s.v[a], sizeof(double) * g.ntot);
         }
     }
+    if (recon && (rc = forward_continue(&g, &s, slo, shi, bands, nband, nsamp))) goto done;
     /* residual and misfit */
     double J = 0.0;
     for (long k = 0; k < (long)g.nt * nrec; k++) {
@@ -908,9 +980,10 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
         else full_box(&g, lo, hi);
         adjoint_update_p(&g, &ad, lo, hi);
         adjoint_update_v(&g, &ad, lo, hi);
-        if (recon)
-            reconstruct_step(&g, &s, &sst, g.dt * stf[it] / g.dV, box, prev,
-                             bands + nband * (long)it);
+        if (recon) {
+            band_at(&g, bands, nband, nsamp, it, bandt);
+            reconstruct_step(&g, &s, &sst, g.dt * stf[it] / g.dV, box, prev, bandt);
+        }
     }
     {
         long c = 0;
@@ -930,6 +1003,7 @@ done:
     state_free(&s);
     state_free(&ad);
     free(bands);
+    free(bandt);
     free(store_p);
     for (int a = 0; a < 3; a++) free(store_v[a]);
     free(acc);
@@ -955,25 +1029,29 @@ int orc_reconstruct(const orc_par *par, const double *vp, const double *rho, con
     memset(&s, 0, sizeof s);
     if (!rc) rc = state_alloc(&g, &s);
     long nband = band_count(&g);
-    double *bands = rc ? NULL : malloc(sizeof(double) * (nband * (long)g.nt + 1));
-    if (!rc && !bands) rc = ORC_ERR_NOMEM;
-    if (rc) { state_free(&s); grid_free(&g); return rc; }
+    const int nsamp = band_samples(&g);
+    double *bands = rc ? NULL : malloc(sizeof(double) * (nband * (long)nsamp + 1));
+    double *bandt = rc ? NULL : malloc(sizeof(double) * (nband + 1));
+    if (!rc && (!bands || !bandt)) rc = ORC_ERR_NOMEM;
     int slo[3], shi[3];
     stencil_extent(&sst, 1, slo, shi);
-    for (int it = 0; it < g.nt; it++) {
-        band_copy(&g, s.v, bands + nband * (long)it, 0);
+    for (int it = 0; it < g.nt && !rc; it++) {
+        if (it % g.dr == 0) band_copy(&g, s.v, bands + nband * (long)(it / g.dr), 0);
         int lo[3], hi[3];
         box_at(&g, slo, shi, it, lo, hi);
         update_v(&g, &s, lo, hi);
         update_p(&g, &s, lo, hi);
         stencil_add(&g, s.p, &sst, g.dt * stf[it] / g.dV);
     }
+    if (!rc) rc = forward_continue(&g, &s, slo, shi, bands, nband, nsamp);
+    if (rc) { free(bands); free(bandt); state_free(&s); grid_free(&g); return rc; }
     long nphys = (long)(g.H[0] - g.L[0] + 1) * (g.H[1] - g.L[1] + 1) * (g.H[2] - g.L[2] + 1);
     for (int it = g.nt - 1; it >= 0; it--) {
         int box[2][3], prev[2][3];
         box_at(&g, slo, shi, it, box[0], box[1]);
         box_at(&g, slo, shi, it - 1, prev[0], prev[1]);
-        reconstruct_step(&g, &s, &sst, g.dt * stf[it] / g.dV, box, prev, bands + nband * (long)it);
+        band_at(&g, bands, nband, nsamp, it, bandt);
+        reconstruct_step(&g, &s, &sst, g.dt * stf[it] / g.dV, box, prev, bandt);
         long c = 0;
         for (int i3 = g.L[2]; i3 <= g.H[2]; i3++)
         for (int i2 = g.L[1]; i2 <= g.H[1]; i2++)
@@ -981,6 +1059,7 @@ int orc_reconstruct(const orc_par *par, const double *vp, const double *rho, con
             prec[(long)it * nphys + c++] = s.p[IDX(&g, i1, i2, i3)];
     }
     free(bands);
+    free(bandt);
     state_free(&s);
     grid_free(&g);
     return ORC_OK;
