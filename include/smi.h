@@ -15,7 +15,9 @@
  *                    discrete gradient with respect to Vp (Eq.
  *                    gradrhokappa via kappa = rho Vp^2), Algorithm 2, with
  *                    the source field rebuilt backwards from saved
- *                    boundaries (Sec. 4.2, dr = 1).
+ *                    boundaries (Sec. 4.2; every dr-th step stored and
+ *                    interpolated in time with a Kaiser-windowed sinc of
+ *                    radius 8 samples when dr > 1).
  *
  * Conventions
  *   - Axes: n1 = z (fastest), n2 = x, n3 = y (Sec. 3.6).  A 2D model has
@@ -61,7 +63,7 @@ extern "C" {
 #define SMI_ERR_UNSTABLE (-5)     /* a non-finite value appeared */
 #define SMI_ERR_TIMEOUT (-6)      /* a bounded device wait gave up */
 #define SMI_ERR_CUDA (-7)         /* a CUDA runtime call failed */
-#define SMI_ERR_UNSUPPORTED (-8)  /* option outside this build (freesurf, dr > 1) */
+#define SMI_ERR_UNSUPPORTED (-8)  /* option outside this build (freesurf) */
 
 /* Storage precision of the saved boundaries (Sec. 4.2). */
 #define SMI_PREC_F32 0
@@ -102,7 +104,9 @@ typedef struct {
     int order;                /* 4 or 8 (FD order in space, Sec. 3.8) */
     int nb;                   /* CPML layers per face, >= order/2 (paper: 20) */
     int freesurf;             /* 0 only (free surface is not built: SMI_ERR_UNSUPPORTED) */
-    int dr;                   /* boundary decimation ratio: 1 only (SMI_ERR_UNSUPPORTED otherwise) */
+    int dr;                   /* boundary decimation ratio (Sec. 4.2): the boundary of every dr-th
+                                 step is stored and interpolated in time during reconstruction;
+                                 1 <= dr <= 5 vmax / vmin (SMI_ERR_ARG otherwise) */
     int use_box;              /* dynamic computing box (Sec. 4.1), 1 = on */
     int shell_prec;           /* SMI_PREC_* storage of the saved boundaries */
     double kaiser_b;          /* Kaiser window shape (default 4.0) */

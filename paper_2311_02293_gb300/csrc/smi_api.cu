@@ -76,6 +76,7 @@ struct Setup {
     Grid g{};
     int ndim = 0, n[3] = {1, 1, 1};
     int nshot = 0, nt = 0;
+    int dr = 1, nsamp = 0, nt_fwd = 0;     // boundary decimation: stored samples, forward steps
     long long nrec_total = 0;
     std::vector<int> rec_offset;
     std::vector<Stencil> src_st, rec_st;
@@ -86,7 +87,7 @@ struct Setup {
     // device tables
     Stencil *d_src = nullptr, *d_rec = nullptr;
     int *d_box_src = nullptr, *d_box_rec = nullptr;
-    int *d_tab_src = nullptr, *d_tab_rec = nullptr;   // [nshot][nt+1][6] box tables
+    int *d_tab_src = nullptr, *d_tab_rec = nullptr;   // [nshot][nt_fwd+1][6] box tables
     Bands bands{};
 };
 
@@ -126,7 +127,7 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     if (m->ndim != 2 && m->ndim != 3) return fail(SMI_ERR_ARG, "ndim must be 2 or 3");
     if (o->order != 4 && o->order != 8) return fail(SMI_ERR_ARG, "order must be 4 or 8");
     if (o->freesurf != 0) return fail(SMI_ERR_UNSUPPORTED, "free surface is not built (freesurf must be 0)");
-    if (o->dr != 1) return fail(SMI_ERR_UNSUPPORTED, "boundary decimation dr > 1 is not built (dr must be 1)");
+    if (o->dr < 1) return fail(SMI_ERR_ARG, "dr must be >= 1");
     if (o->shell_prec < SMI_PREC_F32 || o->shell_prec > SMI_PREC_BF16)
         return fail(SMI_ERR_ARG, "shell_prec must be SMI_PREC_F32, F16 or BF16");
     const int N = o->order / 2;
@@ -147,6 +148,9 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     }
     S.nshot = geo->nshot;
     S.nt = w->nt;
+    S.dr = o->dr;
+    S.nsamp = band_samples(S.nt, S.dr);
+    S.nt_fwd = forward_steps(S.nt, S.dr);
     S.rec_offset.assign(geo->rec_offset, geo->rec_offset + geo->nshot + 1);
     if (S.rec_offset[0] != 0) return fail(SMI_ERR_ARG, "rec_offset[0] must be 0");
     for (int s = 0; s < S.nshot; s++)
@@ -201,6 +205,11 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     S.vmin = hm[0];
     S.vmax = hm[1];
     g.vdt = (double)S.vmax * w->dt;
+    // Sec. 4.2: dr = 5 vmax / vmin, read as the largest ratio that keeps the
+    // stored boundary above its Nyquist rate
+    if (S.dr > 1 && (double)S.dr > 5.0 * (double)S.vmax / (double)S.vmin)
+        return fail(SMI_ERR_ARG, "dr = %d exceeds 5 vmax / vmin = %.2f (Sec. 4.2)", S.dr,
+                    5.0 * (double)S.vmax / (double)S.vmin);
     const double cfl = cfl_number(m->ndim, hh, w->dt, S.vmax, N);
     if (cfl > 1.0) return fail(SMI_ERR_CFL, "CFL number %.4f exceeds 1 (Eq. cfl)", cfl);
     if (w->fm > 0.0) {
@@ -278,21 +287,22 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     cudaMemcpyAsync(S.d_box_src, S.box_src.data(), sizeof(int) * 6 * S.nshot, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(S.d_box_rec, S.box_rec.data(), sizeof(int) * 6 * S.nshot, cudaMemcpyHostToDevice, st);
     // the computing box of every step, evaluated once on the device
-    S.d_tab_src = ar.get<int>((size_t)S.nshot * (S.nt + 1) * 6);
-    S.d_tab_rec = ar.get<int>((size_t)S.nshot * (S.nt + 1) * 6);
+    S.d_tab_src = ar.get<int>((size_t)S.nshot * (S.nt_fwd + 1) * 6);
+    S.d_tab_rec = ar.get<int>((size_t)S.nshot * (S.nt_fwd + 1) * 6);
     if (!ar.ok) return fail(SMI_ERR_NOMEM, "device allocation failed");
-    launch_box_fill(lc, g, S.d_box_src, S.nshot, S.nt, S.d_tab_src);
-    launch_box_fill(lc, g, S.d_box_rec, S.nshot, S.nt, S.d_tab_rec);
+    launch_box_fill(lc, g, S.d_box_src, S.nshot, S.nt_fwd, S.d_tab_src);
+    launch_box_fill(lc, g, S.d_box_rec, S.nshot, S.nt_fwd, S.d_tab_rec);
     double dV = 1.0;
     for (int a = 0; a < m->ndim; a++) dV *= hh[a];
     S.src_scale = w->dt / dV;
 
     // boundary bands: v_a on the 2N-1 half nodes straddling each face of the
-    // physical domain, over the physical cross-section (Sec. 4.2, dr = 1)
+    // physical domain, over the physical cross-section, stored every dr-th
+    // step (Sec. 4.2)
     Bands &bd = S.bands;
     bd.count = 0;
     bd.prec = o->shell_prec;
-    bd.nt = S.nt;
+    bd.nt = S.nsamp;
     for (int a = 0; a < 3; a++)
         for (int sd = 0; sd < 2; sd++) {
             bd.off[a][sd] = bd.count;
@@ -332,8 +342,9 @@ size_t per_shot_bytes(const Setup &S, int kind)
     size_t b = fields + slabs + (size_t)S.nt * maxrec * 4;
     if (kind != 0) {
         b += fields;                                                   // adjoint fields
-        b += (size_t)S.nt * S.bands.count * band_bytes(S.bands.prec);   // saved bands
-        b += (size_t)S.nt * 6 * 4;                                     // band scales
+        b += (size_t)S.nsamp * S.bands.count * band_bytes(S.bands.prec);   // saved bands
+        b += (size_t)S.nsamp * 6 * 4;                                  // band scales
+        if (S.dr > 1) b += fields;                                     // state kept during the continuation
         b += (size_t)g.nphys * 4;                                      // accumulator
         b += (size_t)S.nt * maxrec * 4 * 2;                            // seis + residual
     }
@@ -496,7 +507,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             float *seis = (kind == 0) ? d_seis_out + (size_t)S.nt * S.rec_offset[s0]
                                       : ba.get<float>(std::max<long long>(1, batch_seis));
             Bands bd = S.bands;
-            float *res = nullptr, *acc = nullptr;
+            float *res = nullptr, *acc = nullptr, *keep = nullptr;
             double *partials = nullptr;
             const int npart = 256;
             if (kind != 0) {
@@ -506,8 +517,9 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     A.psip[a] = F.psip[a];
                     A.psiv[a] = F.psiv[a];
                 }
-                bd.data = ba.raw((size_t)nb_shot * S.nt * bd.count * band_bytes(bd.prec));
-                bd.scale = ba.get<float>((size_t)nb_shot * S.nt * 6);
+                bd.data = ba.raw((size_t)nb_shot * S.nsamp * bd.count * band_bytes(bd.prec));
+                bd.scale = ba.get<float>((size_t)nb_shot * S.nsamp * 6);
+                if (S.dr > 1) keep = ba.get<float>((size_t)(1 + g.ndim) * g.ntot * nb_shot);
                 res = ba.get<float>(std::max<long long>(1, batch_seis));
                 acc = ba.get<float>((size_t)g.nphys * nb_shot);
                 partials = ba.get<double>(npart);
@@ -528,7 +540,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             b.max_rec = max_rec;
             b.tab_src = S.d_tab_src + (size_t)s0 * (S.nt + 1) * 6;
             b.tab_rec = S.d_tab_rec + (size_t)s0 * (S.nt + 1) * 6;
-            b.nt1 = S.nt + 1;
+            b.nt1 = S.nt_fwd + 1;
             // union of the batch's boxes after n steps (bounds the CPML launches)
             auto batch_box = [&](const std::vector<int> &ext, int n, int lo[3], int hi[3]) {
                 for (int a = 0; a < 3; a++) {
@@ -552,8 +564,13 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             }
 
             // ---- forward loop (Algorithm 2) ----
-            for (int it = 0; it < S.nt; it++) {
-                if (kind != 0) launch_save_bands(lc, g, b, F, bd, it, d_absmax);
+            // With dr > 1 the loop continues past nt-1 without a source until
+            // the last stored sample (every time-interpolation window of the
+            // reverse loop complete); the state after step nt-1 is kept.
+            const size_t fbytes = sizeof(float) * g.ntot * nb_shot;
+            const int nsteps = kind != 0 ? S.nt_fwd : S.nt;
+            for (int it = 0; it < nsteps; it++) {
+                if (kind != 0 && it % S.dr == 0) launch_save_bands(lc, g, b, F, bd, it / S.dr, d_absmax);
                 tm.begin(0);
                 if (fast3) {
                     int blo[3], bhi[3];
@@ -567,13 +584,27 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     launch_fwd_p(lc, g, b, F, it);
                 }
                 tm.end();
-                launch_inject_source(lc, g, b, F.p, S.stf, it, (float)S.src_scale);
-                if (max_rec > 0) launch_gather(lc, g, b, F.p, seis, d_soff, S.nt, it);
+                if (it < S.nt) {
+                    launch_inject_source(lc, g, b, F.p, S.stf, it, (float)S.src_scale);
+                    if (max_rec > 0) launch_gather(lc, g, b, F.p, seis, d_soff, S.nt, it);
+                }
                 for (int s = 0; s < nb_shot; s++) {
                     int lo[3], hi[3];
                     box_bounds(g, S.box_src.data() + 6 * (s0 + s), it, lo, hi);
                     account(g, lo, hi, 0, t_stats);
                 }
+                if (keep && it == S.nt - 1) {
+                    cudaMemcpyAsync(keep, F.p, fbytes, cudaMemcpyDeviceToDevice, st);
+                    for (int a = 0; a < g.ndim; a++)
+                        cudaMemcpyAsync(keep + (size_t)(1 + a) * g.ntot * nb_shot, F.v[a], fbytes,
+                                        cudaMemcpyDeviceToDevice, st);
+                }
+            }
+            if (keep) {
+                cudaMemcpyAsync(F.p, keep, fbytes, cudaMemcpyDeviceToDevice, st);
+                for (int a = 0; a < g.ndim; a++)
+                    cudaMemcpyAsync(F.v[a], keep + (size_t)(1 + a) * g.ntot * nb_shot, fbytes,
+                                    cudaMemcpyDeviceToDevice, st);
             }
             if (batch_seis > 0) launch_nonfinite(lc, seis, batch_seis, d_flag);
             launch_nonfinite(lc, F.p, g.ntot * nb_shot, d_flag);
@@ -606,7 +637,8 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     launch_recon_v(lc, g, b, F, it);
                 }
                 tm.end();
-                launch_restore_bands(lc, g, b, F, bd, it);
+                if (S.dr == 1) launch_restore_bands(lc, g, b, F, bd, it);
+                else launch_restore_bands_interp(lc, g, b, F, bd, time_weights(it, S.dr, S.nsamp));
                 tm.begin(1);
                 if (fast3) {
                     int blo[3], bhi[3];

@@ -78,7 +78,7 @@ struct Bands {
     int prec;                    // SMI_PREC_*
     void *data;                  // [nshot][nt][count] of float / half / bf16
     float *scale;                // [nshot][nt][3][2] (16-bit storage only)
-    int nt;
+    int nt;                      // stored samples per shot (steps 0, dr, 2dr, ...)
 };
 
 // ---------------------------------------------------------------------------
@@ -101,6 +101,25 @@ void cpml_tables(int ne, int nb, double h, double vmax, double fm, double R, dou
 // Kaiser-windowed sinc stencil of a position (metres) on the extended grid;
 // false if it leaves the physical domain or its stencil leaves the grid.
 bool make_stencil(const Grid &g, const double pos[3], double kaiser_b, Stencil *st);
+
+// Decimated boundaries (Sec. 4.2): the band of step k*dr is stored for
+// k = 0..nsamp-1, and the band of step it is a Kaiser-windowed sinc (radius
+// kTimeR samples, shape kTimeB) of the stored samples first..first+2kTimeR-1
+// at the fractional sample it/dr; a step on a stored sample takes that
+// sample alone.  Samples before 0 are zero (the field before the first
+// step); the forward run continues past nt-1 without a source so that the
+// window of every step it < nt is complete.
+constexpr int kTimeR = 8;
+constexpr double kTimeB = 8.0;
+struct TimeWeights {
+    int first;             // first stored sample of the window
+    int nsamp;             // stored samples per shot
+    float w[2 * kTimeR];
+};
+TimeWeights time_weights(int it, int dr, int nsamp);
+// Samples stored per shot, and forward steps including the continuation.
+inline int band_samples(int nt, int dr) { return dr == 1 ? nt : (nt - 1) / dr + kTimeR + 1; }
+inline int forward_steps(int nt, int dr) { return dr == 1 ? nt : (band_samples(nt, dr) - 1) * dr + 1; }
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (smi_kernels.cu).  All run on `stream`.
@@ -125,6 +144,9 @@ void launch_save_bands(const LaunchCtx &lc, const Grid &g, const Batch &b, Field
                        Bands bd, int it, unsigned *absmax_tmp);
 void launch_restore_bands(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f,
                           Bands bd, int it);
+// Band of a step between stored samples (decimated boundaries).
+void launch_restore_bands_interp(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, Bands bd,
+                                 const TimeWeights &tw);
 void launch_residual(const LaunchCtx &lc, const float *seis, const float *dobs, long long n,
                      int mode, float *res, double *partials, int npart);
 void launch_sum_partials(const LaunchCtx &lc, const double *partials, int npart, double *out);

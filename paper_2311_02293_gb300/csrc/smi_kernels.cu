@@ -912,6 +912,41 @@ __global__ void k_band_restore(Grid g, Fields f, Bands bd, int it)
     }
 }
 
+// Band of a step between stored samples: sum_q w_q sample[first+q] over the
+// samples that exist (before sample 0 the field is zero).
+__global__ void k_band_restore_interp(Grid g, Fields f, Bands bd, TimeWeights tw)
+{
+    const BandRegion R(bd, blockIdx.y);
+    if (R.a >= g.ndim || R.n <= 0) return;
+    const int s = blockIdx.z;
+    float *v = f.v[R.a] + (long long)s * g.ntot;
+    float x[kBandVals];
+#pragma unroll
+    for (int q = 0; q < kBandVals; q++) x[q] = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 2 * kTimeR; t++) {
+        const int k = tw.first + t;
+        if (k < 0 || k >= tw.nsamp || tw.w[t] == 0.0f) continue;
+        const long long o0 = ((long long)s * bd.nt + k) * bd.count + R.off;
+        const float wt = bd.prec == SMI_PREC_F32 ? tw.w[t] : tw.w[t] * bd.scale[((long long)s * bd.nt + k) * 6 + blockIdx.y];
+#pragma unroll
+        for (int q = 0; q < kBandVals; q++) {
+            const int u = (blockIdx.x * kBandVals + q) * blockDim.x + threadIdx.x;
+            if (u >= R.n) continue;
+            float y;
+            if (bd.prec == SMI_PREC_F32) y = static_cast<const float *>(bd.data)[o0 + u];
+            else if (bd.prec == SMI_PREC_F16) y = __half2float(static_cast<const __half *>(bd.data)[o0 + u]);
+            else y = __bfloat162float(static_cast<const __nv_bfloat16 *>(bd.data)[o0 + u]);
+            x[q] += wt * y;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kBandVals; q++) {
+        const int u = (blockIdx.x * kBandVals + q) * blockDim.x + threadIdx.x;
+        if (u < R.n) v[R.node(g, u)] = x[q];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Residual (mode 0: u - d, mode 1: d) and per-block partial sums of
 // 1/2 (u - d)^2 in FP64 (Eq. objfwi).
@@ -1261,6 +1296,14 @@ void launch_restore_bands(const LaunchCtx &lc, const Grid &g, const Batch &b, Fi
 {
     const dim3 grid = band_grid(bd, b.nshot);
     k_band_restore<<<grid, kThreads, 0, S(lc)>>>(g, f, bd, it);
+    ++*lc.launches;
+}
+
+void launch_restore_bands_interp(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, Bands bd,
+                                 const TimeWeights &tw)
+{
+    const dim3 grid = band_grid(bd, b.nshot);
+    k_band_restore_interp<<<grid, kThreads, 0, S(lc)>>>(g, f, bd, tw);
     ++*lc.launches;
 }
 

@@ -149,7 +149,7 @@ int forward_noalloc(const smi_model *m, const smi_geometry *geo, const smi_wavel
     if (m->ndim != 2 && m->ndim != 3) return err(SMI_ERR_ARG, "ndim must be 2 or 3");
     if (o->order != 4 && o->order != 8) return err(SMI_ERR_ARG, "order must be 4 or 8");
     if (o->freesurf != 0) return err(SMI_ERR_UNSUPPORTED, "free surface is not built (freesurf must be 0)");
-    if (o->dr != 1) return err(SMI_ERR_UNSUPPORTED, "boundary decimation dr > 1 is not built (dr must be 1)");
+    if (o->dr < 1) return err(SMI_ERR_ARG, "dr must be >= 1");
     if (o->shell_prec < SMI_PREC_F32 || o->shell_prec > SMI_PREC_BF16)
         return err(SMI_ERR_ARG, "shell_prec must be SMI_PREC_F32, F16 or BF16");
     const int N = o->order / 2;
@@ -228,6 +228,11 @@ int forward_noalloc(const smi_model *m, const smi_geometry *geo, const smi_wavel
     if (!(hm[0] > 0.0f) || !(hm[2] > 0.0f) || !std::isfinite(hm[1]) || !std::isfinite(hm[3]))
         return err(SMI_ERR_ARG, "vp and rho must be positive and finite");
     g.vdt = (double)hm[1] * w->dt;
+    // the same admission as smi_forward (Sec. 4.2 dr rule, although forward
+    // modelling stores no boundaries)
+    if (o->dr > 1 && (double)o->dr > 5.0 * (double)hm[1] / (double)hm[0])
+        return err(SMI_ERR_ARG, "dr = %d exceeds 5 vmax / vmin = %.2f (Sec. 4.2)", o->dr,
+                   5.0 * (double)hm[1] / (double)hm[0]);
     const double cfl = cfl_number(m->ndim, hh, w->dt, hm[1], N);
     if (cfl > 1.0) return err(SMI_ERR_CFL, "CFL number %.4f exceeds 1 (Eq. cfl)", cfl);
     if (w->fm > 0.0) {

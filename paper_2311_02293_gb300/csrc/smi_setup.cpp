@@ -122,6 +122,30 @@ bool make_stencil(const Grid &g, const double pos[3], double kaiser_b, Stencil *
     return true;
 }
 
+TimeWeights time_weights(int it, int dr, int nsamp)
+{
+    TimeWeights tw{};
+    tw.nsamp = nsamp;
+    if (it % dr == 0) {                 // on a stored sample: that sample alone
+        tw.first = it / dr;
+        tw.w[0] = 1.0f;
+        return tw;
+    }
+    const double x = (double)it / (double)dr;
+    const int base = (int)std::floor(x);
+    tw.first = base - kTimeR + 1;
+    const double i0b = std::cyl_bessel_i(0.0, kTimeB);
+    for (int q = 0; q < 2 * kTimeR; q++) {
+        const double u = (tw.first + q) - x;
+        const double sinc = std::sin(M_PI * u) / (M_PI * u);
+        const double r = u / kTimeR;
+        const double arg = 1.0 - r * r;
+        const double win = arg > 0.0 ? std::cyl_bessel_i(0.0, kTimeB * std::sqrt(arg)) / i0b : 0.0;
+        tw.w[q] = (float)(sinc * win);
+    }
+    return tw;
+}
+
 void set_layout(Grid &g, const int n[3])
 {
     g.px = (g.ne[0] + 7) / 8 * 8;

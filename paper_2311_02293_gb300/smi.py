@@ -154,6 +154,7 @@ class Problem:
     cpml_R: float = 1e-3
     max_batch: int = 0
     profile: bool = False
+    dr: int = 1             # boundary decimation ratio (Sec. 4.2)
 
 
 def _geometry(srcs, recs):
@@ -199,6 +200,7 @@ def _opts(prob: Problem, stream):
     o.cpml_R = prob.cpml_R
     o.max_batch = prob.max_batch
     o.profile = int(prob.profile)
+    o.dr = int(prob.dr)
     if stream is not None:
         o.stream = stream
     elif torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():

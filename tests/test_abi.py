@@ -75,12 +75,14 @@ def test_unbuilt_features_are_refused(smi):
     m = smi.smi_model(2, 30, 30, 1, 10.0, 10.0, 1.0, None, None)
     geo = smi.smi_geometry(0, None, None, None)
     w = smi.smi_wavelet(10, 1e-3, 10.0, None)
-    for field, value in (("freesurf", 1), ("dr", 10)):
+    # free surface is not built; a decimation ratio below 1 is an argument
+    # error (both refused before any device work)
+    for field, value, code in (("freesurf", 1, -8), ("dr", 0, -1)):
         o2 = smi.smi_opts.from_buffer_copy(o)
         setattr(o2, field, value)
         rc = smi.lib().smi_forward(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w),
                                    ctypes.byref(o2), None)
-        assert rc == -8
+        assert rc == code
         assert smi.lib().smi_last_error().decode()
 
 
