@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--shell", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--dr", type=int, default=1, help="boundary decimation ratio (Sec. 4.2; 1 = every step)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nt", type=int, default=2500, help="time steps (full workload: 2500)")
@@ -220,7 +221,7 @@ def run_ours(args):
 
     w = synth.salt_3d(nt=args.nt)
     prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, shell_prec=args.shell,
-                       profile=True)
+                       profile=True, dr=args.dr)
     vp = torch.from_numpy(w.vp).to(dev)
     rho = torch.from_numpy(w.rho).to(dev)
     stf = torch.from_numpy(w.stf).to(dev)
@@ -309,6 +310,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "shots_per_step": 1, "boundary_storage": args.shell,
+                           "boundary_decimation": args.dr,
                            "nt": w.nt, "grid_extended": ne, "l2": "inputs larger than L2 (157 MB per field)",
                            "parallelism": f"replicas x{world} (shots sharded)"},
                 "effective_gpts": float(eff),
@@ -346,13 +348,19 @@ def run_profile(args):
             "ms": dict(zip(names, st["ms"])),
             "algorithmic_gbs": {c: (b / (m * 1e6) if m else None) for c, b, m in zip(names, st["bytes"], st["ms"])},
             "kernel_launches": st["kernel_launches"]}
-    if args.profile == "rtm" and args.shell != "f32":
-        # the image with 16-bit boundary storage against FP32 storage
-        p16 = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, use_box=not args.no_box,
-                          shell_prec=args.shell)
-        i16 = smi.smi_rtm(vp, rho, p16, w.srcs, w.recs, stf, seis[0])
+    if args.profile == "rtm" and (args.shell != "f32" or args.dr > 1):
+        # the image with 16-bit and / or decimated boundary storage against
+        # FP32 storage of every step, with the time and footprint of the call
+        pq = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, use_box=not args.no_box,
+                         shell_prec=args.shell, dr=args.dr, profile=True)
+        iq = smi.smi_rtm(vp, rho, pq, w.srcs, w.recs, stf, seis[0])
+        torch.cuda.synchronize()
+        sq = smi.smi_last_stats()
         line["shell"] = args.shell
-        line["image_rel_l2_vs_f32_shells"] = float(torch.linalg.norm(i16 - img) / torch.linalg.norm(img))
+        line["dr"] = args.dr
+        line["image_rel_l2_vs_f32_every_step"] = float(torch.linalg.norm(iq - img) / torch.linalg.norm(img))
+        line["ms_with_options"] = dict(zip(names, sq["ms"]))
+        line["device_bytes"] = {"f32_every_step": st["device_bytes"], "with_options": sq["device_bytes"]}
     print(json.dumps(line), flush=True)
 
 

@@ -127,7 +127,8 @@ typedef struct {
     double ms[3];             /* summed CUDA-event time of those steps (opts.profile = 1) */
     long long steps[3];       /* stencil steps taken (per shot) */
     long long kernel_launches;   /* every kernel the call launched */
-    double device_bytes;      /* peak device memory allocated by the call (set-up arena) */
+    double device_bytes;      /* peak device memory the call allocated: set-up tables plus its largest
+                                 batch of shots (fields, saved boundaries, accumulators) */
     long long band_values;    /* boundary values saved per shot per step (0 for forward) */
 } smi_stats;
 

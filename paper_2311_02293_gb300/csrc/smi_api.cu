@@ -481,7 +481,9 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         launch_zero(lc, d_flag, sizeof(unsigned));
         launch_zero(lc, d_wait, sizeof(unsigned));
         const bool fast3 = stencil3d_supported(g);
+        const bool fast2 = stencil2d_supported(g);
 
+        size_t batch_peak = 0;                   // largest batch arena (fields, bands, accumulators)
         for (int s0 = 0; s0 < S.nshot; s0 += B) {
             const int nb_shot = std::min(B, S.nshot - s0);
             // per-batch tables
@@ -525,6 +527,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 partials = ba.get<double>(npart);
             }
             if (!ba.ok) return fail(SMI_ERR_NOMEM, "device allocation for a batch of %d shots failed", nb_shot);
+            batch_peak = std::max(batch_peak, ba.peak);
             cudaMemcpyAsync(d_roff, roff.data(), sizeof(int) * roff.size(), cudaMemcpyHostToDevice, st);
             cudaMemcpyAsync(d_soff, soff.data(), sizeof(long long) * soff.size(), cudaMemcpyHostToDevice, st);
             Maps3 mF{}, mA{};
@@ -572,16 +575,22 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             for (int it = 0; it < nsteps; it++) {
                 if (kind != 0 && it % S.dr == 0) launch_save_bands(lc, g, b, F, bd, it / S.dr, d_absmax);
                 tm.begin(0);
+                int blo[3], bhi[3];
+                batch_box(S.box_src, it, blo, bhi);
                 if (fast3) {
-                    int blo[3], bhi[3];
-                    batch_box(S.box_src, it, blo, bhi);
                     launch3_v(lc, mF, g, b, F, it, 0, d_wait);
                     launch_fwd_corrections(lc, g, b, F, it, true, blo, bhi);
                     launch3_p(lc, mF, nullptr, g, b, F, it, 0, d_wait, nullptr, 0, nullptr, 0.0f);
                     launch_fwd_corrections(lc, g, b, F, it, false, blo, bhi);
+                } else if (fast2) {
+                    launch2_v(lc, g, b, F, it, 0, blo, bhi);
+                    launch_fwd_corrections(lc, g, b, F, it, true, blo, bhi);
+                    launch2_p(lc, g, b, F, it, 0, blo, bhi, nullptr, nullptr, 0, nullptr, 0.0f);
+                    launch_fwd_corrections(lc, g, b, F, it, false, blo, bhi);
                 } else {
-                    launch_fwd_v(lc, g, b, F, it);
-                    launch_fwd_p(lc, g, b, F, it);
+                    const long long work = box_points(blo, bhi);
+                    launch_fwd_v(lc, g, b, F, it, work);
+                    launch_fwd_p(lc, g, b, F, it, work);
                 }
                 tm.end();
                 if (it < S.nt) {
@@ -633,23 +642,41 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     launch3_p(lc, mF, &mA, g, b, F, it, 2, d_wait, acc, mode, S.stf, (float)S.src_scale);
                     launch3_v(lc, mF, g, b, F, it, 2, d_wait);
                 } else {
-                    launch_recon_p(lc, g, b, F, A.p, acc, mode, S.stf, it, (float)S.src_scale);
-                    launch_recon_v(lc, g, b, F, it);
+                    int blo[3], bhi[3];
+                    batch_box(S.box_src, it, blo, bhi);
+                    for (int a = 0; a < 3; a++) {        // reconstruction: box within the physical domain
+                        blo[a] = std::max(blo[a], g.L[a]);
+                        bhi[a] = std::min(bhi[a], g.H[a]);
+                    }
+                    if (fast2) {
+                        launch2_p(lc, g, b, F, it, 2, blo, bhi, A.p, acc, mode, S.stf, (float)S.src_scale);
+                        launch2_v(lc, g, b, F, it, 2, blo, bhi);
+                    } else {
+                        const long long work = box_points(blo, bhi);
+                        launch_recon_p(lc, g, b, F, A.p, acc, mode, S.stf, it, (float)S.src_scale, work);
+                        launch_recon_v(lc, g, b, F, it, work);
+                    }
                 }
                 tm.end();
                 if (S.dr == 1) launch_restore_bands(lc, g, b, F, bd, it);
                 else launch_restore_bands_interp(lc, g, b, F, bd, time_weights(it, S.dr, S.nsamp));
                 tm.begin(1);
+                int blo[3], bhi[3];
+                batch_box(S.box_rec, mrev, blo, bhi);
                 if (fast3) {
-                    int blo[3], bhi[3];
-                    batch_box(S.box_rec, mrev, blo, bhi);
                     launch_adj_corrections(lc, g, b, A, mrev, true, blo, bhi);
                     launch3_v(lc, mA, g, b, A, mrev, 1, d_wait);
                     launch_adj_corrections(lc, g, b, A, mrev, false, blo, bhi);
                     launch3_p(lc, mA, nullptr, g, b, A, mrev, 1, d_wait, nullptr, 0, nullptr, 0.0f);
+                } else if (fast2) {
+                    launch_adj_corrections(lc, g, b, A, mrev, true, blo, bhi);
+                    launch2_v(lc, g, b, A, mrev, 1, blo, bhi);
+                    launch_adj_corrections(lc, g, b, A, mrev, false, blo, bhi);
+                    launch2_p(lc, g, b, A, mrev, 1, blo, bhi, nullptr, nullptr, 0, nullptr, 0.0f);
                 } else {
-                    launch_adj_v(lc, g, b, A, mrev);
-                    launch_adj_p(lc, g, b, A, mrev);
+                    const long long work = box_points(blo, bhi);
+                    launch_adj_v(lc, g, b, A, mrev, work);
+                    launch_adj_p(lc, g, b, A, mrev, work);
                 }
                 tm.end();
                 for (int s = 0; s < nb_shot; s++) {
@@ -687,7 +714,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         if (!rc && flag) rc = fail(SMI_ERR_UNSTABLE, "non-finite values in the wavefield or outputs");
         tm.collect(t_stats);
         t_stats.kernel_launches = launches;
-        t_stats.device_bytes = (double)ar.peak;
+        t_stats.device_bytes = (double)(ar.peak + batch_peak);
         t_stats.band_values = kind == 0 ? 0 : S.bands.count;
     }
     // the arena's frees are stream ordered; make them complete before return

@@ -61,6 +61,14 @@ SMI_HD void box_bounds(const Grid &g, const int *ext, int n, int lo[3], int hi[3
     }
 }
 
+// Points of the box [lo, hi] (0 if empty).
+SMI_HD long long box_points(const int lo[3], const int hi[3])
+{
+    long long v = 1;
+    for (int a = 0; a < 3; a++) v *= hi[a] >= lo[a] ? (long long)(hi[a] - lo[a] + 1) : 0LL;
+    return v;
+}
+
 // Box of shot s after n steps (n >= -1) from a table filled by box_bounds.
 SMI_HD void box_at(const int *tab, int nt1, int s, int n, int lo[3], int hi[3])
 {

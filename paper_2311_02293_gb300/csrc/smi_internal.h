@@ -134,8 +134,11 @@ void launch_extend_model(const LaunchCtx &lc, const Grid &g, const float *vp, co
 void launch_minmax(const LaunchCtx &lc, const float *vp, long long n, float *out2, unsigned *tmp);
 void launch_zero(const LaunchCtx &lc, void *ptr, size_t bytes);
 
-void launch_fwd_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it);
-void launch_fwd_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it);
+// Generic kernels (2D, and 3D without the TMA path): `work` = the largest
+// number of points a shot of the batch updates in this launch (its box), which
+// sizes the grid.
+void launch_fwd_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, long long work);
+void launch_fwd_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, long long work);
 void launch_inject_source(const LaunchCtx &lc, const Grid &g, const Batch &b, float *p,
                           const float *stf, int it, float scale);
 void launch_gather(const LaunchCtx &lc, const Grid &g, const Batch &b, const float *p,
@@ -152,8 +155,8 @@ void launch_residual(const LaunchCtx &lc, const float *seis, const float *dobs, 
 void launch_sum_partials(const LaunchCtx &lc, const double *partials, int npart, double *out);
 void launch_adj_inject(const LaunchCtx &lc, const Grid &g, const Batch &b, float *lp,
                        const float *res, const long long *seis_off, int nt, int it);
-void launch_adj_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m);
-void launch_adj_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m);
+void launch_adj_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, long long work);
+void launch_adj_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, long long work);
 // One piece of the union of the CPML bands: per axis up to two index
 // intervals {start0, len0, start1, len1}; nodes = product of the counts.
 struct Piece {
@@ -173,23 +176,32 @@ struct Pieces {
 };
 // uz: nodes per lane along x in the z piece's kernel.
 Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, int w_hi, int uz);
-// 3D only.  Transposed z and x CPML terms of the adjoint (vel: velocity
-// part, else pressure part, which also updates phi_y at its own nodes) over
-// the union of the z and x bands within the box [lo, hi] (union of the
-// batch's receiver boxes after m reverse steps); run before the main 3D
-// kernels, which apply the y terms.
+// Transposed z and x CPML terms of the adjoint (vel: velocity part, else
+// pressure part, which in 3D also updates phi_y at its own nodes) over the
+// union of the z and x bands within the box [lo, hi] (union of the batch's
+// receiver boxes after m reverse steps); run before the main kernels (in 3D
+// those apply the y terms).
 void launch_adj_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, bool vel,
                             const int lo[3], const int hi[3]);
-// 3D only.  Forward z and x CPML memory-variable updates over the slabs
-// (vel: velocity part, else pressure part) within the box [lo, hi] (union
-// of the batch's source boxes at step it); added to the update of the main
-// 3D kernels, which apply the y terms.
+// Forward z and x CPML memory-variable updates over the slabs (vel:
+// velocity part, else pressure part) within the box [lo, hi] (union of the
+// batch's source boxes at step it); added to the update of the main kernels
+// (in 3D those apply the y terms).
 void launch_fwd_corrections(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, bool vel,
                             const int lo[3], const int hi[3]);
 void launch_recon_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f,
                     const float *lp, float *acc, int mode, const float *stf, int it,
-                    float src_scale);
-void launch_recon_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it);
+                    float src_scale, long long work);
+void launch_recon_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, long long work);
+
+// 2D kernels (smi_stencil2d.cu): mode 0 forward, 1 adjoint (interior
+// update; CPML by the band kernels), 2 reconstruction + imaging; [lo, hi] =
+// the batch's box union (for mode 2 within the physical domain).
+bool stencil2d_supported(const Grid &g);
+void launch2_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int step, int mode, const int lo[3],
+               const int hi[3]);
+void launch2_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int step, int mode, const int lo[3],
+               const int hi[3], const float *lp, float *acc, int img_mode, const float *stf, float src_scale);
 void launch_reduce_shots(const LaunchCtx &lc, const Grid &g, const float *acc, int nshot,
                          float *out, int accumulate);
 void launch_finalize_grad(const LaunchCtx &lc, long long n, const float *vp, float dt,

@@ -65,7 +65,8 @@ __device__ __forceinline__ long long slab_index(const Grid &g, int a, int i1, in
 
 __device__ __forceinline__ float buoyancy(const Grid &g, int a, int ia, long long k, float rho0)
 {
-    return (ia + 1 < g.ne[a]) ? 2.0f / (rho0 + g.rho[k + gstride(g, a)]) : 1.0f / rho0;
+    // fast reciprocal-based division: a few ulp, far below the FP32 scheme error
+    return (ia + 1 < g.ne[a]) ? __fdividef(2.0f, rho0 + g.rho[k + gstride(g, a)]) : __fdividef(1.0f, rho0);
 }
 
 struct BoxIter {
@@ -82,6 +83,13 @@ struct BoxIter {
     }
     __device__ void at(long long q, int i[3]) const
     {
+        if (vol < (1LL << 31)) {          // 32-bit division (uniform branch)
+            const int qq = (int)q, r = qq / w0;
+            i[0] = lo[0] + (qq - r * w0);
+            i[1] = lo[1] + r % w1;
+            i[2] = lo[2] + r / w1;
+            return;
+        }
         i[0] = lo[0] + (int)(q % w0);
         long long r = q / w0;
         i[1] = lo[1] + (int)(r % w1);
@@ -459,7 +467,7 @@ struct CpmlPhiY {
         B = 0.0f;
         step = step_;
         const int y = i[2];
-        if (y < g.nb || y >= g.ne[2] - g.nb - 1) {
+        if (g.ndim == 3 && (y < g.nb || y >= g.ne[2] - g.nb - 1)) {
             const int js = y < g.nb ? y : y - (g.ne[2] - 2 * g.nb - 1);
             ph = f.psiv[2] + (long long)s * g.slab_n[2] + i[0] + g.px * (i[1] + g.ne[1] * js);
             B = g.cpb[2][y];
@@ -620,15 +628,16 @@ __device__ __forceinline__ void cpml_zwarp(const Grid &g, const Fields &f, const
     }
 }
 
-// x piece: block = 64 z indices x 4 y indices; blockIdx.y = chunk along x,
-// blockIdx.z = shot.
+// x piece: block = ZB z indices x 256/ZB y indices (ZB = 64 in 3D, 256 in 2D
+// where y has one index); blockIdx.y = chunk along x, blockIdx.z = shot.
 template <int N, int KIND>
 __global__ void __launch_bounds__(256) k_cpml_x(Grid g, Batch b, Fields f, Pieces P, int m)
 {
     const Piece &p = P.q[1];
-    const int nbz = (p.cnt[0] + 63) >> 6;
+    const int zb = g.ndim == 3 ? 64 : 256;
+    const int nbz = (p.cnt[0] + zb - 1) / zb;
     const int bz = blockIdx.x % nbz, br = blockIdx.x / nbz;
-    const int c0 = bz * 64 + (threadIdx.x & 63), cr = br * 4 + (threadIdx.x >> 6);
+    const int c0 = bz * zb + (int)threadIdx.x % zb, cr = br * (256 / zb) + (int)threadIdx.x / zb;
     if (c0 >= p.cnt[0] || cr >= p.cnt[2]) return;
     const int s = blockIdx.z;
     int lo[3], hi[3];
@@ -1099,40 +1108,40 @@ inline int blocks_for(long long n)
         ++*lc.launches;                                                                    \
     } while (0)
 
-void launch_fwd_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it)
+void launch_fwd_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, long long work)
 {
-    dim3 grid(blocks_for(g.ntot), b.nshot);
+    dim3 grid(blocks_for(work), b.nshot);
     SMI_DISPATCH(k_fwd_v, grid, g, b, f, it);
 }
 
-void launch_fwd_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it)
+void launch_fwd_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, long long work)
 {
-    dim3 grid(blocks_for(g.ntot), b.nshot);
+    dim3 grid(blocks_for(work), b.nshot);
     SMI_DISPATCH(k_fwd_p, grid, g, b, f, it);
 }
 
-void launch_adj_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m)
+void launch_adj_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, long long work)
 {
-    dim3 grid(blocks_for(g.ntot), b.nshot);
+    dim3 grid(blocks_for(work), b.nshot);
     SMI_DISPATCH(k_adj_v, grid, g, b, f, m);
 }
 
-void launch_adj_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m)
+void launch_adj_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, long long work)
 {
-    dim3 grid(blocks_for(g.ntot), b.nshot);
+    dim3 grid(blocks_for(work), b.nshot);
     SMI_DISPATCH(k_adj_p, grid, g, b, f, m);
 }
 
 void launch_recon_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, const float *lp,
-                    float *acc, int mode, const float *stf, int it, float src_scale)
+                    float *acc, int mode, const float *stf, int it, float src_scale, long long work)
 {
-    dim3 grid(blocks_for(g.nphys), b.nshot);
+    dim3 grid(blocks_for(work), b.nshot);
     SMI_DISPATCH(k_recon_p, grid, g, b, f, lp, acc, mode, stf, it, src_scale);
 }
 
-void launch_recon_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it)
+void launch_recon_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, long long work)
 {
-    dim3 grid(blocks_for(g.nphys), b.nshot);
+    dim3 grid(blocks_for(work), b.nshot);
     SMI_DISPATCH(k_recon_v, grid, g, b, f, it);
 }
 
@@ -1185,7 +1194,8 @@ Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, in
             const long long zw = (p.iv[0][1] + bw - 1) / bw + (p.iv[0][3] + bw - 1) / bw;
             p.blocks = (int)((zw * p.cnt[2] + 7) / 8);
         } else {
-            p.blocks = ((p.cnt[0] + 63) / 64) * ((p.cnt[2] + 3) / 4);
+            const int zb = g.ndim == 3 ? 64 : 256;
+            p.blocks = ((p.cnt[0] + zb - 1) / zb) * ((p.cnt[2] + 256 / zb - 1) / (256 / zb));
         }
     }
     return P;

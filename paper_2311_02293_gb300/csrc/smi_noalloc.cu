@@ -12,6 +12,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "smi_box.h"
 #include "smi_internal.h"
 
 namespace smi {
@@ -332,8 +333,10 @@ int forward_noalloc(const smi_model *m, const smi_geometry *geo, const smi_wavel
         }
         float *out = seis + (size_t)w->nt * r0;
         for (int it = 0; it < w->nt; it++) {
-            launch_fwd_v(lc, g, b, F, it);
-            launch_fwd_p(lc, g, b, F, it);
+            int lo[3], hi[3];
+            box_bounds(g, box, it, lo, hi);
+            launch_fwd_v(lc, g, b, F, it, box_points(lo, hi));
+            launch_fwd_p(lc, g, b, F, it, box_points(lo, hi));
             launch_inject_source(lc, g, b, F.p, w->stf, it, src_scale);
             if (nr > 0) launch_gather(lc, g, b, F.p, out, pl.seis_off, w->nt, it);
         }

@@ -1,0 +1,279 @@
+// smi_stencil2d.cu -- 2D staggered-grid stencil kernels (sm_103a).
+//
+// Two kernels advance one half of a leap-frog step each (Sec. 2.1 update
+// equations): k2_v updates v_z and v_x from p, k2_p updates p from them.
+// Modes:
+//   FWD / ADJ  the interior update, on the computing box of the forward
+//              (source) or adjoint (receiver) run; the CPML terms are added
+//              by the band kernels of smi_kernels.cu (for the adjoint: the
+//              transposed terms, applied before these kernels), so the
+//              adjoint in "same solver" form runs this same code;
+//   REC        source-field reconstruction backwards in time (Sec. 4.2) on
+//              the physical domain inside the forward box of the step,
+//              fused with the imaging / gradient accumulation in k2_p;
+//              nodes outside the previous step's box are set to zero.
+//
+// A block is 8 x 32 threads over a 32 (z) x 32 (x) tile of the batch's box
+// union (blockIdx.z = shot); a thread owns 4 consecutive z nodes of one x
+// column as one float4.  z-derivatives use a 12-value window (three float4
+// loads), x-derivatives one float4 per tap; neighbours come through L1.
+// Rows are padded to px (a multiple of 8) and the padding holds zeros, so a
+// float4 that reaches past the last z node reads the scheme's zero values.
+// Offsets inside one shot's arrays are 32-bit (fewer than 2^31 points).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "smi_box.h"
+#include "smi_internal.h"
+
+namespace smi {
+
+namespace {
+
+enum { FWD = 0, ADJ = 1, REC = 2 };
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void put(float (&a)[4], float4 v) { a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w; }
+__device__ __forceinline__ bool in_range(int v, int lo, int hi) { return v >= lo && v <= hi; }
+
+// Quad of field q at (oz..oz+3, x): zero outside the grid.
+__device__ __forceinline__ void quad(const Grid &g, const float *q, int oz, int x, float (&a)[4])
+{
+    if (oz < 0 || oz >= g.px || x < 0 || x >= g.ne[1]) {
+        a[0] = a[1] = a[2] = a[3] = 0.0f;
+        return;
+    }
+    put(a, ld4(q + oz + g.px * x));
+}
+
+// The node block of this thread and the update box of its shot (REC: the
+// forward box within the physical domain, plus the previous step's box).
+struct Node2 {
+    int s, oz, ox;
+    bool mx, mz[4], any;
+    int plo[3], phi[3];
+};
+
+template <int MODE>
+__device__ __forceinline__ bool node2(const Grid &g, const Batch &b, int step, int z0, int x0, Node2 &n)
+{
+    n.s = blockIdx.z;
+    n.oz = z0 + 32 * blockIdx.x + 4 * threadIdx.x;
+    n.ox = x0 + 32 * blockIdx.y + threadIdx.y;
+    if (n.oz >= g.ne[0] || n.ox >= g.ne[1]) return false;
+    int lo[3], hi[3];
+    box_at(MODE == ADJ ? b.tab_rec : b.tab_src, b.nt1, n.s, step, lo, hi);
+    if (MODE == REC) {
+        for (int a = 0; a < 2; a++) {
+            lo[a] = max(lo[a], g.L[a]);
+            hi[a] = min(hi[a], g.H[a]);
+        }
+        box_at(b.tab_src, b.nt1, n.s, step - 1, n.plo, n.phi);
+    }
+    n.mx = in_range(n.ox, lo[1], hi[1]);
+    n.any = false;
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        n.mz[r] = n.mx && in_range(n.oz + r, lo[0], hi[0]);
+        n.any = n.any || n.mz[r];
+    }
+    return n.any;
+}
+
+__device__ __forceinline__ float buoy2(float r0, float r1, bool last)
+{
+    // fast reciprocal-based division: a few ulp, far below the FP32 scheme error
+    return last ? __fdividef(1.0f, r0) : __fdividef(2.0f, r0 + r1);
+}
+
+// FWD / ADJ: v_a -= dt b_a D_a p.  REC: v_a += dt b_a D_a p on
+// L_a+N-1 .. H_a-N along a (elsewhere v_a keeps its saved value), zero
+// outside the previous box.
+template <int N, int MODE>
+__global__ void __launch_bounds__(256) k2_v(Grid g, Batch b, Fields f, int step, int z0, int x0)
+{
+    Node2 n;
+    if (!node2<MODE>(g, b, step, z0, x0, n)) return;
+    const long long sh = (long long)n.s * g.ntot;
+    const float *p = f.p + sh;
+    const int oz = n.oz, ox = n.ox, k = oz + g.px * ox;
+    float W[12];
+    {
+        float a[4], c[4], d[4];
+        quad(g, p, oz - 4, ox, a);
+        quad(g, p, oz, ox, c);
+        quad(g, p, oz + 4, ox, d);
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            W[r] = a[r];
+            W[4 + r] = c[r];
+            W[8 + r] = d[r];
+        }
+    }
+    float Xp[N][4], Xm[N][4];                 // p at ox + l and ox - l + 1
+#pragma unroll
+    for (int l = 1; l <= N; l++) {
+        quad(g, p, oz, ox + l, Xp[l - 1]);
+        if (l == 1) {
+#pragma unroll
+            for (int r = 0; r < 4; r++) Xm[0][r] = W[4 + r];
+        } else {
+            quad(g, p, oz, ox - l + 1, Xm[l - 1]);
+        }
+    }
+    float rho0[4], rx[4], vz[4], vx[4];
+    put(rho0, ld4(g.rho + k));
+    const bool lastx = ox + 1 >= g.ne[1];
+    if (!lastx) put(rx, ld4(g.rho + k + g.px));
+    const float rz4 = oz + 4 < g.ne[0] ? g.rho[k + 4] : 0.0f;
+    put(vz, ld4(f.v[0] + sh + k));
+    put(vx, ld4(f.v[1] + sh + k));
+    bool keep[4];
+    if (MODE == REC) {
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+            keep[r] = in_range(oz + r, n.plo[0], n.phi[0]) && in_range(ox, n.plo[1], n.phi[1]);
+    }
+    const bool rxm = in_range(ox, g.L[1] + N - 1, g.H[1] - N);
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        if (!n.mz[r]) continue;
+        float dz = 0.0f, dx = 0.0f;
+#pragma unroll
+        for (int l = 1; l <= N; l++) {
+            dz += g.c[0][l - 1] * (W[4 + r + l] - W[4 + r - l + 1]);
+            dx += g.c[1][l - 1] * (Xp[l - 1][r] - Xm[l - 1][r]);
+        }
+        const int z = oz + r;
+        const float bz = buoy2(rho0[r], r < 3 ? rho0[r + 1] : rz4, z + 1 >= g.ne[0]);
+        const float bx = buoy2(rho0[r], lastx ? 0.0f : rx[r], lastx);
+        if (MODE == REC) {
+            if (in_range(z, g.L[0] + N - 1, g.H[0] - N)) vz[r] = keep[r] ? vz[r] + g.dt * bz * dz : 0.0f;
+            if (rxm) vx[r] = keep[r] ? vx[r] + g.dt * bx * dx : 0.0f;
+        } else {
+            vz[r] -= g.dt * bz * dz;
+            vx[r] -= g.dt * bx * dx;
+        }
+    }
+    *reinterpret_cast<float4 *>(f.v[0] + sh + k) = make_float4(vz[0], vz[1], vz[2], vz[3]);
+    *reinterpret_cast<float4 *>(f.v[1] + sh + k) = make_float4(vx[0], vx[1], vx[2], vx[3]);
+}
+
+// FWD / ADJ: p -= dt kappa (D_z v_z + D_x v_x).  REC: acc += lp * (div v |
+// p^{it+1}), p^{it} = p^{it+1} + dt kappa div v - dt stf w / dV, zero
+// outside the previous box.
+template <int N, int MODE>
+__global__ void __launch_bounds__(256) k2_p(Grid g, Batch b, Fields f, int step, int z0, int x0, const float *lpall,
+                                            float *acc, int img_mode, const float *stf, float src_scale)
+{
+    Node2 n;
+    if (!node2<MODE>(g, b, step, z0, x0, n)) return;
+    const long long sh = (long long)n.s * g.ntot;
+    const float *vzf = f.v[0] + sh, *vxf = f.v[1] + sh;
+    const int oz = n.oz, ox = n.ox, k = oz + g.px * ox;
+    float W[12];
+    {
+        float a[4], c[4], d[4];
+        quad(g, vzf, oz - 4, ox, a);
+        quad(g, vzf, oz, ox, c);
+        quad(g, vzf, oz + 4, ox, d);
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            W[r] = a[r];
+            W[4 + r] = c[r];
+            W[8 + r] = d[r];
+        }
+    }
+    float Xp[N][4], Xm[N][4];                 // v_x at ox + l - 1 and ox - l
+#pragma unroll
+    for (int l = 1; l <= N; l++) {
+        quad(g, vxf, oz, ox + l - 1, Xp[l - 1]);
+        quad(g, vxf, oz, ox - l, Xm[l - 1]);
+    }
+    float pv[4], Kv[4];
+    put(pv, ld4(f.p + sh + k));
+    put(Kv, ld4(g.K + k));
+    float lpv[4];
+    if (MODE == REC) put(lpv, ld4(lpall + sh + k));
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        if (!n.mz[r]) continue;
+        float div = 0.0f;
+#pragma unroll
+        for (int l = 1; l <= N; l++)
+            div += g.c[0][l - 1] * (W[4 + r + l - 1] - W[4 + r - l]) + g.c[1][l - 1] * (Xp[l - 1][r] - Xm[l - 1][r]);
+        if (MODE == REC) {
+            const int z = oz + r;
+            const long long kp = (long long)n.s * g.nphys + (z - g.L[0]) +
+                                 (long long)(g.H[0] - g.L[0] + 1) * (ox - g.L[1]);
+            acc[kp] += lpv[r] * (img_mode == 0 ? div : pv[r]);
+            float pn = pv[r] + g.dt * Kv[r] * div;
+            const Stencil &st = b.src[n.s];
+            const int t0 = z - st.first[0], t1 = ox - st.first[1];
+            if (t0 >= 0 && t0 < st.cnt[0] && t1 >= 0 && t1 < st.cnt[1])
+                pn -= src_scale * stf[step] * st.w[0][t0] * st.w[1][t1] * st.w[2][0];
+            const bool keep = in_range(z, n.plo[0], n.phi[0]) && in_range(ox, n.plo[1], n.phi[1]);
+            pv[r] = keep ? pn : 0.0f;
+        } else {
+            pv[r] -= g.dt * Kv[r] * div;
+        }
+    }
+    *reinterpret_cast<float4 *>(f.p + sh + k) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+}
+
+// Tile grid over the box union [lo, hi] (z start rounded down to 4).
+dim3 grid2(const int lo[3], const int hi[3], int nshot, int &z0, int &x0)
+{
+    z0 = lo[0] & ~3;
+    x0 = lo[1];
+    const int nz = hi[0] - z0 + 1, nx = hi[1] - x0 + 1;
+    if (nz <= 0 || nx <= 0) return dim3(0, 0, 0);
+    return dim3((nz + 31) / 32, (nx + 31) / 32, nshot);
+}
+
+}  // namespace
+
+bool stencil2d_supported(const Grid &g) { return g.ndim == 2 && (g.N == 2 || g.N == 4) && g.ntot < (1LL << 31); }
+
+void launch2_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int step, int mode, const int lo[3],
+               const int hi[3])
+{
+    int z0, x0;
+    const dim3 grid = grid2(lo, hi, b.nshot, z0, x0);
+    if (grid.x == 0) return;
+    const dim3 block(8, 32);
+    cudaStream_t st = static_cast<cudaStream_t>(lc.stream);
+    if (g.N == 2) {
+        if (mode == FWD) k2_v<2, FWD><<<grid, block, 0, st>>>(g, b, f, step, z0, x0);
+        else if (mode == ADJ) k2_v<2, ADJ><<<grid, block, 0, st>>>(g, b, f, step, z0, x0);
+        else k2_v<2, REC><<<grid, block, 0, st>>>(g, b, f, step, z0, x0);
+    } else {
+        if (mode == FWD) k2_v<4, FWD><<<grid, block, 0, st>>>(g, b, f, step, z0, x0);
+        else if (mode == ADJ) k2_v<4, ADJ><<<grid, block, 0, st>>>(g, b, f, step, z0, x0);
+        else k2_v<4, REC><<<grid, block, 0, st>>>(g, b, f, step, z0, x0);
+    }
+    ++*lc.launches;
+}
+
+void launch2_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int step, int mode, const int lo[3],
+               const int hi[3], const float *lp, float *acc, int img_mode, const float *stf, float src_scale)
+{
+    int z0, x0;
+    const dim3 grid = grid2(lo, hi, b.nshot, z0, x0);
+    if (grid.x == 0) return;
+    const dim3 block(8, 32);
+    cudaStream_t st = static_cast<cudaStream_t>(lc.stream);
+    if (g.N == 2) {
+        if (mode == FWD) k2_p<2, FWD><<<grid, block, 0, st>>>(g, b, f, step, z0, x0, lp, acc, img_mode, stf, src_scale);
+        else if (mode == ADJ) k2_p<2, ADJ><<<grid, block, 0, st>>>(g, b, f, step, z0, x0, lp, acc, img_mode, stf, src_scale);
+        else k2_p<2, REC><<<grid, block, 0, st>>>(g, b, f, step, z0, x0, lp, acc, img_mode, stf, src_scale);
+    } else {
+        if (mode == FWD) k2_p<4, FWD><<<grid, block, 0, st>>>(g, b, f, step, z0, x0, lp, acc, img_mode, stf, src_scale);
+        else if (mode == ADJ) k2_p<4, ADJ><<<grid, block, 0, st>>>(g, b, f, step, z0, x0, lp, acc, img_mode, stf, src_scale);
+        else k2_p<4, REC><<<grid, block, 0, st>>>(g, b, f, step, z0, x0, lp, acc, img_mode, stf, src_scale);
+    }
+    ++*lc.launches;
+}
+
+}  // namespace smi
