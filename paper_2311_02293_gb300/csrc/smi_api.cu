@@ -582,11 +582,10 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     launch_fwd_corrections(lc, g, b, F, it, true, blo, bhi);
                     launch3_p(lc, mF, nullptr, g, b, F, it, 0, d_wait, nullptr, 0, nullptr, 0.0f);
                     launch_fwd_corrections(lc, g, b, F, it, false, blo, bhi);
-                } else if (fast2) {
+                } else if (fast2) {                    // CPML and (it < nt) the source inline
                     launch2_v(lc, g, b, F, it, 0, blo, bhi);
-                    launch_fwd_corrections(lc, g, b, F, it, true, blo, bhi);
-                    launch2_p(lc, g, b, F, it, 0, blo, bhi, nullptr, nullptr, 0, nullptr, 0.0f);
-                    launch_fwd_corrections(lc, g, b, F, it, false, blo, bhi);
+                    launch2_p(lc, g, b, F, it, 0, blo, bhi, nullptr, nullptr, 0, it < S.nt ? S.stf : nullptr,
+                              (float)S.src_scale);
                 } else {
                     const long long work = box_points(blo, bhi);
                     launch_fwd_v(lc, g, b, F, it, work);
@@ -594,7 +593,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 }
                 tm.end();
                 if (it < S.nt) {
-                    launch_inject_source(lc, g, b, F.p, S.stf, it, (float)S.src_scale);
+                    if (!fast2) launch_inject_source(lc, g, b, F.p, S.stf, it, (float)S.src_scale);
                     if (max_rec > 0) launch_gather(lc, g, b, F.p, seis, d_soff, S.nt, it);
                 }
                 for (int s = 0; s < nb_shot; s++) {
@@ -668,10 +667,8 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     launch3_v(lc, mA, g, b, A, mrev, 1, d_wait);
                     launch_adj_corrections(lc, g, b, A, mrev, false, blo, bhi);
                     launch3_p(lc, mA, nullptr, g, b, A, mrev, 1, d_wait, nullptr, 0, nullptr, 0.0f);
-                } else if (fast2) {
-                    launch_adj_corrections(lc, g, b, A, mrev, true, blo, bhi);
+                } else if (fast2) {                    // transposed CPML inline in the 2D kernels
                     launch2_v(lc, g, b, A, mrev, 1, blo, bhi);
-                    launch_adj_corrections(lc, g, b, A, mrev, false, blo, bhi);
                     launch2_p(lc, g, b, A, mrev, 1, blo, bhi, nullptr, nullptr, 0, nullptr, 0.0f);
                 } else {
                     const long long work = box_points(blo, bhi);

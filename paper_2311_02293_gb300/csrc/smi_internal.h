@@ -194,9 +194,9 @@ void launch_recon_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f
                     float src_scale, long long work);
 void launch_recon_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int it, long long work);
 
-// 2D kernels (smi_stencil2d.cu): mode 0 forward, 1 adjoint (interior
-// update; CPML by the band kernels), 2 reconstruction + imaging; [lo, hi] =
-// the batch's box union (for mode 2 within the physical domain).
+// 2D kernels (smi_stencil2d.cu): mode 0 forward, 1 adjoint (both with the
+// CPML terms inline), 2 reconstruction + imaging; [lo, hi] = the batch's box
+// union (for mode 2 within the physical domain).
 bool stencil2d_supported(const Grid &g);
 void launch2_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int step, int mode, const int lo[3],
                const int hi[3]);

@@ -3,11 +3,15 @@
 // Two kernels advance one half of a leap-frog step each (Sec. 2.1 update
 // equations): k2_v updates v_z and v_x from p, k2_p updates p from them.
 // Modes:
-//   FWD / ADJ  the interior update, on the computing box of the forward
-//              (source) or adjoint (receiver) run; the CPML terms are added
-//              by the band kernels of smi_kernels.cu (for the adjoint: the
-//              transposed terms, applied before these kernels), so the
-//              adjoint in "same solver" form runs this same code;
+//   FWD  forward update on the computing box of the source, with the CPML
+//        memory variables (Sec. 2.1, Komatitsch & Martin) inline;
+//   ADJ  the exact discrete adjoint in "same solver" form on the box of the
+//        receivers: the interior scheme applied to operands that carry the
+//        transposed CPML terms -- in the slabs D_a acts on
+//        lp + Ap_a (lp + phi_a) (velocity kernel) or
+//        lv_a + Av_a (lv_a + chi_a) (pressure kernel) instead of the plain
+//        field -- and the memory variables chi_a, phi_a updated at the
+//        thread's own nodes;
 //   REC        source-field reconstruction backwards in time (Sec. 4.2) on
 //              the physical domain inside the forward box of the step,
 //              fused with the imaging / gradient accumulation in k2_p;
@@ -87,7 +91,48 @@ __device__ __forceinline__ float buoy2(float r0, float r1, bool last)
     return last ? __fdividef(1.0f, r0) : __fdividef(2.0f, r0 + r1);
 }
 
-// FWD / ADJ: v_a -= dt b_a D_a p.  REC: v_a += dt b_a D_a p on
+// CPML slabs: nodes 0..nb-1 and ne-nb-1..ne-1 of an axis (the latter covers
+// the first v node of the high layer).  Slab arrays of one shot: axis z at
+// js + S x, axis x at z + ne_z js (js = index inside the slab).
+__device__ __forceinline__ bool slab2(const Grid &g, int a, int j) { return j < g.nb || j >= g.ne[a] - g.nb - 1; }
+__device__ __forceinline__ int js2(const Grid &g, int a, int j) { return j < g.nb ? j : j - (g.ne[a] - 2 * g.nb - 1); }
+__device__ __forceinline__ int zslab_idx(const Grid &g, int z, int x) { return js2(g, 0, z) + g.S * x; }
+__device__ __forceinline__ int xslab_idx(const Grid &g, int z, int x) { return z + g.ne[0] * js2(g, 1, x); }
+
+// ADJ: operand q -> q + A (q + m) at the slab nodes of a z window W
+// (W[e] at z = oz - 4 + e, column x) and of the x taps, m the memory
+// variable of the axis (shot's slab arrays mz_s, mx_s), A = coefficient
+// table of the axis.
+template <int N>
+__device__ __forceinline__ void adj_operand(const Grid &g, int oz, int ox, float (&W)[12], float (&Xp)[N][4],
+                                            float (&Xm)[N][4], int xp0, int xm0, const float *Az,
+                                            const float *Ax, const float *mz_s, const float *mx_s)
+{
+    if (oz - 4 < g.nb || oz + 7 >= g.ne[0] - g.nb - 1) {       // window reaches a z slab
+#pragma unroll
+        for (int e = 0; e < 12; e++) {
+            const int z = oz - 4 + e;
+            if (z >= 0 && z < g.ne[0] && slab2(g, 0, z)) W[e] += Az[z] * (W[e] + mz_s[zslab_idx(g, z, ox)]);
+        }
+    }
+#pragma unroll
+    for (int l = 1; l <= N; l++) {
+#pragma unroll
+        for (int side = 0; side < 2; side++) {
+            const int x = side == 0 ? ox + xp0 + l : ox + xm0 - l;
+            float(&X)[4] = side == 0 ? Xp[l - 1] : Xm[l - 1];
+            if (x < 0 || x >= g.ne[1] || !slab2(g, 1, x)) continue;
+            const float A = Ax[x];
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+                if (oz + r < g.ne[0]) X[r] += A * (X[r] + mx_s[xslab_idx(g, oz + r, x)]);
+        }
+    }
+}
+
+// FWD: v_a -= dt b_a (D_a p + psi_a), psi_a <- Bv psi_a + Av D_a p in the
+// slabs.  ADJ: chi_a <- Bv (chi_a + lv_a) at own slab nodes, then
+// lv_a -= dt b_a D_a[lp + Ap_a (lp + phi_a)].  REC: v_a += dt b_a D_a p on
 // L_a+N-1 .. H_a-N along a (elsewhere v_a keeps its saved value), zero
 // outside the previous box.
 template <int N, int MODE>
@@ -122,6 +167,9 @@ __global__ void __launch_bounds__(256) k2_v(Grid g, Batch b, Fields f, int step,
             quad(g, p, oz, ox - l + 1, Xm[l - 1]);
         }
     }
+    if (MODE == ADJ)
+        adj_operand<N>(g, oz, ox, W, Xp, Xm, 0, 1, g.cpa[0], g.cpa[1], f.psiv[0] + n.s * g.slab_n[0],
+                       f.psiv[1] + n.s * g.slab_n[1]);
     float rho0[4], rx[4], vz[4], vx[4];
     put(rho0, ld4(g.rho + k));
     const bool lastx = ox + 1 >= g.ne[1];
@@ -136,6 +184,8 @@ __global__ void __launch_bounds__(256) k2_v(Grid g, Batch b, Fields f, int step,
             keep[r] = in_range(oz + r, n.plo[0], n.phi[0]) && in_range(ox, n.plo[1], n.phi[1]);
     }
     const bool rxm = in_range(ox, g.L[1] + N - 1, g.H[1] - N);
+    const bool sx = MODE != REC && slab2(g, 1, ox);
+    float *mz_s = f.psip[0] + n.s * g.slab_n[0], *mx_s = f.psip[1] + n.s * g.slab_n[1];
 #pragma unroll
     for (int r = 0; r < 4; r++) {
         if (!n.mz[r]) continue;
@@ -151,18 +201,40 @@ __global__ void __launch_bounds__(256) k2_v(Grid g, Batch b, Fields f, int step,
         if (MODE == REC) {
             if (in_range(z, g.L[0] + N - 1, g.H[0] - N)) vz[r] = keep[r] ? vz[r] + g.dt * bz * dz : 0.0f;
             if (rxm) vx[r] = keep[r] ? vx[r] + g.dt * bx * dx : 0.0f;
-        } else {
-            vz[r] -= g.dt * bz * dz;
-            vx[r] -= g.dt * bx * dx;
+            continue;
         }
+        if (slab2(g, 0, z)) {
+            float &m = mz_s[zslab_idx(g, z, ox)];
+            if (MODE == FWD) {
+                const float ps = g.cvb[0][z] * m + g.cva[0][z] * dz;
+                m = ps;
+                dz += ps;
+            } else {
+                m = g.cvb[0][z] * (m + vz[r]);            // deferred chi update, lv before this step
+            }
+        }
+        if (sx) {
+            float &m = mx_s[xslab_idx(g, z, ox)];
+            if (MODE == FWD) {
+                const float ps = g.cvb[1][ox] * m + g.cva[1][ox] * dx;
+                m = ps;
+                dx += ps;
+            } else {
+                m = g.cvb[1][ox] * (m + vx[r]);
+            }
+        }
+        vz[r] -= g.dt * bz * dz;
+        vx[r] -= g.dt * bx * dx;
     }
     *reinterpret_cast<float4 *>(f.v[0] + sh + k) = make_float4(vz[0], vz[1], vz[2], vz[3]);
     *reinterpret_cast<float4 *>(f.v[1] + sh + k) = make_float4(vx[0], vx[1], vx[2], vx[3]);
 }
 
-// FWD / ADJ: p -= dt kappa (D_z v_z + D_x v_x).  REC: acc += lp * (div v |
-// p^{it+1}), p^{it} = p^{it+1} + dt kappa div v - dt stf w / dV, zero
-// outside the previous box.
+// FWD: p -= dt kappa sum_a (D_a v_a + psi_a), psi_a <- Bp psi_a + Ap D_a v_a
+// in the slabs, then (stf not null) p += dt stf w / dV at the source stencil.  ADJ: phi_a <- Bp (phi_a + lp) at own slab nodes (lp before
+// this step), then lp -= dt kappa sum_a D_a[lv_a + Av_a (lv_a + chi_a)].
+// REC: acc += lp * (div v | p^{it+1}), p^{it} = p^{it+1} + dt kappa div v -
+// dt stf w / dV, zero outside the previous box.
 template <int N, int MODE>
 __global__ void __launch_bounds__(256) k2_p(Grid g, Batch b, Fields f, int step, int z0, int x0, const float *lpall,
                                             float *acc, int img_mode, const float *stf, float src_scale)
@@ -191,20 +263,28 @@ __global__ void __launch_bounds__(256) k2_p(Grid g, Batch b, Fields f, int step,
         quad(g, vxf, oz, ox + l - 1, Xp[l - 1]);
         quad(g, vxf, oz, ox - l, Xm[l - 1]);
     }
+    if (MODE == ADJ)
+        adj_operand<N>(g, oz, ox, W, Xp, Xm, -1, 0, g.cva[0], g.cva[1], f.psip[0] + n.s * g.slab_n[0],
+                       f.psip[1] + n.s * g.slab_n[1]);
     float pv[4], Kv[4];
     put(pv, ld4(f.p + sh + k));
     put(Kv, ld4(g.K + k));
     float lpv[4];
     if (MODE == REC) put(lpv, ld4(lpall + sh + k));
+    const bool sx = MODE != REC && slab2(g, 1, ox);
+    float *mz_s = f.psiv[0] + n.s * g.slab_n[0], *mx_s = f.psiv[1] + n.s * g.slab_n[1];
 #pragma unroll
     for (int r = 0; r < 4; r++) {
         if (!n.mz[r]) continue;
-        float div = 0.0f;
+        float dz = 0.0f, dx = 0.0f;
 #pragma unroll
-        for (int l = 1; l <= N; l++)
-            div += g.c[0][l - 1] * (W[4 + r + l - 1] - W[4 + r - l]) + g.c[1][l - 1] * (Xp[l - 1][r] - Xm[l - 1][r]);
+        for (int l = 1; l <= N; l++) {
+            dz += g.c[0][l - 1] * (W[4 + r + l - 1] - W[4 + r - l]);
+            dx += g.c[1][l - 1] * (Xp[l - 1][r] - Xm[l - 1][r]);
+        }
+        const int z = oz + r;
         if (MODE == REC) {
-            const int z = oz + r;
+            const float div = dz + dx;
             const long long kp = (long long)n.s * g.nphys + (z - g.L[0]) +
                                  (long long)(g.H[0] - g.L[0] + 1) * (ox - g.L[1]);
             acc[kp] += lpv[r] * (img_mode == 0 ? div : pv[r]);
@@ -215,8 +295,34 @@ __global__ void __launch_bounds__(256) k2_p(Grid g, Batch b, Fields f, int step,
                 pn -= src_scale * stf[step] * st.w[0][t0] * st.w[1][t1] * st.w[2][0];
             const bool keep = in_range(z, n.plo[0], n.phi[0]) && in_range(ox, n.plo[1], n.phi[1]);
             pv[r] = keep ? pn : 0.0f;
-        } else {
-            pv[r] -= g.dt * Kv[r] * div;
+            continue;
+        }
+        if (slab2(g, 0, z)) {
+            float &m = mz_s[zslab_idx(g, z, ox)];
+            if (MODE == FWD) {
+                const float ps = g.cpb[0][z] * m + g.cpa[0][z] * dz;
+                m = ps;
+                dz += ps;
+            } else {
+                m = g.cpb[0][z] * (m + pv[r]);            // phi update, lp before this step
+            }
+        }
+        if (sx) {
+            float &m = mx_s[xslab_idx(g, z, ox)];
+            if (MODE == FWD) {
+                const float ps = g.cpb[1][ox] * m + g.cpa[1][ox] * dx;
+                m = ps;
+                dx += ps;
+            } else {
+                m = g.cpb[1][ox] * (m + pv[r]);
+            }
+        }
+        pv[r] -= g.dt * Kv[r] * (dz + dx);
+        if (MODE == FWD && stf) {                // source injection of this step (Algorithm 2)
+            const Stencil &st = b.src[n.s];
+            const int t0 = z - st.first[0], t1 = ox - st.first[1];
+            if (t0 >= 0 && t0 < st.cnt[0] && t1 >= 0 && t1 < st.cnt[1])
+                pv[r] += src_scale * stf[step] * st.w[0][t0] * st.w[1][t1] * st.w[2][0];
         }
     }
     *reinterpret_cast<float4 *>(f.p + sh + k) = make_float4(pv[0], pv[1], pv[2], pv[3]);
