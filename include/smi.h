@@ -114,6 +114,9 @@ typedef struct {
     void *stream;             /* cudaStream_t to run on; NULL = the legacy default stream */
     int max_batch;            /* shots propagated together in one launch; 0 = automatic */
     int profile;              /* 1: time the stencil kernels with CUDA events (smi_last_stats) */
+    int img_norm;             /* smi_rtm only: 0 the zero-lag cross-correlation (Eq. rtmimage); 1 each
+                                 shot's image divided by its source illumination sum_t p_s^2 + eps,
+                                 eps = 1e-3 of the shot's largest illumination (Sec. 2.3) */
 } smi_opts;
 
 /* Per-call measurements, filled for the calling thread's last call.  Index

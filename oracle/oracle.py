@@ -286,7 +286,8 @@ def adjoint(prob: Problem, vp, rho, src, rec, res, box_mode: int = 0) -> np.ndar
 
 def gradient(prob: Problem, vp, rho, stf, src, rec, dobs, mode: str = "fwi", recon: bool = True):
     """One shot of Algorithm 2.  mode 'fwi': (misfit, dJ/dVp, seis);
-    mode 'rtm': (0.0, image, seis).  Output arrays have prob.shape."""
+    mode 'rtm': (0.0, image, seis); mode 'rtm_norm': (0.0, image normalised
+    by the source illumination, seis).  Output arrays have prob.shape."""
     keep, vp_p, rho_p = _model(prob, vp, rho)
     stf_a, stf_p = _d(stf)
     src_a, src_p = _pts(src)
@@ -299,7 +300,7 @@ def gradient(prob: Problem, vp, rho, stf, src, rec, dobs, mode: str = "fwi", rec
     par = prob.par()
     dp = ctypes.POINTER(ctypes.c_double)
     _check(lib().orc_gradient(ctypes.byref(par), vp_p, rho_p, stf_p, src_p, len(rec_a), rec_p,
-                              dobs_p, 0 if mode == "fwi" else 1, int(recon), ctypes.byref(J),
+                              dobs_p, {"fwi": 0, "rtm": 1, "rtm_norm": 2}[mode], int(recon), ctypes.byref(J),
                               out.ctypes.data_as(dp), seis.ctypes.data_as(dp)))
     return J.value, out, seis
 

@@ -873,6 +873,10 @@ int orc_adjoint(const orc_par *par, const double *vp, const double *rho, const d
  *           the receiver field kappa*pbar (which obeys the forward equations,
  *           Eq. adj) with the source field at the same time level
  *           (Eq. rtmimage).
+ *   mode 2: the image of mode 1 divided by the shot's source illumination
+ *           sum_it (p^{it+1})^2 + eps, eps = 1e-3 max_x of the illumination
+ *           (the normalised imaging condition of Sec. 2.3; eps is a
+ *           reading).
  * pbar(it) is the adjoint of p^{it+1} after the receivers of step it have
  * been injected.  recon = 1 rebuilds the source field backwards from the
  * saved boundary bands (Sec. 4.2, every dr-th step, interpolated in time
@@ -891,7 +895,11 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
     stencil_t sst, *rst = calloc(nrec > 0 ? nrec : 1, sizeof(stencil_t));
     double *seis = malloc(sizeof(double) * ((long)g.nt * nrec + 1));
     double *acc = calloc(g.ntot, sizeof(double));
-    if (!rst || !seis || !acc) { free(rst); free(seis); free(acc); grid_free(&g); return ORC_ERR_NOMEM; }
+    double *ill = mode == 2 ? calloc(g.ntot, sizeof(double)) : NULL;
+    if (!rst || !seis || !acc || (mode == 2 && !ill)) {
+        free(rst); free(seis); free(acc); free(ill); grid_free(&g);
+        return ORC_ERR_NOMEM;
+    }
     rc = point_stencil(&g, src, par->kaiser_b, &sst);
     for (int r = 0; r < nrec && !rc; r++) rc = point_stencil(&g, rec + 3 * r, par->kaiser_b, &rst[r]);
     state_t s, ad;
@@ -973,6 +981,7 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
                 acc[k] += -g.dt * ad.p[k] * div;
             } else {
                 acc[k] += g.K[k] * ad.p[k] * s.p[k];
+                if (mode == 2) ill[k] += s.p[k] * s.p[k];
             }
         }
         int lo[3], hi[3];
@@ -986,12 +995,19 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
         }
     }
     {
+        double eps = 0.0;
+        if (mode == 2) {
+            for (long k = 0; k < g.ntot; k++) if (ill[k] > eps) eps = ill[k];
+            eps *= 1e-3;
+        }
         long c = 0;
         for (int i3 = g.L[2]; i3 <= g.H[2]; i3++)
         for (int i2 = g.L[1]; i2 <= g.H[1]; i2++)
         for (int i1 = g.L[0]; i1 <= g.H[0]; i1++, c++) {
             long k = IDX(&g, i1, i2, i3);
-            if (mode == 0) {
+            if (mode == 2) {
+                out[c] = acc[k] / (ill[k] + eps);
+            } else if (mode == 0) {
                 /* dJ/dVp = dJ/dkappa * dkappa/dVp = dJ/dkappa * 2 rho Vp */
                 out[c] = acc[k] * 2.0 * rho[c] * vp[c];
             } else {
@@ -1007,6 +1023,7 @@ done:
     free(store_p);
     for (int a = 0; a < 3; a++) free(store_v[a]);
     free(acc);
+    free(ill);
     free(seis);
     free(rst);
     grid_free(&g);

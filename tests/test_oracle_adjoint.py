@@ -203,3 +203,18 @@ def _rec_weight(prob, r, iz, ix):
         j = i + prob.nb - first
         w *= wts[j] if 0 <= j < len(wts) else 0.0
     return w
+
+
+def test_normalised_image_is_the_image_over_the_forward_illumination():
+    """Normalised imaging condition (Sec. 2.3): the oracle's image divided
+    by sum_it (p^{it+1})^2 + eps, eps = 1e-3 of its maximum, where the
+    illumination here comes from the stored forward snapshots instead of
+    the reconstructed source field."""
+    w = S.tiny_2d(nz=40, nx=44, nt=120, nb=8, order=8, src=(10, 20))
+    prob = O.Problem(w.n, w.d, w.nt, w.dt, order=w.order, nb=w.nb, fm=w.fm)
+    dobs, snaps = O.forward(prob, w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], snapshots=True)
+    _, img, _ = O.gradient(prob, w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs, mode="rtm")
+    _, nimg, _ = O.gradient(prob, w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs, mode="rtm_norm")
+    ill = np.sum(snaps ** 2, axis=0)
+    ref = img / (ill + 1e-3 * ill.max())
+    assert np.linalg.norm(nimg - ref) <= 1e-9 * np.linalg.norm(ref)
