@@ -77,6 +77,7 @@ struct Setup {
     int ndim = 0, n[3] = {1, 1, 1};
     int nshot = 0, nt = 0;
     int dr = 1, nsamp = 0, nt_fwd = 0;     // boundary decimation: stored samples, forward steps
+    int img_norm = 0;                      // normalised RTM image
     long long nrec_total = 0;
     std::vector<int> rec_offset;
     std::vector<Stencil> src_st, rec_st;
@@ -149,6 +150,7 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     S.nshot = geo->nshot;
     S.nt = w->nt;
     S.dr = o->dr;
+    S.img_norm = o->img_norm ? 1 : 0;
     S.nsamp = band_samples(S.nt, S.dr);
     S.nt_fwd = forward_steps(S.nt, S.dr);
     S.rec_offset.assign(geo->rec_offset, geo->rec_offset + geo->nshot + 1);
@@ -345,7 +347,7 @@ size_t per_shot_bytes(const Setup &S, int kind)
         b += (size_t)S.nsamp * S.bands.count * band_bytes(S.bands.prec);   // saved bands
         b += (size_t)S.nsamp * 6 * 4;                                  // band scales
         if (S.dr > 1) b += fields;                                     // state kept during the continuation
-        b += (size_t)g.nphys * 4;                                      // accumulator
+        b += (size_t)g.nphys * 4 * (kind == 1 && S.img_norm ? 2 : 1);  // accumulator (+ illumination)
         b += (size_t)S.nt * maxrec * 4 * 2;                            // seis + residual
     }
     return b;
@@ -482,6 +484,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         launch_zero(lc, d_wait, sizeof(unsigned));
         const bool fast3 = stencil3d_supported(g);
         const bool fast2 = stencil2d_supported(g);
+        const bool norm = kind == 1 && S.img_norm;       // normalised RTM image
 
         size_t batch_peak = 0;                   // largest batch arena (fields, bands, accumulators)
         for (int s0 = 0; s0 < S.nshot; s0 += B) {
@@ -510,6 +513,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                                       : ba.get<float>(std::max<long long>(1, batch_seis));
             Bands bd = S.bands;
             float *res = nullptr, *acc = nullptr, *keep = nullptr;
+            unsigned *norm_mx = nullptr;
             double *partials = nullptr;
             const int npart = 256;
             if (kind != 0) {
@@ -523,7 +527,8 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 bd.scale = ba.get<float>((size_t)nb_shot * S.nsamp * 6);
                 if (S.dr > 1) keep = ba.get<float>((size_t)(1 + g.ndim) * g.ntot * nb_shot);
                 res = ba.get<float>(std::max<long long>(1, batch_seis));
-                acc = ba.get<float>((size_t)g.nphys * nb_shot);
+                acc = ba.get<float>((size_t)g.nphys * nb_shot * (norm ? 2 : 1));   // [images | illuminations]
+                if (norm) norm_mx = ba.get<unsigned>(nb_shot);
                 partials = ba.get<double>(npart);
             }
             if (!ba.ok) return fail(SMI_ERR_NOMEM, "device allocation for a batch of %d shots failed", nb_shot);
@@ -631,8 +636,9 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 launch_zero(lc, A.psip[a], sizeof(float) * g.slab_n[a] * nb_shot);
                 launch_zero(lc, A.psiv[a], sizeof(float) * g.slab_n[a] * nb_shot);
             }
-            launch_zero(lc, acc, sizeof(float) * g.nphys * nb_shot);
-            const int mode = (kind == 2 || kind == 3) ? 0 : 1;     // 0: gradient, 1: image
+            launch_zero(lc, acc, sizeof(float) * g.nphys * nb_shot * (norm ? 2 : 1));
+            // 0: gradient, 1: image, 2: image and source illumination
+            const int mode = (kind == 2 || kind == 3) ? 0 : (norm ? 2 : 1);
             for (int it = S.nt - 1; it >= 0; it--) {
                 const int mrev = S.nt - 1 - it;
                 if (max_rec > 0) launch_adj_inject(lc, g, b, A.p, res, d_soff, S.nt, it);
@@ -689,7 +695,8 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 }
             }
             launch_nonfinite(lc, acc, g.nphys * nb_shot, d_flag);
-            launch_reduce_shots(lc, g, acc, nb_shot, d_img, s0 > 0);
+            if (norm) launch_reduce_norm(lc, g, acc, nb_shot, norm_mx, d_img, s0 > 0);
+            else launch_reduce_shots(lc, g, acc, nb_shot, d_img, s0 > 0);
             // batch buffers are released (stream-ordered) when `ba` goes out of scope
         }
         if (kind == 2 || kind == 3) launch_finalize_grad(lc, g.nphys, S.vp, g.dt, d_img);
@@ -745,6 +752,7 @@ void smi_opts_default(smi_opts *o)
     o->stream = nullptr;
     o->max_batch = 0;
     o->profile = 0;
+    o->img_norm = 0;
 }
 
 int smi_forward(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,

@@ -204,6 +204,10 @@ void launch2_p(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int
                const int hi[3], const float *lp, float *acc, int img_mode, const float *stf, float src_scale);
 void launch_reduce_shots(const LaunchCtx &lc, const Grid &g, const float *acc, int nshot,
                          float *out, int accumulate);
+// Normalised image: acc holds [nshot][nphys] images then [nshot][nphys]
+// illuminations; mx = nshot unsigned scratch.
+void launch_reduce_norm(const LaunchCtx &lc, const Grid &g, const float *acc, int nshot, unsigned *mx, float *out,
+                        int accumulate);
 void launch_finalize_grad(const LaunchCtx &lc, long long n, const float *vp, float dt,
                           float *g);
 void launch_nonfinite(const LaunchCtx &lc, const float *x, long long n, unsigned *flag);

@@ -711,6 +711,7 @@ k_recon_p(Grid g, Batch b, Fields f, const float *lpall, float *acc, int mode, c
                              (long long)(g.H[0] - g.L[0] + 1) *
                                  ((long long)(i[1] - g.L[1]) + (long long)(g.H[1] - g.L[1] + 1) * (i[2] - g.L[2]));
         acc[s * g.nphys + kp] += lp[k] * (mode == 0 ? dv : pk);
+        if (mode == 2) acc[(long long)(b.nshot + s) * g.nphys + kp] += pk * pk;   // illumination
         float pn = pk + g.dt * g.K[k] * dv;
         bool in_src = true;
         float w = 1.0f;
@@ -994,6 +995,31 @@ __global__ void k_reduce_shots(const float *acc, long long n, int nshot, float *
          t += (long long)gridDim.x * blockDim.x) {
         float s = accumulate ? out[t] : 0.0f;
         for (int k = 0; k < nshot; k++) s += acc[k * n + t];
+        out[t] = s;
+    }
+}
+
+// Normalised image (Sec. 2.3): per shot s the largest illumination ill_s,
+// then out (+)= sum_s acc_s / (ill_s + 1e-3 max ill_s), shots in order.
+// Illuminations are non-negative, so their bit patterns order as unsigned.
+__global__ void k_shot_max(const float *ill, long long n, unsigned *mx)
+{
+    const int s = blockIdx.y;
+    float m = 0.0f;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, ill[s * n + t]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(mx + s, __float_as_uint(m));
+}
+
+__global__ void k_reduce_norm(const float *acc, const float *ill, long long n, int nshot, const unsigned *mx,
+                              float *out, int accumulate)
+{
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        float s = accumulate ? out[t] : 0.0f;
+        for (int k = 0; k < nshot; k++) s += acc[k * n + t] / (ill[k * n + t] + 1e-3f * __uint_as_float(mx[k]));
         out[t] = s;
     }
 }
@@ -1335,6 +1361,16 @@ void launch_reduce_shots(const LaunchCtx &lc, const Grid &g, const float *acc, i
 {
     k_reduce_shots<<<blocks_for(g.nphys), kThreads, 0, S(lc)>>>(acc, g.nphys, nshot, out, accumulate);
     ++*lc.launches;
+}
+
+void launch_reduce_norm(const LaunchCtx &lc, const Grid &g, const float *acc, int nshot, unsigned *mx, float *out,
+                        int accumulate)
+{
+    const float *ill = acc + (long long)nshot * g.nphys;
+    cudaMemsetAsync(mx, 0, sizeof(unsigned) * nshot, S(lc));
+    k_shot_max<<<dim3(blocks_for(g.nphys), nshot), kThreads, 0, S(lc)>>>(ill, g.nphys, mx);
+    k_reduce_norm<<<blocks_for(g.nphys), kThreads, 0, S(lc)>>>(acc, ill, g.nphys, nshot, mx, out, accumulate);
+    *lc.launches += 2;
 }
 
 void launch_finalize_grad(const LaunchCtx &lc, long long n, const float *vp, float dt, float *gr)

@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(256) k2_v(Grid g, Batch b, Fields f, int step,
 // FWD: p -= dt kappa sum_a (D_a v_a + psi_a), psi_a <- Bp psi_a + Ap D_a v_a
 // in the slabs, then (stf not null) p += dt stf w / dV at the source stencil.  ADJ: phi_a <- Bp (phi_a + lp) at own slab nodes (lp before
 // this step), then lp -= dt kappa sum_a D_a[lv_a + Av_a (lv_a + chi_a)].
-// REC: acc += lp * (div v | p^{it+1}), p^{it} = p^{it+1} + dt kappa div v -
+// REC: acc += lp * (div v | p^{it+1}) (and, img_mode 2, the illumination
+// p^2 into the second half of acc), p^{it} = p^{it+1} + dt kappa div v -
 // dt stf w / dV, zero outside the previous box.
 template <int N, int MODE>
 __global__ void __launch_bounds__(256) k2_p(Grid g, Batch b, Fields f, int step, int z0, int x0, const float *lpall,
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(256) k2_p(Grid g, Batch b, Fields f, int step,
             const long long kp = (long long)n.s * g.nphys + (z - g.L[0]) +
                                  (long long)(g.H[0] - g.L[0] + 1) * (ox - g.L[1]);
             acc[kp] += lpv[r] * (img_mode == 0 ? div : pv[r]);
+            if (img_mode == 2) acc[(long long)b.nshot * g.nphys + kp] += pv[r] * pv[r];   // illumination
             float pn = pv[r] + g.dt * Kv[r] * div;
             const Stencil &st = b.src[n.s];
             const int t0 = z - st.first[0], t1 = ox - st.first[1];

@@ -840,6 +840,7 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
                         np[r] = pv[r];
                         if (!mz[r]) continue;
                         acc[accb + r] = accv[r] + lpv[r] * (img_mode == 0 ? div[r] : pv[r]);
+                        if (img_mode == 2) acc[(long long)b.nshot * g.nphys + accb + r] += pv[r] * pv[r];   // illumination
                         float pn = pv[r] + dt * Kv[r] * div[r];
                         const int t0 = z - st.first[0], t1 = ox - st.first[1], t2 = y - st.first[2];
                         if (t0 >= 0 && t0 < st.cnt[0] && t1 >= 0 && t1 < st.cnt[1] && t2 >= 0 && t2 < st.cnt[2])

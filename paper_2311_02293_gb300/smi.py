@@ -67,7 +67,7 @@ class smi_opts(ctypes.Structure):
                 ("dr", ctypes.c_int), ("use_box", ctypes.c_int), ("shell_prec", ctypes.c_int),
                 ("kaiser_b", ctypes.c_double), ("cpml_R", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("max_batch", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("img_norm", ctypes.c_int)]
 
 
 class smi_stats(ctypes.Structure):
@@ -155,6 +155,7 @@ class Problem:
     max_batch: int = 0
     profile: bool = False
     dr: int = 1             # boundary decimation ratio (Sec. 4.2)
+    img_norm: bool = False  # smi_rtm: normalise each shot's image by its source illumination
 
 
 def _geometry(srcs, recs):
@@ -201,6 +202,7 @@ def _opts(prob: Problem, stream):
     o.max_batch = prob.max_batch
     o.profile = int(prob.profile)
     o.dr = int(prob.dr)
+    o.img_norm = int(prob.img_norm)
     if stream is not None:
         o.stream = stream
     elif torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():

@@ -250,3 +250,20 @@ def test_long_adjoint_through_cpml_corners_3d(smi, order):
     img = smi.smi_rtm(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs, _dev(w.stf), _dev(dobs))
     _, ir, _ = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs, mode="rtm")
     assert _rel(img.cpu().numpy(), ir) <= IMG_TOL
+
+
+@pytest.mark.parametrize("case", ["2d_o8_on", "3d_o8_on"])
+def test_normalised_rtm_image_parity(smi, case):
+    """Normalised imaging condition (Sec. 2.3): per-shot image over the
+    shot's source illumination, summed over shots; two shots so that the
+    normalisation is per shot."""
+    w = SMALL[case]()
+    moved = w.srcs.copy()
+    moved[:, 1] += 3 * w.d[1]                          # a second shot 3 cells along x
+    srcs = np.concatenate([w.srcs, moved])
+    recs = [w.recs[0], w.recs[0]]
+    dobs = [O.forward(_oprob(w), w.vp, w.rho, w.stf, s, recs[0]) for s in srcs]
+    img = smi.smi_rtm(_dev(w.vp), _dev(w.rho), _gprob(smi, w, img_norm=True), srcs, recs, _dev(w.stf),
+                      [_dev(d.astype(np.float32)) for d in dobs])
+    ref = sum(O.gradient(_oprob(w), w.vp, w.rho, w.stf, s, recs[0], d, mode="rtm_norm")[1] for s, d in zip(srcs, dobs))
+    assert _rel(img.cpu().numpy(), ref) <= IMG_TOL
