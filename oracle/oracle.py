@@ -124,7 +124,7 @@ def lib():
         L.orc_forward.argtypes = [P, dp, dp, dp, dp, c_int, dp, dp, dp]
         L.orc_propagate.argtypes = [P, dp, dp] + [dp] * 10 + [c_int, c_int, dp, dp]
         L.orc_adjoint.argtypes = [P, dp, dp, dp, c_int, dp, dp, c_int, dp]
-        L.orc_gradient.argtypes = [P, dp, dp, dp, dp, c_int, dp, dp, c_int, c_int, dp, dp, dp]
+        L.orc_gradient.argtypes = [P, dp, dp, dp, dp, c_int, dp, dp, c_int, c_int, dp, dp, dp, dp]
         L.orc_reconstruct.argtypes = [P, dp, dp, dp, dp, dp]
         L.orc_check.argtypes = [P, dp, dp]
         L.orc_cpml_profile.argtypes = [P, dp, dp, c_int, c_int, dp, dp]
@@ -284,10 +284,12 @@ def adjoint(prob: Problem, vp, rho, src, rec, res, box_mode: int = 0) -> np.ndar
     return sbar
 
 
-def gradient(prob: Problem, vp, rho, stf, src, rec, dobs, mode: str = "fwi", recon: bool = True):
-    """One shot of Algorithm 2.  mode 'fwi': (misfit, dJ/dVp, seis);
-    mode 'rtm': (0.0, image, seis); mode 'rtm_norm': (0.0, image normalised
-    by the source illumination, seis).  Output arrays have prob.shape."""
+def gradient(prob: Problem, vp, rho, stf, src, rec, dobs, mode: str = "fwi", recon: bool = True,
+             with_rho: bool = False):
+    """One shot of Algorithm 2.  mode 'fwi': (misfit, dJ/dVp, seis), and
+    with_rho: (misfit, dJ/dVp, seis, dJ/drho at fixed Vp); mode 'rtm':
+    (0.0, image, seis); mode 'rtm_norm': (0.0, image normalised by the source
+    illumination, seis).  Output arrays have prob.shape."""
     keep, vp_p, rho_p = _model(prob, vp, rho)
     stf_a, stf_p = _d(stf)
     src_a, src_p = _pts(src)
@@ -296,12 +298,17 @@ def gradient(prob: Problem, vp, rho, stf, src, rec, dobs, mode: str = "fwi", rec
     assert dobs_a.size == prob.nt * len(rec_a)
     out = np.zeros(prob.shape)
     seis = np.zeros((prob.nt, len(rec_a)))
+    g_rho = np.zeros(prob.shape)
+    assert not with_rho or mode == "fwi"
     J = ctypes.c_double()
     par = prob.par()
     dp = ctypes.POINTER(ctypes.c_double)
     _check(lib().orc_gradient(ctypes.byref(par), vp_p, rho_p, stf_p, src_p, len(rec_a), rec_p,
                               dobs_p, {"fwi": 0, "rtm": 1, "rtm_norm": 2}[mode], int(recon), ctypes.byref(J),
-                              out.ctypes.data_as(dp), seis.ctypes.data_as(dp)))
+                              out.ctypes.data_as(dp), seis.ctypes.data_as(dp),
+                              g_rho.ctypes.data_as(dp) if with_rho else None))
+    if with_rho:
+        return J.value, out, seis, g_rho
     return J.value, out, seis
 
 

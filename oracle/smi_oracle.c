@@ -861,6 +861,71 @@ int orc_adjoint(const orc_par *par, const double *vp, const double *rho, const d
     return ORC_OK;
 }
 
+/* Density part of the gradient (Eq. gradrhokappa with rho varied at fixed
+ * Vp).  Step it sets v_a^{it+1/2} = v_a^{it-1/2} - dt b_a (d_a p + psi_a), and
+ * nothing else of the step depends on b_a, so
+ *   dJ/db_a = sum_it vbar_a^{it+1/2} (v_a^{it+1/2} - v_a^{it-1/2}) / b_a,
+ * with vbar_a^{it+1/2} the complete adjoint of v_a^{it+1/2} (what the adjoint
+ * velocity holds once the transposed pressure update of step it has run).
+ * Accumulated on the half nodes that touch a physical node: i_a in
+ * [L_a-1, H_a] along a, the other coordinates physical.  vold NULL: zero. */
+static void accumulate_gb(const grid_t *g, const state_t *ad, double *const vnew[3], double *const vold[3],
+                          double *gb[3])
+{
+    for (int a = 0; a < g->ndim; a++) {
+        int lo[3], hi[3];
+        for (int b = 0; b < 3; b++) { lo[b] = g->L[b]; hi[b] = g->H[b]; }
+        if (lo[a] > 0) lo[a]--;
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int i3 = lo[2]; i3 <= hi[2]; i3++)
+        for (int i2 = lo[1]; i2 <= hi[1]; i2++)
+        for (int i1 = lo[0]; i1 <= hi[0]; i1++) {
+            long k = IDX(g, i1, i2, i3);
+            double dv = vnew[a][k] - (vold ? vold[a][k] : 0.0);
+            gb[a][k] += ad->v[a][k] * dv / g->bu[a][k];
+        }
+    }
+}
+
+/* dJ/drho at fixed Vp on the physical nodes: kappa = rho Vp^2 gives
+ * Vp^2 dJ/dkappa; each half-node buoyancy b = 2 / (rho_i + rho_{i+1}) gives
+ * -b^2/2 dJ/db to both of its nodes (b = 1/rho at the last node of an axis:
+ * -b^2 dJ/db).  The CPML cells' rho is held fixed, like their kappa in the
+ * Vp gradient. */
+static int finish_rho(const grid_t *g, const double *vp, const double *acc, double *const gb[3], double *out_rho)
+{
+    double *gr = calloc(g->ntot, sizeof(double));
+    if (!gr) return ORC_ERR_NOMEM;
+    for (int a = 0; a < g->ndim; a++) {
+        int lo[3], hi[3];
+        for (int b = 0; b < 3; b++) { lo[b] = g->L[b]; hi[b] = g->H[b]; }
+        if (lo[a] > 0) lo[a]--;
+        for (int i3 = lo[2]; i3 <= hi[2]; i3++)
+        for (int i2 = lo[1]; i2 <= hi[1]; i2++)
+        for (int i1 = lo[0]; i1 <= hi[0]; i1++) {
+            int i[3] = {i1, i2, i3};
+            long k = IDX(g, i1, i2, i3);
+            double b = g->bu[a][k];
+            if (i[a] + 1 < g->ne[a] || g->periodic) {
+                i[a] = (i[a] + 1) % g->ne[a];
+                gr[k] += -0.5 * b * b * gb[a][k];
+                gr[IDX(g, i[0], i[1], i[2])] += -0.5 * b * b * gb[a][k];
+            } else {
+                gr[k] += -b * b * gb[a][k];
+            }
+        }
+    }
+    long c = 0;
+    for (int i3 = g->L[2]; i3 <= g->H[2]; i3++)
+    for (int i2 = g->L[1]; i2 <= g->H[1]; i2++)
+    for (int i1 = g->L[0]; i1 <= g->H[0]; i1++, c++) {
+        long k = IDX(g, i1, i2, i3);
+        out_rho[c] = vp[c] * vp[c] * acc[k] + gr[k];
+    }
+    free(gr);
+    return ORC_OK;
+}
+
 /* FWI misfit + gradient (mode 0) or RTM image (mode 1) of one shot
  * (Algorithm 2).
  *   mode 0: residual r = u - d, misfit J = 1/2 sum r^2 (Eq. objfwi, read with
@@ -883,10 +948,12 @@ int orc_adjoint(const orc_par *par, const double *vp, const double *rho, const d
  * when dr > 1); recon = 0 keeps every forward
  * state in memory (small grids only; tests).  The adjoint field uses the
  * receiver box when use_box is set (Sec. 4.1).
- * seis (optional): the forward seismograms [nt][nrec]. */
+ * seis (optional): the forward seismograms [nt][nrec].
+ * out_rho (optional, mode 0): dJ/drho at fixed Vp on the physical grid (see
+ * accumulate_gb). */
 int orc_gradient(const orc_par *par, const double *vp, const double *rho, const double *stf,
                  const double *src, int nrec, const double *rec, const double *dobs,
-                 int mode, int recon, double *misfit, double *out, double *seis_out)
+                 int mode, int recon, double *misfit, double *out, double *seis_out, double *out_rho)
 {
     grid_t g;
     int rc = grid_init(&g, par, vp, rho);
@@ -896,8 +963,18 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
     double *seis = malloc(sizeof(double) * ((long)g.nt * nrec + 1));
     double *acc = calloc(g.ntot, sizeof(double));
     double *ill = mode == 2 ? calloc(g.ntot, sizeof(double)) : NULL;
-    if (!rst || !seis || !acc || (mode == 2 && !ill)) {
-        free(rst); free(seis); free(acc); free(ill); grid_free(&g);
+    const int want_rho = out_rho && mode == 0;
+    double *gb[3] = {0}, *vsave[3] = {0};
+    int nomem = !rst || !seis || !acc || (mode == 2 && !ill);
+    for (int a = 0; a < g.ndim && want_rho; a++) {
+        gb[a] = calloc(g.ntot, sizeof(double));
+        vsave[a] = malloc(sizeof(double) * g.ntot);
+        nomem |= !gb[a] || !vsave[a];
+    }
+    if (nomem) {
+        free(rst); free(seis); free(acc); free(ill);
+        for (int a = 0; a < 3; a++) { free(gb[a]); free(vsave[a]); }
+        grid_free(&g);
         return ORC_ERR_NOMEM;
     }
     rc = point_stencil(&g, src, par->kaiser_b, &sst);
@@ -989,11 +1066,19 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
         else full_box(&g, lo, hi);
         adjoint_update_p(&g, &ad, lo, hi);
         adjoint_update_v(&g, &ad, lo, hi);
+        if (want_rho)
+            for (int a = 0; a < g.ndim; a++) memcpy(vsave[a], s.v[a], sizeof(double) * g.ntot);
         if (recon) {
             band_at(&g, bands, nband, nsamp, it, bandt);
             reconstruct_step(&g, &s, &sst, g.dt * stf[it] / g.dV, box, prev, bandt);
+            if (want_rho) accumulate_gb(&g, &ad, vsave, s.v, gb);
+        } else if (want_rho) {
+            double *vold[3] = {0};
+            for (int a = 0; a < g.ndim; a++) vold[a] = it > 0 ? store_v[a] + g.ntot * (long)(it - 1) : NULL;
+            accumulate_gb(&g, &ad, vsave, it > 0 ? vold : NULL, gb);
         }
     }
+    if (want_rho && (rc = finish_rho(&g, vp, acc, gb, out_rho))) goto done;
     {
         double eps = 0.0;
         if (mode == 2) {
@@ -1021,7 +1106,7 @@ done:
     free(bands);
     free(bandt);
     free(store_p);
-    for (int a = 0; a < 3; a++) free(store_v[a]);
+    for (int a = 0; a < 3; a++) { free(store_v[a]); free(gb[a]); free(vsave[a]); }
     free(acc);
     free(ill);
     free(seis);
