@@ -160,6 +160,23 @@ int smi_rtm(const smi_model *model, const smi_geometry *geom, const smi_wavelet 
 int smi_fwi_gradient(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
                      const smi_opts *opts, const float *dobs, double *misfit, float *grad_vp);
 
+/* FWI misfit (as smi_fwi_gradient) and its gradient in a parametrisation
+ * family (Sec. 2.2: family 1 = (Vp, rho), family 2 = (Vp, Ip) with
+ * Ip = rho Vp), from both parts of Eq. gradrhokappa by the chain rule:
+ *   dJ/dVp|rho = 2 rho Vp dJ/dkappa,   dJ/drho|Vp = Vp^2 dJ/dkappa + dJ/drho|kappa,
+ *   family 2:  dJ/dVp|Ip = dJ/dVp|rho - dJ/drho|Vp rho / Vp,  dJ/dIp = dJ/drho|Vp / Vp.
+ * dJ/drho|kappa is the exact discrete gradient through the half-node
+ * buoyancy 2 / (rho_i + rho_{i+1}); the CPML cells' rho and kappa are held
+ * fixed.  log_param = 1: gradients with respect to the logarithms of the
+ * parameters (each multiplied by its parameter), the log transform of
+ * Sec. 3.7.  grad1 (Vp), grad2 (rho or Ip): n1*n2*n3 floats each, host or
+ * device, both required; misfit may be NULL.  family outside {1, 2} or
+ * log_param outside {0, 1}: SMI_ERR_ARG.  Costs one extra set of source
+ * velocities per shot of a batch and one accumulator per axis. */
+int smi_fwi_gradient_family(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                            const smi_opts *opts, const float *dobs, int family, int log_param, double *misfit,
+                            float *grad1, float *grad2);
+
 /* Vector-Jacobian product of smi_forward with respect to Vp: for an upstream
  * gradient g = dL/dseis (adj_src, seis layout, host or device), writes
  * dL/dVp = sum over shots, receivers and samples of g * d seis / d Vp on the
@@ -173,7 +190,8 @@ int smi_forward_vjp(const smi_model *model, const smi_geometry *geom, const smi_
 
 /* Sizes a caller needs before a call: seismogram floats, image floats and
  * the device bytes the call will allocate (kind: 0 forward, 1 rtm, 2
- * gradient, 3 vector-Jacobian product).  Validates like the calls themselves (CFL, dispersion,
+ * gradient, 3 vector-Jacobian product, 4 gradient of a parametrisation
+ * family).  Validates like the calls themselves (CFL, dispersion,
  * positions) and launches one small reduction to find vmin/vmax.  Any
  * output pointer may be NULL. */
 int smi_query(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,

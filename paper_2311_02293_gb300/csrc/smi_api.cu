@@ -78,6 +78,7 @@ struct Setup {
     int nshot = 0, nt = 0;
     int dr = 1, nsamp = 0, nt_fwd = 0;     // boundary decimation: stored samples, forward steps
     int img_norm = 0;                      // normalised RTM image
+    bool rho_grad = false;                 // gradient with the density part (parametrisation families)
     long long nrec_total = 0;
     std::vector<int> rec_offset;
     std::vector<Stencil> src_st, rec_st;
@@ -348,6 +349,7 @@ size_t per_shot_bytes(const Setup &S, int kind)
         b += (size_t)S.nsamp * 6 * 4;                                  // band scales
         if (S.dr > 1) b += fields;                                     // state kept during the continuation
         b += (size_t)g.nphys * 4 * (kind == 1 && S.img_norm ? 2 : 1);  // accumulator (+ illumination)
+        if (S.rho_grad) b += (size_t)g.ndim * g.ntot * 4;              // velocities of the previous step
         b += (size_t)S.nt * maxrec * 4 * 2;                            // seis + residual
     }
     return b;
@@ -425,9 +427,12 @@ int finish_stream(cudaStream_t st)
 }
 
 // kind: 0 forward, 1 rtm, 2 gradient, 3 vector-Jacobian product of the
-// forward map with respect to vp (adjoint source given)
+// forward map with respect to vp (adjoint source given).  family > 0 (kind
+// 2): the gradient of parametrisation family 1 (Vp, rho) or 2 (Vp, Ip), of
+// the logarithms when logp, into img_out and img2_out.
 int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet *w, const smi_opts *o,
-        const float *dobs, float *seis_out, float *img_out, double *misfit_out)
+        const float *dobs, float *seis_out, float *img_out, double *misfit_out, float *img2_out = nullptr,
+        int family = 0, int logp = 0)
 {
     t_err.clear();
     memset(&t_stats, 0, sizeof t_stats);
@@ -446,6 +451,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         const Grid &g = S.g;
         LaunchCtx lc{st, &launches};
         const size_t nseis = (size_t)S.nt * S.nrec_total;
+        S.rho_grad = kind == 2 && family > 0;
         if (kind == 0 && !seis_out) return fail(SMI_ERR_ARG, "seis is null");
         if (kind != 0 && !dobs) return fail(SMI_ERR_ARG, kind == 3 ? "adj_src is null" : "dobs is null");
 
@@ -462,6 +468,15 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             if (rc) return rc;
             if (img_out) d_img = is_device_ptr(img_out) ? img_out : ar.get<float>((size_t)g.nphys);
             else d_img = ar.get<float>((size_t)g.nphys);
+        }
+        float *d_img2 = nullptr;
+        RhoAcc R{};
+        if (S.rho_grad) {
+            d_img2 = is_device_ptr(img2_out) ? img2_out : ar.get<float>((size_t)g.nphys);
+            for (int a = 0; a < g.ndim; a++) {
+                R.G[a] = ar.get<float>((size_t)g.ntot);
+                if (R.G[a]) launch_zero(lc, R.G[a], sizeof(float) * g.ntot);
+            }
         }
         if (!ar.ok) return fail(SMI_ERR_NOMEM, "device allocation of outputs failed");
 
@@ -530,6 +545,8 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 acc = ba.get<float>((size_t)g.nphys * nb_shot * (norm ? 2 : 1));   // [images | illuminations]
                 if (norm) norm_mx = ba.get<unsigned>(nb_shot);
                 partials = ba.get<double>(npart);
+                if (S.rho_grad)
+                    for (int a = 0; a < g.ndim; a++) R.vprev[a] = ba.get<float>((size_t)g.ntot * nb_shot);
             }
             if (!ba.ok) return fail(SMI_ERR_NOMEM, "device allocation for a batch of %d shots failed", nb_shot);
             batch_peak = std::max(batch_peak, ba.peak);
@@ -637,6 +654,9 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 launch_zero(lc, A.psiv[a], sizeof(float) * g.slab_n[a] * nb_shot);
             }
             launch_zero(lc, acc, sizeof(float) * g.nphys * nb_shot * (norm ? 2 : 1));
+            if (S.rho_grad)
+                for (int a = 0; a < g.ndim; a++)
+                    cudaMemcpyAsync(R.vprev[a], F.v[a], fbytes, cudaMemcpyDeviceToDevice, st);
             // 0: gradient, 1: image, 2: image and source illumination
             const int mode = (kind == 2 || kind == 3) ? 0 : (norm ? 2 : 1);
             for (int it = S.nt - 1; it >= 0; it--) {
@@ -682,6 +702,15 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     launch_adj_p(lc, g, b, A, mrev, work);
                 }
                 tm.end();
+                if (S.rho_grad) {                      // half nodes touching the physical domain
+                    IBox rb;
+                    batch_box(S.box_src, it, rb.lo, rb.hi);
+                    for (int a = 0; a < 3; a++) {
+                        rb.lo[a] = std::max(rb.lo[a], a < g.ndim ? g.L[a] - 1 : 0);
+                        rb.hi[a] = std::min(rb.hi[a], g.H[a]);
+                    }
+                    launch_rho_acc(lc, g, nb_shot, F, A, R, rb);
+                }
                 for (int s = 0; s < nb_shot; s++) {
                     int lo[3], hi[3];
                     box_bounds(g, S.box_rec.data() + 6 * (s0 + s), mrev, lo, hi);
@@ -699,13 +728,16 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             else launch_reduce_shots(lc, g, acc, nb_shot, d_img, s0 > 0);
             // batch buffers are released (stream-ordered) when `ba` goes out of scope
         }
-        if (kind == 2 || kind == 3) launch_finalize_grad(lc, g.nphys, S.vp, g.dt, d_img);
+        if (S.rho_grad) launch_finalize_family(lc, g, S.vp, S.rho, d_img, R, family, logp, d_img, d_img2);
+        else if (kind == 2 || kind == 3) launch_finalize_grad(lc, g.nphys, S.vp, g.dt, d_img);
 
         // outputs back to the host where needed
         if (kind == 0 && d_seis_out != seis_out)
             cudaMemcpyAsync(seis_out, d_seis_out, nseis * sizeof(float), cudaMemcpyDeviceToHost, st);
         if (kind != 0 && img_out && d_img != img_out)
             cudaMemcpyAsync(img_out, d_img, (size_t)g.nphys * sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (d_img2 && d_img2 != img2_out)
+            cudaMemcpyAsync(img2_out, d_img2, (size_t)g.nphys * sizeof(float), cudaMemcpyDeviceToHost, st);
         if (kind == 2 && misfit_out) {
             cudaMemcpyAsync(misfit_out, d_misfit, sizeof(double),
                             is_device_ptr(misfit_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
@@ -774,6 +806,16 @@ int smi_fwi_gradient(const smi_model *model, const smi_geometry *geom, const smi
     return run(2, model, geom, wav, opts, dobs, nullptr, grad_vp, misfit);
 }
 
+int smi_fwi_gradient_family(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                            const smi_opts *opts, const float *dobs, int family, int log_param, double *misfit,
+                            float *grad1, float *grad2)
+{
+    if (family != 1 && family != 2) return fail(SMI_ERR_ARG, "family must be 1 (Vp, rho) or 2 (Vp, Ip)");
+    if (log_param != 0 && log_param != 1) return fail(SMI_ERR_ARG, "log_param must be 0 or 1");
+    if (!grad1 || !grad2) return fail(SMI_ERR_ARG, "gradient outputs are null");
+    return run(2, model, geom, wav, opts, dobs, nullptr, grad1, misfit, grad2, family, log_param);
+}
+
 int smi_forward_vjp(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
                     const smi_opts *opts, const float *adj_src, float *grad_vp)
 {
@@ -787,7 +829,7 @@ int smi_query(const smi_model *model, const smi_geometry *geom, const smi_wavele
 {
     t_err.clear();
     if (!opts) return fail(SMI_ERR_ARG, "null options");
-    if (kind < 0 || kind > 3) return fail(SMI_ERR_ARG, "kind must be 0, 1, 2 or 3");
+    if (kind < 0 || kind > 4) return fail(SMI_ERR_ARG, "kind must be 0 .. 4");
     cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
     long long launches = 0;
     Setup S;
@@ -801,7 +843,9 @@ int smi_query(const smi_model *model, const smi_geometry *geom, const smi_wavele
             if (device_bytes) {
                 int B = S.nshot;
                 if (opts->max_batch > 0) B = std::min(B, opts->max_batch);
-                *device_bytes = ar.peak + (size_t)B * per_shot_bytes(S, kind);
+                S.rho_grad = kind == 4;
+                size_t extra = kind == 4 ? (size_t)S.g.ndim * S.g.ntot * 4 + (size_t)S.g.nphys * 4 : 0;
+                *device_bytes = ar.peak + extra + (size_t)B * per_shot_bytes(S, kind == 4 ? 2 : kind);
             }
         }
     }

@@ -210,6 +210,23 @@ void launch_reduce_norm(const LaunchCtx &lc, const Grid &g, const float *acc, in
                         int accumulate);
 void launch_finalize_grad(const LaunchCtx &lc, long long n, const float *vp, float dt,
                           float *g);
+// Density gradient (Eq. gradrhokappa): per axis, vprev = [nshot][ntot] source
+// velocities of the previous reverse step, G = [ntot] half-node sums of
+// lambda_v (v^{it+1/2} - v^{it-1/2}) over shots and steps.
+struct RhoAcc {
+    float *vprev[3];
+    float *G[3];
+};
+struct IBox {
+    int lo[3], hi[3];
+};
+// G += sum_s lambda_v (vprev - v) and vprev <- v over the nodes of box.
+void launch_rho_acc(const LaunchCtx &lc, const Grid &g, int nshot, Fields F, Fields A, RhoAcc r, IBox box);
+// (dJ/dm1, dJ/dm2) of parametrisation family 1 (Vp, rho) or 2 (Vp, Ip), of
+// the logarithms when logp; acc = summed lambda_p div v (physical grid); vp,
+// rho physical; g1 may alias acc.
+void launch_finalize_family(const LaunchCtx &lc, const Grid &g, const float *vp, const float *rho, const float *acc,
+                            RhoAcc r, int family, int logp, float *g1, float *g2);
 void launch_nonfinite(const LaunchCtx &lc, const float *x, long long n, unsigned *flag);
 // Sets the padded layout: px, ntot, nphys and the slab sizes (ne, nb, ndim set).
 void set_layout(Grid &g, const int n[3]);

@@ -1033,6 +1033,72 @@ __global__ void k_finalize_grad(long long n, const float *vp, float dt, float *g
         gr[t] = -2.0f * dt * gr[t] / vp[t];
 }
 
+// Density gradient (Eq. gradrhokappa, rho varied at fixed Vp).  Step it sets
+// v^{it+1/2} = v^{it-1/2} - dt b (D p + psi) and nothing else of the step
+// depends on b; with lambda_v = -b vbar and b = 2 / (rho_i + rho_{i+1}),
+// each half node gives half of G = sum_it lambda_v (v^{it+1/2} - v^{it-1/2})
+// to dJ/drho of both of its nodes (the b^2 of db/drho cancels the 1/b^2 of
+// vbar dv/db).  k_rho_acc runs at the end of reverse step it, when vprev
+// holds v^{it+1/2}, the source field v^{it-1/2} and the adjoint lambda_v of
+// v^{it+1/2}: G_a += sum_s lambda_v (vprev - v), then vprev <- v.
+__global__ void __launch_bounds__(kThreads) k_rho_acc(Grid g, int nshot, Fields F, Fields A, RhoAcc r, IBox box)
+{
+    BoxIter bi;
+    bi.set(box.lo, box.hi);
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < bi.vol;
+         q += (long long)gridDim.x * blockDim.x) {
+        int i[3];
+        bi.at(q, i);
+        const long long k = gidx(g, i[0], i[1], i[2]);
+        for (int a = 0; a < g.ndim; a++) {
+            float c = 0.0f;
+            for (int s = 0; s < nshot; s++) {
+                const long long kk = s * g.ntot + k;
+                const float v = F.v[a][kk];
+                c += A.v[a][kk] * (r.vprev[a][kk] - v);
+                r.vprev[a][kk] = v;
+            }
+            r.G[a][k] += c;
+        }
+    }
+}
+
+// Outputs of a gradient with a parametrisation family (Sec. 2.2).  acc =
+// sum over shots and steps of lambda_p div v on the physical grid, so that
+// dJ/dkappa = -dt acc / kappa; then
+//   dJ/dVp|rho = 2 rho Vp dJ/dkappa,  dJ/drho|Vp = Vp^2 dJ/dkappa + buoyancy part,
+// family 1 (Vp, rho): those two; family 2 (Vp, Ip = rho Vp):
+//   dJ/dVp|Ip = dJ/dVp|rho - dJ/drho|Vp rho / Vp,  dJ/dIp|Vp = dJ/drho|Vp / Vp;
+// logp: with respect to the logarithms (each times its parameter).
+// g1 may alias acc.
+__global__ void k_finalize_family(Grid g, const float *vp, const float *rho, const float *acc, RhoAcc r,
+                                  int family, int logp, float *g1, float *g2)
+{
+    const int n0 = g.H[0] - g.L[0] + 1, n1 = g.H[1] - g.L[1] + 1;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < g.nphys;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i0 = (int)(t % n0);
+        const int i1 = (int)((t / n0) % n1);
+        const int i2 = (int)(t / ((long long)n0 * n1));
+        const long long k = gidx(g, i0 + g.L[0], i1 + g.L[1], i2 + g.L[2]);
+        const float v = vp[t], d = rho[t], A0 = acc[t];
+        float gb = 0.0f;
+        for (int a = 0; a < g.ndim; a++) gb += r.G[a][k] + r.G[a][k - gstride(g, a)];
+        float gv = -2.0f * g.dt * A0 / v;
+        float gr = -g.dt * A0 / d + 0.5f * gb;
+        if (family == 2) {
+            gv -= gr * d / v;
+            gr /= v;
+        }
+        if (logp) {
+            gv *= v;
+            gr *= family == 2 ? d * v : d;
+        }
+        g1[t] = gv;
+        g2[t] = gr;
+    }
+}
+
 __global__ void k_nonfinite(const float *x, long long n, unsigned *flag)
 {
     bool bad = false;
@@ -1376,6 +1442,22 @@ void launch_reduce_norm(const LaunchCtx &lc, const Grid &g, const float *acc, in
 void launch_finalize_grad(const LaunchCtx &lc, long long n, const float *vp, float dt, float *gr)
 {
     k_finalize_grad<<<blocks_for(n), kThreads, 0, S(lc)>>>(n, vp, dt, gr);
+    ++*lc.launches;
+}
+
+void launch_rho_acc(const LaunchCtx &lc, const Grid &g, int nshot, Fields F, Fields A, RhoAcc r, IBox box)
+{
+    long long vol = 1;
+    for (int a = 0; a < 3; a++) vol *= std::max(0, box.hi[a] - box.lo[a] + 1);
+    if (vol == 0) return;
+    k_rho_acc<<<blocks_for(vol), kThreads, 0, S(lc)>>>(g, nshot, F, A, r, box);
+    ++*lc.launches;
+}
+
+void launch_finalize_family(const LaunchCtx &lc, const Grid &g, const float *vp, const float *rho, const float *acc,
+                            RhoAcc r, int family, int logp, float *g1, float *g2)
+{
+    k_finalize_family<<<blocks_for(g.nphys), kThreads, 0, S(lc)>>>(g, vp, rho, acc, r, family, logp, g1, g2);
     ++*lc.launches;
 }
 

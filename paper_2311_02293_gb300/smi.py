@@ -81,7 +81,7 @@ class smi_stats(ctypes.Structure):
 EXPORTS = ["smi_opts_default", "smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query",
            "smi_box_table", "smi_last_stats", "smi_last_error", "smi_version", "smi_forward_noalloc",
            "smi_forward_vjp", "smi_server_create", "smi_submit", "smi_wait", "smi_poll", "smi_cancel",
-           "smi_server_info", "smi_server_destroy"]
+           "smi_server_info", "smi_server_destroy", "smi_fwi_gradient_family"]
 
 
 def _load():
@@ -97,6 +97,7 @@ def _load():
     L.smi_forward_noalloc.argtypes = common + [vp]
     L.smi_rtm.argtypes = common + [vp, vp]
     L.smi_fwi_gradient.argtypes = common + [vp, vp, vp]
+    L.smi_fwi_gradient_family.argtypes = common + [vp, c_int, c_int, vp, vp, vp]
     L.smi_forward_vjp.argtypes = common + [vp, vp]
     L.smi_query.argtypes = common + [c_int, P(ctypes.c_size_t), P(ctypes.c_size_t), P(ctypes.c_size_t)]
     L.smi_box_table.argtypes = common + [c_int, c_int, c_int, c_int, vp, vp]
@@ -104,7 +105,7 @@ def _load():
     L.smi_last_error.restype = ctypes.c_char_p
     L.smi_version.restype = ctypes.c_char_p
     for name in ("smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query", "smi_box_table",
-                 "smi_last_stats", "smi_forward_noalloc", "smi_forward_vjp"):
+                 "smi_last_stats", "smi_forward_noalloc", "smi_forward_vjp", "smi_fwi_gradient_family"):
         getattr(L, name).restype = c_int
     return L
 
@@ -305,6 +306,25 @@ def smi_fwi_gradient(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None,
     return J, g.reshape(shape)
 
 
+def smi_fwi_gradient_family(vp, rho, prob: Problem, srcs, recs, stf, dobs, family: int = 1, log: bool = False,
+                            stream=None):
+    """(misfit, dJ/dVp, dJ/drho) for family 1, (misfit, dJ/dVp, dJ/dIp) for
+    family 2 (Ip = rho Vp); log: gradients with respect to the logarithms."""
+    m, keep_m, cuda, shape = _model(vp, rho, prob.d)
+    geo, keep_g, off = _geometry(srcs, recs)
+    ks, ps, _ = _as_f32(stf)
+    kd, pd, _ = _dobs_flat(dobs, cuda, None)
+    w = smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
+    o = _opts(prob, stream)
+    dev = vp.device if cuda else None
+    g1, p1 = _out(None, int(np.prod(shape)), cuda, dev)
+    g2, p2 = _out(None, int(np.prod(shape)), cuda, dev)
+    J, pJ = _empty(1, cuda, dtype=np.float64, device=dev)
+    _check(_lib.smi_fwi_gradient_family(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w), ctypes.byref(o),
+                                        pd, int(family), int(bool(log)), pJ, p1, p2))
+    return J, g1.reshape(shape), g2.reshape(shape)
+
+
 def smi_forward_vjp(vp, rho, prob: Problem, srcs, recs, stf, adj_src, stream=None, out=None):
     """dL/dVp for an upstream gradient adj_src = dL/dseis (seismogram layout)."""
     m, keep_m, cuda, shape = _model(vp, rho, prob.d)
@@ -326,7 +346,7 @@ def smi_query(vp, rho, prob: Problem, srcs, recs, stf, kind: str = "forward", st
     w = smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
     o = _opts(prob, stream)
     a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
-    k = {"forward": 0, "rtm": 1, "gradient": 2, "vjp": 3}[kind]
+    k = {"forward": 0, "rtm": 1, "gradient": 2, "vjp": 3, "gradient_family": 4}[kind]
     _check(_lib.smi_query(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w), ctypes.byref(o), k,
                           ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value

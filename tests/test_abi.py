@@ -95,3 +95,22 @@ def test_null_arguments_rejected(smi):
     w = smi.smi_wavelet(10, 1e-3, 10.0, None)
     assert smi.lib().smi_forward(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w),
                                  ctypes.byref(o), None) == -1
+
+
+def test_family_gradient_arguments_checked_on_host(smi):
+    """Family outside {1, 2}, log_param outside {0, 1} and null outputs are
+    argument errors, raised before any device work."""
+    o = smi.smi_opts()
+    smi.lib().smi_opts_default(ctypes.byref(o))
+    m = smi.smi_model(2, 30, 30, 1, 10.0, 10.0, 1.0, None, None)
+    geo = smi.smi_geometry(0, None, None, None)
+    w = smi.smi_wavelet(10, 1e-3, 10.0, None)
+    buf = (ctypes.c_float * 900)()
+    f = smi.lib().smi_fwi_gradient_family
+    args = (ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w), ctypes.byref(o), None)
+    assert f(*args, 0, 0, None, buf, buf) == -1
+    assert f(*args, 3, 0, None, buf, buf) == -1
+    assert f(*args, 1, 2, None, buf, buf) == -1
+    assert f(*args, 2, 0, None, buf, None) == -1
+    assert smi.lib().smi_last_error().decode()
+
