@@ -64,6 +64,7 @@ class _Par(ctypes.Structure):
         ("periodic", ctypes.c_int),
         ("nthreads", ctypes.c_int),
         ("dr", ctypes.c_int),
+        ("freesurf", ctypes.c_int),
     ]
 
 
@@ -83,6 +84,7 @@ class Problem:
     periodic: bool = False
     nthreads: int = 0
     dr: int = 1         # boundary decimation ratio (Sec. 4.2)
+    freesurf: bool = False   # free surface on the top face (image method, Sec. 2.1)
 
     @property
     def ndim(self) -> int:
@@ -102,7 +104,7 @@ class Problem:
         d = list(self.d) + [1.0] * (3 - len(self.d))
         return _Par(self.ndim, n[0], n[1], n[2], d[0], d[1], d[2], self.order, self.nb,
                     self.nt, self.dt, self.fm, self.kaiser_b, self.cpml_R, int(self.use_box),
-                    int(self.periodic), self.nthreads, self.dr)
+                    int(self.periodic), self.nthreads, self.dr, int(self.freesurf))
 
 
 _lib = None

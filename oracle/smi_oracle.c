@@ -59,6 +59,7 @@ typedef struct {
     int periodic;         /* tests only: periodic wrap instead of zero reads */
     int nthreads;         /* OpenMP threads, 0 = library default */
     int dr;               /* boundary decimation ratio (Sec. 4.2); 1 = every step */
+    int freesurf;         /* 1: free surface on the top face (image method, Sec. 2.1) */
 } orc_par;
 
 #define MAXN 8
@@ -71,7 +72,7 @@ typedef struct {
     long ntot;
     double d[3], dt, dV;
     double a[MAXN];       /* FD coefficients a_1..a_N stored at a[0..N-1] */
-    int periodic, use_box, nt, dr;
+    int periodic, use_box, nt, dr, freesurf;
     double vmax, vmin;
     double *K;            /* bulk modulus at p nodes */
     double *bu[3];        /* buoyancy at v_a nodes */
@@ -216,6 +217,7 @@ static int grid_init(grid_t *g, const orc_par *par, const double *vp, const doub
     if (par->order != 2 && par->order != 4 && par->order != 8) return ORC_ERR_ARG;
     if (par->nt < 1 || !(par->dt > 0.0) || par->nb < 0) return ORC_ERR_ARG;
     if (par->periodic && par->nb != 0) return ORC_ERR_ARG;
+    if (par->freesurf && (par->periodic || par->nb < par->order / 2)) return ORC_ERR_ARG;
 #ifdef _OPENMP
     if (par->nthreads > 0) omp_set_num_threads(par->nthreads);
 #endif
@@ -223,6 +225,7 @@ static int grid_init(grid_t *g, const orc_par *par, const double *vp, const doub
     g->N = par->order / 2;
     g->ri = g->N;
     g->periodic = par->periodic;
+    g->freesurf = par->freesurf != 0;
     g->use_box = par->use_box;
     g->nt = par->nt;
     g->dt = par->dt;
@@ -318,6 +321,10 @@ static int grid_init(grid_t *g, const orc_par *par, const double *vp, const doub
         cpml_axis(g->ne[a], g->L[a], g->H[a], par->nb, d[a], g->vmax, par->fm,
                   par->cpml_R, g->dt, 1, g->cva[a], g->cvb[a]);
     }
+    /* Free surface: the top layer holds the image of the field, not an
+     * absorbing layer (its memory variables stay zero). */
+    for (int i = 0; g->freesurf && i < g->L[0]; i++)
+        g->cpa[0][i] = g->cpb[0][i] = g->cva[0][i] = g->cvb[0][i] = 0.0;
     return ORC_OK;
 }
 
@@ -489,6 +496,87 @@ static void adjoint_update_v(const grid_t *g, state_t *ad, const int lo[3], cons
 }
 
 /* ---------------------------------------------------------------------- */
+/* Free surface on the top face by the image method (Sec. 2.1, after
+ * Levander 1988).  The surface is the first physical node row L = L[0].
+ * After the velocity update, v_z on the N half nodes above it mirrors v_z
+ * below it (symmetric: half node L-1-j takes L+j); after the pressure
+ * update and the source, p = 0 at L and p on the N nodes above it is minus
+ * its mirror (antisymmetric: node L-j takes -p at L+j).  Every x and y. */
+static void fs_mirror_v(const grid_t *g, double *vz)
+{
+    if (!g->freesurf) return;
+    for (int i3 = 0; i3 < g->ne[2]; i3++)
+    for (int i2 = 0; i2 < g->ne[1]; i2++)
+    for (int j = 0; j < g->N; j++)
+        vz[IDX(g, g->L[0] - 1 - j, i2, i3)] = vz[IDX(g, g->L[0] + j, i2, i3)];
+}
+
+static void fs_mirror_p(const grid_t *g, double *p)
+{
+    if (!g->freesurf) return;
+    for (int i3 = 0; i3 < g->ne[2]; i3++)
+    for (int i2 = 0; i2 < g->ne[1]; i2++) {
+        p[IDX(g, g->L[0], i2, i3)] = 0.0;
+        for (int j = 1; j <= g->N; j++)
+            p[IDX(g, g->L[0] - j, i2, i3)] = -p[IDX(g, g->L[0] + j, i2, i3)];
+    }
+}
+
+/* Transposes of the two mirrors, applied to the adjoint fields: an image
+ * node's adjoint goes (negated for p) to its mirror node and is cleared; the
+ * adjoint of p at the surface node is cleared. */
+static void fs_fold_v(const grid_t *g, double *vzb)
+{
+    if (!g->freesurf) return;
+    for (int i3 = 0; i3 < g->ne[2]; i3++)
+    for (int i2 = 0; i2 < g->ne[1]; i2++)
+    for (int j = 0; j < g->N; j++) {
+        long ki = IDX(g, g->L[0] - 1 - j, i2, i3);
+        vzb[IDX(g, g->L[0] + j, i2, i3)] += vzb[ki];
+        vzb[ki] = 0.0;
+    }
+}
+
+static void fs_fold_p(const grid_t *g, double *pb)
+{
+    if (!g->freesurf) return;
+    for (int i3 = 0; i3 < g->ne[2]; i3++)
+    for (int i2 = 0; i2 < g->ne[1]; i2++) {
+        for (int j = 1; j <= g->N; j++) {
+            long ki = IDX(g, g->L[0] - j, i2, i3);
+            pb[IDX(g, g->L[0] + j, i2, i3)] -= pb[ki];
+            pb[ki] = 0.0;
+        }
+        pb[IDX(g, g->L[0], i2, i3)] = 0.0;
+    }
+}
+
+static void stencil_add(const grid_t *g, double *f, const stencil_t *st, double scale);
+
+/* One forward step (Algorithm 2, Sec. 2.1) on the box [lo, hi]: velocity
+ * update, velocity mirror, pressure update, the source (src may be NULL:
+ * none), pressure mirror. */
+static void forward_step(const grid_t *g, state_t *s, const int lo[3], const int hi[3], const stencil_t *src,
+                         double scale)
+{
+    update_v(g, s, lo, hi);
+    fs_mirror_v(g, s->v[0]);
+    update_p(g, s, lo, hi);
+    if (src) stencil_add(g, s->p, src, scale);
+    fs_mirror_p(g, s->p);
+}
+
+/* Transpose of forward_step's propagation, after the step's adjoint sources
+ * are in ad->p and whatever reads the adjoint of the updated pressure has run
+ * (fs_fold_p goes before that). */
+static void adjoint_step(const grid_t *g, state_t *ad, const int lo[3], const int hi[3])
+{
+    adjoint_update_p(g, ad, lo, hi);
+    fs_fold_v(g, ad->v[0]);
+    adjoint_update_v(g, ad, lo, hi);
+}
+
+/* ---------------------------------------------------------------------- */
 /* Stencil of a point given in metres (z, x, y) from the first physical node.
  * The point must lie inside the physical domain and its 2ri-node stencil
  * inside the extended grid. */
@@ -507,6 +595,21 @@ static int point_stencil(const grid_t *g, const double pos[3], double kb, stenci
         orc_kaiser_1d(x0 + g->L[a], g->ri, kb, &st->first[a], st->w[a]);
         st->cnt[a] = 2 * g->ri;
         if (st->first[a] < 0 || st->first[a] + st->cnt[a] - 1 > g->ne[a] - 1) return ORC_ERR_ARG;
+        if (a == 0 && g->freesurf) {
+            /* Free surface (reading, the image-source form of Hicks 2002): a
+             * weight above the surface node L goes, negated, to its mirror
+             * node 2L - i; the weight at L is dropped (p = 0 there). */
+            for (int q = 0; q < st->cnt[0]; q++) {
+                int node = st->first[0] + q;
+                if (node >= g->L[0]) continue;
+                int qm = 2 * g->L[0] - node - st->first[0];
+                if (qm >= st->cnt[0]) return ORC_ERR_ARG;
+                st->w[0][qm] -= st->w[0][q];
+                st->w[0][q] = 0.0;
+            }
+            int q0 = g->L[0] - st->first[0];
+            if (q0 >= 0 && q0 < st->cnt[0]) st->w[0][q0] = 0.0;
+        }
     }
     return ORC_OK;
 }
@@ -575,11 +678,15 @@ static void box_at(const grid_t *g, const int slo[3], const int shi[3], int n,
         if (lo[a] < 0) lo[a] = 0;
         if (hi[a] > g->ne[a] - 1) hi[a] = g->ne[a] - 1;
     }
+    if (n >= 0 && g->freesurf && lo[0] < g->L[0] - g->N) lo[0] = g->L[0] - g->N;
 }
 
+/* With the free surface, the nodes above the image zone (more than N above
+ * the surface) are never updated and stay zero. */
 static void full_box(const grid_t *g, int lo[3], int hi[3])
 {
     for (int a = 0; a < 3; a++) { lo[a] = 0; hi[a] = g->ne[a] - 1; }
+    if (g->freesurf) lo[0] = g->L[0] - g->N;
 }
 
 static int in_box(const int i[3], const int lo[3], const int hi[3])
@@ -691,8 +798,7 @@ static int forward_continue(const grid_t *g, state_t *s, const int slo[3], const
         if (it % g->dr == 0) band_copy(g, s->v, bands + nband * (long)(it / g->dr), 0);
         int lo[3], hi[3];
         box_at(g, slo, shi, it, lo, hi);
-        update_v(g, s, lo, hi);
-        update_p(g, s, lo, hi);
+        forward_step(g, s, lo, hi, NULL, 0.0);
     }
     memcpy(s->p, keep, sizeof(double) * g->ntot);
     for (int a = 0; a < g->ndim; a++) memcpy(s->v[a], keep + g->ntot * (1 + a), sizeof(double) * g->ntot);
@@ -723,7 +829,7 @@ static void reconstruct_step(const grid_t *g, state_t *s, const stencil_t *src,
         double div = 0.0;
         for (int a = 0; a < g->ndim; a++) div += deriv_v(g, s->v[a], a, i);
         s->p[k] += g->dt * g->K[k] * div;
-        if (!in_box(i, prev[0], prev[1])) s->p[k] = 0.0;
+        if (!in_box(i, prev[0], prev[1]) || (g->freesurf && i1 == g->L[0])) s->p[k] = 0.0;
     }
     for (int a = 0; a < g->ndim; a++) {
         int vlo[3], vhi[3];
@@ -766,9 +872,7 @@ int orc_forward(const orc_par *par, const double *vp, const double *rho, const d
     for (int it = 0; it < g.nt; it++) {
         int lo[3], hi[3];
         box_at(&g, slo, shi, it, lo, hi);
-        update_v(&g, &s, lo, hi);
-        update_p(&g, &s, lo, hi);
-        stencil_add(&g, s.p, &sst, g.dt * stf[it] / g.dV);
+        forward_step(&g, &s, lo, hi, &sst, g.dt * stf[it] / g.dV);
         for (int r = 0; r < nrec; r++) seis[(long)it * nrec + r] = stencil_get(&g, s.p, &rst[r]);
         if (psnap) {
             long c = 0, nphys = (long)(g.H[0] - g.L[0] + 1) * (g.H[1] - g.L[1] + 1) * (g.H[2] - g.L[2] + 1);
@@ -814,8 +918,7 @@ int orc_propagate(const orc_par *par, const double *vp, const double *rho,
     int lo[3], hi[3];
     full_box(&g, lo, hi);
     for (int it = 0; it < nsteps; it++) {
-        update_v(&g, &s, lo, hi);
-        update_p(&g, &s, lo, hi);
+        forward_step(&g, &s, lo, hi, NULL, 0.0);
         for (int r = 0; r < nrec; r++) seis[(long)it * nrec + r] = stencil_get(&g, s.p, &rst[r]);
     }
     for (int k = 0; k < 6; k++) free(tmp[k]);
@@ -847,13 +950,13 @@ int orc_adjoint(const orc_par *par, const double *vp, const double *rho, const d
     stencil_extent(rst, nrec, rlo, rhi);
     for (int it = g.nt - 1; it >= 0; it--) {
         for (int r = 0; r < nrec; r++) stencil_add(&g, ad.p, &rst[r], res[(long)it * nrec + r]);
+        fs_fold_p(&g, ad.p);
         sbar[it] = g.dt / g.dV * stencil_get(&g, ad.p, &sst);
         int lo[3], hi[3];
         if (box_mode == 1) box_at(&g, slo, shi, it, lo, hi);
         else if (box_mode == 2) box_at(&g, rlo, rhi, g.nt - 1 - it, lo, hi);
         else full_box(&g, lo, hi);
-        adjoint_update_p(&g, &ad, lo, hi);
-        adjoint_update_v(&g, &ad, lo, hi);
+        adjoint_step(&g, &ad, lo, hi);
     }
     state_free(&ad);
     free(rst);
@@ -1010,9 +1113,7 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
         if (recon && it % g.dr == 0) band_copy(&g, s.v, bands + nband * (long)(it / g.dr), 0);
         int lo[3], hi[3];
         box_at(&g, slo, shi, it, lo, hi);
-        update_v(&g, &s, lo, hi);
-        update_p(&g, &s, lo, hi);
-        stencil_add(&g, s.p, &sst, g.dt * stf[it] / g.dV);
+        forward_step(&g, &s, lo, hi, &sst, g.dt * stf[it] / g.dV);
         for (int r = 0; r < nrec; r++) seis[(long)it * nrec + r] = stencil_get(&g, s.p, &rst[r]);
         if (!recon) {
             memcpy(store_p + g.ntot * (long)it, s.p, sizeof(double) * g.ntot);
@@ -1042,6 +1143,7 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
             double src_r = (mode == 0) ? seis[k] - dobs[k] : dobs[k];
             stencil_add(&g, ad.p, &rst[r], src_r);
         }
+        fs_fold_p(&g, ad.p);
         int box[2][3], prev[2][3];
         box_at(&g, slo, shi, it, box[0], box[1]);
         box_at(&g, slo, shi, it - 1, prev[0], prev[1]);
@@ -1064,8 +1166,7 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
         int lo[3], hi[3];
         if (g.use_box) box_at(&g, rlo, rhi, g.nt - 1 - it, lo, hi);
         else full_box(&g, lo, hi);
-        adjoint_update_p(&g, &ad, lo, hi);
-        adjoint_update_v(&g, &ad, lo, hi);
+        adjoint_step(&g, &ad, lo, hi);
         if (want_rho)
             for (int a = 0; a < g.ndim; a++) memcpy(vsave[a], s.v[a], sizeof(double) * g.ntot);
         if (recon) {
@@ -1141,9 +1242,7 @@ int orc_reconstruct(const orc_par *par, const double *vp, const double *rho, con
         if (it % g.dr == 0) band_copy(&g, s.v, bands + nband * (long)(it / g.dr), 0);
         int lo[3], hi[3];
         box_at(&g, slo, shi, it, lo, hi);
-        update_v(&g, &s, lo, hi);
-        update_p(&g, &s, lo, hi);
-        stencil_add(&g, s.p, &sst, g.dt * stf[it] / g.dV);
+        forward_step(&g, &s, lo, hi, &sst, g.dt * stf[it] / g.dV);
     }
     if (!rc) rc = forward_continue(&g, &s, slo, shi, bands, nband, nsamp);
     if (rc) { free(bands); free(bandt); state_free(&s); grid_free(&g); return rc; }
