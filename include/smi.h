@@ -63,7 +63,7 @@ extern "C" {
 #define SMI_ERR_UNSTABLE (-5)     /* a non-finite value appeared */
 #define SMI_ERR_TIMEOUT (-6)      /* a bounded device wait gave up */
 #define SMI_ERR_CUDA (-7)         /* a CUDA runtime call failed */
-#define SMI_ERR_UNSUPPORTED (-8)  /* option outside this build (freesurf) */
+#define SMI_ERR_UNSUPPORTED (-8)  /* a size outside this build (boundary bands of a step >= 2^31 values) */
 
 /* Storage precision of the saved boundaries (Sec. 4.2). */
 #define SMI_PREC_F32 0
@@ -103,7 +103,11 @@ typedef struct {
 typedef struct {
     int order;                /* 4 or 8 (FD order in space, Sec. 3.8) */
     int nb;                   /* CPML layers per face, >= order/2 (paper: 20) */
-    int freesurf;             /* 0 only (free surface is not built: SMI_ERR_UNSUPPORTED) */
+    int freesurf;             /* 1: free surface on the top face by the image method (Sec. 2.1): p = 0
+                                 at the first physical node row, p mirrored antisymmetrically and v_z
+                                 symmetrically into the top layer (which then absorbs nothing);
+                                 source / receiver weights above the surface fold, negated, onto
+                                 their mirror nodes.  0: absorbing top face.  Else SMI_ERR_ARG */
     int dr;                   /* boundary decimation ratio (Sec. 4.2): the boundary of every dr-th
                                  step is stored and interpolated in time during reconstruction;
                                  1 <= dr <= 5 vmax / vmin (SMI_ERR_ARG otherwise) */

@@ -128,7 +128,7 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     if (!m || !geo || !w || !o) return fail(SMI_ERR_ARG, "null argument");
     if (m->ndim != 2 && m->ndim != 3) return fail(SMI_ERR_ARG, "ndim must be 2 or 3");
     if (o->order != 4 && o->order != 8) return fail(SMI_ERR_ARG, "order must be 4 or 8");
-    if (o->freesurf != 0) return fail(SMI_ERR_UNSUPPORTED, "free surface is not built (freesurf must be 0)");
+    if (o->freesurf != 0 && o->freesurf != 1) return fail(SMI_ERR_ARG, "freesurf must be 0 or 1");
     if (o->dr < 1) return fail(SMI_ERR_ARG, "dr must be >= 1");
     if (o->shell_prec < SMI_PREC_F32 || o->shell_prec > SMI_PREC_BF16)
         return fail(SMI_ERR_ARG, "shell_prec must be SMI_PREC_F32, F16 or BF16");
@@ -180,6 +180,7 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     set_layout(g, S.n);
     g.dt = (float)w->dt;
     g.use_box = o->use_box ? 1 : 0;
+    g.freesurf = o->freesurf;
     double coef[kMaxHalf] = {0};
     fd_coefficients(N, coef);
     for (int a = 0; a < 3; a++)
@@ -231,6 +232,9 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
         cpml_tables(g.ne[a], o->nb, hh[a], S.vmax, w->fm, R, w->dt, false, tab.data(), tab.data() + g.ne[a]);
         cpml_tables(g.ne[a], o->nb, hh[a], S.vmax, w->fm, R, w->dt, true, tab.data() + 2 * g.ne[a],
                     tab.data() + 3 * g.ne[a]);
+        if (a == 0 && g.freesurf)              // the top layer is the image zone: no absorption
+            for (int q = 0; q < 4; q++)
+                for (int i = 0; i < g.L[0]; i++) tab[(size_t)q * g.ne[0] + i] = 0.0f;
         float *d = ar.get<float>(tab.size());
         if (!d) return fail(SMI_ERR_NOMEM, "device allocation failed");
         cudaMemcpyAsync(d, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, st);
@@ -599,25 +603,29 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 tm.begin(0);
                 int blo[3], bhi[3];
                 batch_box(S.box_src, it, blo, bhi);
+                // free surface (no-ops without): the v_z mirror after the velocity
+                // update, the p mirror after the pressure update and the source
                 if (fast3) {
                     launch3_v(lc, mF, g, b, F, it, 0, d_wait);
                     launch_fwd_corrections(lc, g, b, F, it, true, blo, bhi);
+                    launch_free_surface(lc, g, F.v[0], nb_shot, kFsMirrorV);
                     launch3_p(lc, mF, nullptr, g, b, F, it, 0, d_wait, nullptr, 0, nullptr, 0.0f);
                     launch_fwd_corrections(lc, g, b, F, it, false, blo, bhi);
                 } else if (fast2) {                    // CPML and (it < nt) the source inline
                     launch2_v(lc, g, b, F, it, 0, blo, bhi);
+                    launch_free_surface(lc, g, F.v[0], nb_shot, kFsMirrorV);
                     launch2_p(lc, g, b, F, it, 0, blo, bhi, nullptr, nullptr, 0, it < S.nt ? S.stf : nullptr,
                               (float)S.src_scale);
                 } else {
                     const long long work = box_points(blo, bhi);
                     launch_fwd_v(lc, g, b, F, it, work);
+                    launch_free_surface(lc, g, F.v[0], nb_shot, kFsMirrorV);
                     launch_fwd_p(lc, g, b, F, it, work);
                 }
                 tm.end();
-                if (it < S.nt) {
-                    if (!fast2) launch_inject_source(lc, g, b, F.p, S.stf, it, (float)S.src_scale);
-                    if (max_rec > 0) launch_gather(lc, g, b, F.p, seis, d_soff, S.nt, it);
-                }
+                if (it < S.nt && !fast2) launch_inject_source(lc, g, b, F.p, S.stf, it, (float)S.src_scale);
+                launch_free_surface(lc, g, F.p, nb_shot, kFsMirrorP);
+                if (it < S.nt && max_rec > 0) launch_gather(lc, g, b, F.p, seis, d_soff, S.nt, it);
                 for (int s = 0; s < nb_shot; s++) {
                     int lo[3], hi[3];
                     box_bounds(g, S.box_src.data() + 6 * (s0 + s), it, lo, hi);
@@ -662,9 +670,15 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             for (int it = S.nt - 1; it >= 0; it--) {
                 const int mrev = S.nt - 1 - it;
                 if (max_rec > 0) launch_adj_inject(lc, g, b, A.p, res, d_soff, S.nt, it);
+                // free surface (no-ops without): the transposed p mirror on the
+                // adjoint before anything reads it; p = 0 again at the surface node
+                // of the reversed source field; the transposed v_z mirror between
+                // the two adjoint stages
+                launch_free_surface(lc, g, A.p, nb_shot, kFsFoldP);
                 tm.begin(2);
                 if (fast3) {
                     launch3_p(lc, mF, &mA, g, b, F, it, 2, d_wait, acc, mode, S.stf, (float)S.src_scale);
+                    launch_free_surface(lc, g, F.p, nb_shot, kFsMirrorP);
                     launch3_v(lc, mF, g, b, F, it, 2, d_wait);
                 } else {
                     int blo[3], bhi[3];
@@ -675,10 +689,12 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     }
                     if (fast2) {
                         launch2_p(lc, g, b, F, it, 2, blo, bhi, A.p, acc, mode, S.stf, (float)S.src_scale);
+                        launch_free_surface(lc, g, F.p, nb_shot, kFsMirrorP);
                         launch2_v(lc, g, b, F, it, 2, blo, bhi);
                     } else {
                         const long long work = box_points(blo, bhi);
                         launch_recon_p(lc, g, b, F, A.p, acc, mode, S.stf, it, (float)S.src_scale, work);
+                        launch_free_surface(lc, g, F.p, nb_shot, kFsMirrorP);
                         launch_recon_v(lc, g, b, F, it, work);
                     }
                 }
@@ -691,14 +707,17 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 if (fast3) {
                     launch_adj_corrections(lc, g, b, A, mrev, true, blo, bhi);
                     launch3_v(lc, mA, g, b, A, mrev, 1, d_wait);
+                    launch_free_surface(lc, g, A.v[0], nb_shot, kFsFoldV);
                     launch_adj_corrections(lc, g, b, A, mrev, false, blo, bhi);
                     launch3_p(lc, mA, nullptr, g, b, A, mrev, 1, d_wait, nullptr, 0, nullptr, 0.0f);
                 } else if (fast2) {                    // transposed CPML inline in the 2D kernels
                     launch2_v(lc, g, b, A, mrev, 1, blo, bhi);
+                    launch_free_surface(lc, g, A.v[0], nb_shot, kFsFoldV);
                     launch2_p(lc, g, b, A, mrev, 1, blo, bhi, nullptr, nullptr, 0, nullptr, 0.0f);
                 } else {
                     const long long work = box_points(blo, bhi);
                     launch_adj_v(lc, g, b, A, mrev, work);
+                    launch_free_surface(lc, g, A.v[0], nb_shot, kFsFoldV);
                     launch_adj_p(lc, g, b, A, mrev, work);
                 }
                 tm.end();

@@ -59,6 +59,8 @@ SMI_HD void box_bounds(const Grid &g, const int *ext, int n, int lo[3], int hi[3
             hi[a] = h > g.ne[a] - 1 ? g.ne[a] - 1 : h;
         }
     }
+    // free surface: the nodes more than N above the surface are never updated
+    if (n >= 0 && g.freesurf && lo[0] < g.L[0] - g.N) lo[0] = g.L[0] - g.N;
 }
 
 // Points of the box [lo, hi] (0 if empty).

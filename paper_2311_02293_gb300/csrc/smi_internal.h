@@ -30,6 +30,7 @@ struct Grid {
     double vdt;            // vmax * dt (FP64, for the computing box)
     double h[3];           // spacings (FP64, for the computing box)
     int use_box;
+    int freesurf;          // free surface on the top face (image method): the top layer is the image zone
     const float *K;        // bulk modulus rho*vp^2 on the extended grid
     const float *rho;      // density on the extended grid
     const float *cpa[3], *cpb[3];   // CPML a, b on the p grid of axis a (length ne[a])
@@ -227,6 +228,16 @@ void launch_rho_acc(const LaunchCtx &lc, const Grid &g, int nshot, Fields F, Fie
 // rho physical; g1 may alias acc.
 void launch_finalize_family(const LaunchCtx &lc, const Grid &g, const float *vp, const float *rho, const float *acc,
                             RhoAcc r, int family, int logp, float *g1, float *g2);
+// Free surface on the top face (image method, Sec. 2.1), on every x, y of
+// nshot fields f (z component for the velocity ops):
+//   kFsMirrorV: v_z on the N half nodes above the surface node L = g.L[0]
+//               mirrors v_z below it (half node L-1-j takes L+j);
+//   kFsMirrorP: p = 0 at L, p at L-j takes -p at L+j (j = 1..N);
+//   kFsFoldV, kFsFoldP: the transposes (adjoint fields): the image node's
+//               value goes to its mirror node (negated for p) and is cleared,
+//               and for p the surface node is cleared.
+enum { kFsMirrorV = 0, kFsMirrorP = 1, kFsFoldV = 2, kFsFoldP = 3 };
+void launch_free_surface(const LaunchCtx &lc, const Grid &g, float *f, int nshot, int op);
 void launch_nonfinite(const LaunchCtx &lc, const float *x, long long n, unsigned *flag);
 // Sets the padded layout: px, ntot, nphys and the slab sizes (ne, nb, ndim set).
 void set_layout(Grid &g, const int n[3]);

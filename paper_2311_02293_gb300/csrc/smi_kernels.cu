@@ -1041,24 +1041,61 @@ __global__ void k_finalize_grad(long long n, const float *vp, float dt, float *g
 // vbar dv/db).  k_rho_acc runs at the end of reverse step it, when vprev
 // holds v^{it+1/2}, the source field v^{it-1/2} and the adjoint lambda_v of
 // v^{it+1/2}: G_a += sum_s lambda_v (vprev - v), then vprev <- v.
+// Four z-consecutive nodes per thread (float4): box.lo[0] is a multiple of
+// 4 and the box's z width a multiple of 4 (the host widens the box; G is
+// read only on the half nodes next to the physical domain, which the
+// widened box always covers).
+template <int NDIM>
 __global__ void __launch_bounds__(kThreads) k_rho_acc(Grid g, int nshot, Fields F, Fields A, RhoAcc r, IBox box)
 {
-    BoxIter bi;
-    bi.set(box.lo, box.hi);
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < bi.vol;
+    const int wq = (box.hi[0] - box.lo[0] + 1) >> 2;
+    const int w1 = box.hi[1] - box.lo[1] + 1;
+    const long long vol = (long long)wq * w1 * (box.hi[2] - box.lo[2] + 1);
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < vol;
          q += (long long)gridDim.x * blockDim.x) {
-        int i[3];
-        bi.at(q, i);
-        const long long k = gidx(g, i[0], i[1], i[2]);
-        for (int a = 0; a < g.ndim; a++) {
-            float c = 0.0f;
-            for (int s = 0; s < nshot; s++) {
-                const long long kk = s * g.ntot + k;
-                const float v = F.v[a][kk];
-                c += A.v[a][kk] * (r.vprev[a][kk] - v);
-                r.vprev[a][kk] = v;
+        int iq, i1, i2;
+        if (vol < (1LL << 31)) {          // 32-bit division (uniform branch)
+            const int qq = (int)q, rr = qq / wq;
+            iq = qq - rr * wq;
+            i1 = rr % w1;
+            i2 = rr / w1;
+        } else {
+            const long long rr = q / wq;
+            iq = (int)(q - rr * wq);
+            i1 = (int)(rr % w1);
+            i2 = (int)(rr / w1);
+        }
+        const long long k = gidx(g, box.lo[0] + 4 * iq, box.lo[1] + i1, box.lo[2] + i2);
+        float4 c[NDIM];
+#pragma unroll
+        for (int a = 0; a < NDIM; a++) c[a] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int s = 0; s < nshot; s++) {
+            const long long kk = s * g.ntot + k;
+            float4 v[NDIM], l[NDIM], pv[NDIM];
+#pragma unroll
+            for (int a = 0; a < NDIM; a++) {
+                v[a] = *reinterpret_cast<const float4 *>(F.v[a] + kk);
+                l[a] = *reinterpret_cast<const float4 *>(A.v[a] + kk);
+                pv[a] = *reinterpret_cast<const float4 *>(r.vprev[a] + kk);
             }
-            r.G[a][k] += c;
+#pragma unroll
+            for (int a = 0; a < NDIM; a++) {
+                c[a].x += l[a].x * (pv[a].x - v[a].x);
+                c[a].y += l[a].y * (pv[a].y - v[a].y);
+                c[a].z += l[a].z * (pv[a].z - v[a].z);
+                c[a].w += l[a].w * (pv[a].w - v[a].w);
+                *reinterpret_cast<float4 *>(r.vprev[a] + kk) = v[a];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NDIM; a++) {
+            float4 *G = reinterpret_cast<float4 *>(r.G[a] + k);
+            float4 t = *G;
+            t.x += c[a].x;
+            t.y += c[a].y;
+            t.z += c[a].z;
+            t.w += c[a].w;
+            *G = t;
         }
     }
 }
@@ -1099,6 +1136,41 @@ __global__ void k_finalize_family(Grid g, const float *vp, const float *rho, con
     }
 }
 
+// Free-surface mirrors and their transposes; thread (j, row, shot), j in
+// 0..N fastest.
+__global__ void k_free_surface(Grid g, float *f, int nshot, int op)
+{
+    const int N = g.N;
+    const long long rows = (long long)g.ne[1] * g.ne[2];
+    const long long n = rows * nshot * (N + 1);
+    const int L = g.L[0];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(t % (N + 1));
+        const long long r = t / (N + 1);                 // shot * rows + row
+        const long long s = r / rows, row = r - s * rows;
+        float *c = f + s * g.ntot + row * g.px;          // the z column of this (x, y)
+        if (op == kFsMirrorV) {
+            if (j < N) c[L - 1 - j] = c[L + j];
+        } else if (op == kFsMirrorP) {
+            if (j == 0) c[L] = 0.0f;
+            else c[L - j] = -c[L + j];
+        } else if (op == kFsFoldV) {
+            if (j < N) {
+                c[L + j] += c[L - 1 - j];
+                c[L - 1 - j] = 0.0f;
+            }
+        } else {
+            if (j == 0) {
+                c[L] = 0.0f;
+            } else {
+                c[L + j] -= c[L - j];
+                c[L - j] = 0.0f;
+            }
+        }
+    }
+}
+
 __global__ void k_nonfinite(const float *x, long long n, unsigned *flag)
 {
     bool bad = false;
@@ -1121,7 +1193,9 @@ __global__ void k_extend_model(Grid g, const float *vp, const float *rho, int n1
             K[t] = 0.0f;
             continue;
         }
-        const int j1 = min(max(i1 - g.L[0], 0), n1 - 1);
+        // free surface: the top layer mirrors the model about the surface node,
+        // so that the transposed mirrors of the adjoint take no model ratio
+        const int j1 = (g.freesurf && i1 < g.L[0]) ? min(g.L[0] - i1, n1 - 1) : min(max(i1 - g.L[0], 0), n1 - 1);
         const int j2 = min(max(i2 - g.L[1], 0), n2 - 1);
         const int j3 = min(max(i3 - g.L[2], 0), n3 - 1);
         const long long kp = (long long)j1 + (long long)n1 * ((long long)j2 + (long long)n2 * j3);
@@ -1450,7 +1524,12 @@ void launch_rho_acc(const LaunchCtx &lc, const Grid &g, int nshot, Fields F, Fie
     long long vol = 1;
     for (int a = 0; a < 3; a++) vol *= std::max(0, box.hi[a] - box.lo[a] + 1);
     if (vol == 0) return;
-    k_rho_acc<<<blocks_for(vol), kThreads, 0, S(lc)>>>(g, nshot, F, A, r, box);
+    box.lo[0] &= ~3;                       // whole float4 quads; px is a multiple of 8
+    box.hi[0] |= 3;
+    const long long quads = (long long)((box.hi[0] - box.lo[0] + 1) >> 2) * (box.hi[1] - box.lo[1] + 1) *
+                            (box.hi[2] - box.lo[2] + 1);
+    if (g.ndim == 3) k_rho_acc<3><<<blocks_for(quads), kThreads, 0, S(lc)>>>(g, nshot, F, A, r, box);
+    else k_rho_acc<2><<<blocks_for(quads), kThreads, 0, S(lc)>>>(g, nshot, F, A, r, box);
     ++*lc.launches;
 }
 
@@ -1458,6 +1537,14 @@ void launch_finalize_family(const LaunchCtx &lc, const Grid &g, const float *vp,
                             RhoAcc r, int family, int logp, float *g1, float *g2)
 {
     k_finalize_family<<<blocks_for(g.nphys), kThreads, 0, S(lc)>>>(g, vp, rho, acc, r, family, logp, g1, g2);
+    ++*lc.launches;
+}
+
+void launch_free_surface(const LaunchCtx &lc, const Grid &g, float *f, int nshot, int op)
+{
+    if (!g.freesurf) return;
+    const long long n = (long long)g.ne[1] * g.ne[2] * nshot * (g.N + 1);
+    k_free_surface<<<blocks_for(n), kThreads, 0, S(lc)>>>(g, f, nshot, op);
     ++*lc.launches;
 }
 

@@ -149,7 +149,7 @@ int forward_noalloc(const smi_model *m, const smi_geometry *geo, const smi_wavel
     if (!m || !geo || !w || !o || !seis) return err(SMI_ERR_ARG, "null argument");
     if (m->ndim != 2 && m->ndim != 3) return err(SMI_ERR_ARG, "ndim must be 2 or 3");
     if (o->order != 4 && o->order != 8) return err(SMI_ERR_ARG, "order must be 4 or 8");
-    if (o->freesurf != 0) return err(SMI_ERR_UNSUPPORTED, "free surface is not built (freesurf must be 0)");
+    if (o->freesurf != 0 && o->freesurf != 1) return err(SMI_ERR_ARG, "freesurf must be 0 or 1");
     if (o->dr < 1) return err(SMI_ERR_ARG, "dr must be >= 1");
     if (o->shell_prec < SMI_PREC_F32 || o->shell_prec > SMI_PREC_BF16)
         return err(SMI_ERR_ARG, "shell_prec must be SMI_PREC_F32, F16 or BF16");
@@ -184,6 +184,7 @@ int forward_noalloc(const smi_model *m, const smi_geometry *geo, const smi_wavel
     set_layout(g, n);
     g.dt = (float)w->dt;
     g.use_box = o->use_box ? 1 : 0;
+    g.freesurf = o->freesurf;
     double coef[kMaxHalf] = {0};
     fd_coefficients(N, coef);
     for (int a = 0; a < 3; a++)
@@ -252,6 +253,9 @@ int forward_noalloc(const smi_model *m, const smi_geometry *geo, const smi_wavel
         const int ne = g.ne[a];
         cpml_tables(ne, o->nb, hh[a], hm[1], w->fm, R, w->dt, false, tab, tab + ne);
         cpml_tables(ne, o->nb, hh[a], hm[1], w->fm, R, w->dt, true, tab + 2 * ne, tab + 3 * ne);
+        if (a == 0 && g.freesurf)              // the top layer is the image zone: no absorption
+            for (int q = 0; q < 4; q++)
+                for (int i = 0; i < g.L[0]; i++) tab[q * ne + i] = 0.0f;
         cudaMemcpyAsync(pl.cpml[a], tab, sizeof(float) * 4 * ne, cudaMemcpyHostToDevice, st);
         if ((rc = sync(st))) return rc;
         g.cpa[a] = pl.cpml[a];
@@ -336,8 +340,10 @@ int forward_noalloc(const smi_model *m, const smi_geometry *geo, const smi_wavel
             int lo[3], hi[3];
             box_bounds(g, box, it, lo, hi);
             launch_fwd_v(lc, g, b, F, it, box_points(lo, hi));
+            launch_free_surface(lc, g, F.v[0], 1, kFsMirrorV);
             launch_fwd_p(lc, g, b, F, it, box_points(lo, hi));
             launch_inject_source(lc, g, b, F.p, w->stf, it, src_scale);
+            launch_free_surface(lc, g, F.p, 1, kFsMirrorP);
             if (nr > 0) launch_gather(lc, g, b, F.p, out, pl.seis_off, w->nt, it);
         }
         if (nr > 0) launch_nonfinite(lc, out, (long long)w->nt * nr, pl.flag);

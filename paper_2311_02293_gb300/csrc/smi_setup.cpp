@@ -102,21 +102,39 @@ bool make_stencil(const Grid &g, const double pos[3], double kaiser_b, Stencil *
         const int base = on_node ? (int)nearest : (int)std::floor(x);
         // the nominal 2*ri-node stencil must fit in the extended grid
         if (base - g.ri + 1 < 0 || base + g.ri > g.ne[ax] - 1) return false;
+        // free surface on the top face (image-source form of Hicks 2002): a
+        // weight above the surface node L folds, negated, onto its mirror
+        // node 2L - i, and the weight at L is dropped (p = 0 there)
+        const bool fold = ax == 0 && g.freesurf;
         if (on_node) {
             st->first[ax] = base;
             st->cnt[ax] = 1;
-            st->w[ax][0] = 1.0f;
+            st->w[ax][0] = (fold && base == g.L[0]) ? 0.0f : 1.0f;
         } else {
             st->first[ax] = base - g.ri + 1;
             st->cnt[ax] = 2 * g.ri;
+            double wd[kMaxTaps] = {0};
             for (int k = 0; k < 2 * g.ri; k++) {
                 const double u = (st->first[ax] + k) - x;
                 const double sinc = std::sin(M_PI * u) / (M_PI * u);
                 const double q = u / g.ri;
                 const double arg = 1.0 - q * q;
                 const double win = arg > 0.0 ? std::cyl_bessel_i(0.0, kaiser_b * std::sqrt(arg)) / i0b : 0.0;
-                st->w[ax][k] = (float)(sinc * win);
+                wd[k] = sinc * win;
             }
+            if (fold) {
+                for (int k = 0; k < 2 * g.ri; k++) {
+                    const int node = st->first[ax] + k;
+                    if (node >= g.L[0]) continue;
+                    const int km = 2 * g.L[0] - node - st->first[ax];
+                    if (km >= 2 * g.ri) return false;
+                    wd[km] -= wd[k];
+                    wd[k] = 0.0;
+                }
+                const int k0 = g.L[0] - st->first[ax];
+                if (k0 >= 0 && k0 < 2 * g.ri) wd[k0] = 0.0;
+            }
+            for (int k = 0; k < 2 * g.ri; k++) st->w[ax][k] = (float)wd[k];
         }
     }
     return true;

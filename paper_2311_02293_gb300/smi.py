@@ -157,6 +157,7 @@ class Problem:
     profile: bool = False
     dr: int = 1             # boundary decimation ratio (Sec. 4.2)
     img_norm: bool = False  # smi_rtm: normalise each shot's image by its source illumination
+    freesurf: bool = False  # free surface on the top face (image method, Sec. 2.1)
 
 
 def _geometry(srcs, recs):
@@ -204,6 +205,7 @@ def _opts(prob: Problem, stream):
     o.profile = int(prob.profile)
     o.dr = int(prob.dr)
     o.img_norm = int(prob.img_norm)
+    o.freesurf = int(prob.freesurf)
     if stream is not None:
         o.stream = stream
     elif torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():

@@ -69,15 +69,15 @@ def test_bad_options_rejected_on_host(smi, field, value, code):
     assert e.value.code == code
 
 
-def test_unbuilt_features_are_refused(smi):
+def test_bad_flags_are_refused(smi):
     o = smi.smi_opts()
     smi.lib().smi_opts_default(ctypes.byref(o))
     m = smi.smi_model(2, 30, 30, 1, 10.0, 10.0, 1.0, None, None)
     geo = smi.smi_geometry(0, None, None, None)
     w = smi.smi_wavelet(10, 1e-3, 10.0, None)
-    # free surface is not built; a decimation ratio below 1 is an argument
-    # error (both refused before any device work)
-    for field, value, code in (("freesurf", 1, -8), ("dr", 0, -1)):
+    # a free-surface flag other than 0 / 1 and a decimation ratio below 1
+    # are argument errors (both refused before any device work)
+    for field, value, code in (("freesurf", 2, -1), ("dr", 0, -1)):
         o2 = smi.smi_opts.from_buffer_copy(o)
         setattr(o2, field, value)
         rc = smi.lib().smi_forward(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w),
