@@ -61,11 +61,12 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-scale", type=float, default=0.5,
                     help="grid sizes and nt of the serving mix relative to the full mix")
-    ap.add_argument("--profile", choices=["fwd", "rtm"],
+    ap.add_argument("--profile", choices=["fwd", "rtm", "family"],
                     help="profiling case instead: one untimed forward call (observed data), then one forward "
                          "or RTM call of a one-shot salt model, printing per-class times")
     ap.add_argument("--n", type=int, default=300, help="physical grid size of the profiling case (n^3)")
     ap.add_argument("--no-box", action="store_true", help="profiling case without the computing box")
+    ap.add_argument("--freesurf", action="store_true", help="profiling case with the free surface (Sec. 2.1)")
     return ap.parse_args()
 
 
@@ -334,9 +335,31 @@ def run_profile(args):
     dev = torch.device("cuda:0")
     w = synth.salt_3d(n=args.n, nt=args.nt, nshot=1)
     vp, rho, stf = (torch.from_numpy(a).to(dev) for a in (w.vp, w.rho, w.stf))
-    prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, profile=True, use_box=not args.no_box)
+    prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, profile=True, use_box=not args.no_box,
+                       freesurf=args.freesurf)
     seis = smi.smi_forward(vp, rho, prob, w.srcs, w.recs, stf)
     torch.cuda.synchronize()
+    if args.profile == "family":
+        # the FWI gradient of Vp alone against the (Vp, Ip) family gradient
+        # (density part included): call times with CUDA events, warm calls
+        dobs = (0.9 * seis[0]).contiguous()
+
+        def timed(f):
+            f()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+        t_vp = timed(lambda: smi.smi_fwi_gradient(vp, rho, prob, w.srcs, w.recs, stf, dobs))
+        t_fam = timed(lambda: smi.smi_fwi_gradient_family(vp, rho, prob, w.srcs, w.recs, stf, dobs, family=2))
+        st = smi.smi_last_stats()
+        print(json.dumps({"profile": "family", "n": args.n, "nt": args.nt, "box": not args.no_box,
+                          "ms_gradient_vp": t_vp, "ms_gradient_family2": t_fam, "ratio": t_fam / t_vp,
+                          "kernel_launches_family2": st["kernel_launches"]}), flush=True)
+        return
     if args.profile == "fwd":
         smi.smi_forward(vp, rho, prob, w.srcs, w.recs, stf)
     else:
@@ -344,7 +367,7 @@ def run_profile(args):
     torch.cuda.synchronize()
     st = smi.smi_last_stats()
     names = ["forward", "adjoint", "reconstruction"]
-    line = {"profile": args.profile, "n": args.n, "nt": args.nt, "box": not args.no_box,
+    line = {"profile": args.profile, "n": args.n, "nt": args.nt, "box": not args.no_box, "freesurf": args.freesurf,
             "ms": dict(zip(names, st["ms"])),
             "algorithmic_gbs": {c: (b / (m * 1e6) if m else None) for c, b, m in zip(names, st["bytes"], st["ms"])},
             "kernel_launches": st["kernel_launches"]}
