@@ -5,12 +5,17 @@
   (Nocedal 1980), and alpha from a backtracking line search on the
   sufficient-decrease (Armijo) condition (Nocedal & Wright 2006).  This is
   the paper's nonlinear FWI algorithm (Sec. 2.2).
+- ``lbfgs_family``: the multiparameter form (Sec. 2.2, Sec. 3.7): the
+  inversion parameters are the logarithms of family 1 (Vp, rho) or family 2
+  (Vp, Ip = rho Vp), stacked into one vector for the same recursion, with
+  bounds on Vp and rho mapped to bounds on those logarithms.
 - ``shuffle_batches`` / ``sgd``: batchwise stochastic gradient descent.  The
   shots are randomly shuffled into batches of at most ``batchsize``, the last
   one taking the remainder, and each batch makes one steepest-descent update
   (Sec. 4.3, batchwise job scheduling).
 
-Every misfit and gradient comes from ``smi.smi_fwi_gradient`` on the GPU.
+Every misfit and gradient comes from ``smi.smi_fwi_gradient`` or
+``smi.smi_fwi_gradient_family`` on the GPU.
 The vectors of the recursion live on the model's device.  A trial model that
 the library refuses (CFL or dispersion) counts as a failed line-search step.
 """
@@ -120,6 +125,63 @@ def lbfgs(vp0, rho, prob, srcs, recs, stf, dobs, niter: int = 5, memory: int = 5
     from . import smi
     return minimize_lbfgs(_fwi_evaluator(rho, prob, srcs, recs, stf, dobs), vp0, niter, memory, first_step,
                           bounds, refused=(smi.SmiError,))
+
+
+def family_parameters(vp, rho, family: int):
+    """(log m1, log m2) stacked: family 1 (Vp, rho), family 2 (Vp, Ip = rho Vp)."""
+    import torch
+    return torch.stack([torch.log(vp), torch.log(rho if family == 1 else rho * vp)])
+
+
+def family_model(m, family: int):
+    """Inverse of family_parameters: (vp, rho)."""
+    import torch
+    vp = torch.exp(m[0]).contiguous()
+    p2 = torch.exp(m[1])
+    return vp, (p2 if family == 1 else p2 / vp).contiguous()
+
+
+def family_bounds(vp_bounds, rho_bounds, family: int, like):
+    """Bounds on the stacked log-parameters from bounds on Vp and rho (for
+    family 2, Ip in [rho_min vp_min, rho_max vp_max])."""
+    import torch
+    lo2 = rho_bounds[0] if family == 1 else rho_bounds[0] * vp_bounds[0]
+    hi2 = rho_bounds[1] if family == 1 else rho_bounds[1] * vp_bounds[1]
+    one = torch.ones_like(like[0])
+    lo = torch.stack([one * float(np.log(vp_bounds[0])), one * float(np.log(lo2))])
+    hi = torch.stack([one * float(np.log(vp_bounds[1])), one * float(np.log(hi2))])
+    return lo, hi
+
+
+def _family_evaluator(prob, srcs, recs, stf, dobs, family: int):
+    """m (stacked log-parameters) -> (J, dJ/dm) through smi_fwi_gradient_family
+    with the log transform."""
+    import torch
+    from . import smi
+
+    def evaluate(m):
+        vp, rho = family_model(m, family)
+        J, g1, g2 = smi.smi_fwi_gradient_family(vp, rho, prob, srcs, recs, stf, dobs, family=family, log=True)
+        return float(J.item()), torch.stack([g1, g2])
+    return evaluate
+
+
+def lbfgs_family(vp0, rho0, prob, srcs, recs, stf, dobs, family: int = 2, niter: int = 5, memory: int = 5,
+                 first_step: float = 0.02, vp_bounds: tuple | None = None, rho_bounds: tuple | None = None):
+    """Multiparameter L-BFGS FWI in family 1 (Vp, rho) or 2 (Vp, Ip) on the
+    logarithms of the parameters (Sec. 2.2, Sec. 3.7).  first_step: the
+    largest change of a log-parameter in the first trial (0.02: about 2 %).
+    vp_bounds, rho_bounds: (min, max), both or neither.  Returns
+    (vp, rho, History)."""
+    from . import smi
+    m0 = family_parameters(vp0, rho0, family)
+    bounds = None
+    if vp_bounds is not None and rho_bounds is not None:
+        bounds = family_bounds(vp_bounds, rho_bounds, family, m0)
+    m, hist = minimize_lbfgs(_family_evaluator(prob, srcs, recs, stf, dobs, family), m0, niter, memory,
+                             first_step, bounds, refused=(smi.SmiError,))
+    vp, rho = family_model(m, family)
+    return vp, rho, hist
 
 
 def shuffle_batches(nshot: int, batchsize: int, seed: int = 0) -> list:

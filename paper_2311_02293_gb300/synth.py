@@ -99,6 +99,12 @@ def two_layer_2d(nz=201, nx=201, h=10.0, nt=1000, dt=1e-3, fm=10.0, order=4) -> 
                     src, [rec])
 
 
+def gardner(vp) -> np.ndarray:
+    """Gardner's relation rho = 310 vp^0.25 (kg/m^3, vp in m/s; Gardner et
+    al. 1974), the density the paper's multiparameter example uses."""
+    return (310.0 * np.asarray(vp, dtype=np.float64) ** 0.25).astype(np.float32)
+
+
 def layered_fault_2d(nz=301, nx=1001, h=12.5, nt=3000, dt=1e-3, fm=8.0, order=8,
                      nshot=40, seed=SEED_BASE + 2) -> Workload:
     """2D FWI stand-in for Marmousi's shape: 8-15 layers with vp increasing

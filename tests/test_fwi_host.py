@@ -101,3 +101,19 @@ def test_shuffled_batches_partition_the_shots(nshot, bs):
     assert [len(b) for b in batches] == [bs] * (nshot // bs) + ([nshot % bs] if nshot % bs else [])
     again = fwi.shuffle_batches(nshot, bs, seed=1)
     assert all(np.array_equal(a, b) for a, b in zip(batches, again))
+
+
+@pytest.mark.parametrize("family", [1, 2])
+def test_family_parameters_round_trip_and_bounds(family):
+    vp = torch.tensor([[1500.0, 2500.0], [3000.0, 4500.0]], dtype=torch.float64)
+    rho = torch.tensor([[1000.0, 2000.0], [2200.0, 2600.0]], dtype=torch.float64)
+    m = fwi.family_parameters(vp, rho, family)
+    assert m.shape == (2, 2, 2)
+    v2, r2 = fwi.family_model(m, family)
+    assert torch.allclose(v2, vp, rtol=1e-14) and torch.allclose(r2, rho, rtol=1e-14)
+    if family == 2:
+        assert torch.allclose(torch.exp(m[1]), vp * rho, rtol=1e-14)
+    lo, hi = fwi.family_bounds((1400.0, 4600.0), (900.0, 2700.0), family, m)
+    assert torch.all(lo <= m) and torch.all(m <= hi)
+    ip_lo = 900.0 if family == 1 else 900.0 * 1400.0
+    assert torch.allclose(lo[1], torch.full_like(lo[1], np.log(ip_lo)))

@@ -49,3 +49,27 @@ def test_sgd_epoch_lowers_the_misfit(env):
     J1 = float(smi.smi_fwi_gradient(vp, t["rho"], prob, w.srcs, w.recs, t["stf"], dobs)[0].item())
     print("SGD epoch misfit", J0, "->", J1)
     assert J1 < J0
+
+
+@pytest.mark.parametrize("family", [1, 2])
+def test_multiparameter_lbfgs_lowers_the_misfit(env, family):
+    """Vp and density together (Gardner density in the true and the start
+    model), on the logarithms of family 1 (Vp, rho) or 2 (Vp, Ip), with the
+    bounds mapped per family."""
+    import torch
+    fwi, w, t, prob, _ = env
+    from paper_2311_02293_gb300 import smi
+    rho_true = torch.from_numpy(S.gardner(w.vp_true)).cuda()
+    rho0 = torch.from_numpy(S.gardner(w.vp)).cuda()
+    dobs = [smi.smi_forward(t["vp_true"], rho_true, prob, w.srcs[i:i + 1], w.recs[i:i + 1], t["stf"])[0]
+            for i in range(len(w.srcs))]
+    vb = (float(w.vp.min()) * 0.9, float(w.vp.max()) * 1.1)
+    rb = (float(rho0.min()) * 0.9, float(rho0.max()) * 1.1)
+    vp, rho, hist = fwi.lbfgs_family(t["vp"], rho0, prob, w.srcs, w.recs, t["stf"], dobs, family=family,
+                                     niter=6, first_step=0.03, vp_bounds=vb, rho_bounds=rb)
+    print(f"family {family} misfit", hist.misfit, "evaluations", hist.evaluations)
+    assert len(hist.misfit) == 7
+    assert all(b < a for a, b in zip(hist.misfit, hist.misfit[1:]))
+    assert hist.misfit[-1] <= 0.9 * hist.misfit[0]
+    assert float(vp.min()) >= vb[0] * (1 - 1e-6) and float(vp.max()) <= vb[1] * (1 + 1e-6)
+    assert float(rho.min()) > 0
