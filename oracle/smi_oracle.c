@@ -12,19 +12,25 @@
  *   cpml_init (Sec. 2.1: 20 PML layers after Komatitsch & Martin 2007)
  *   extend_model (Algorithm 2)
  *   computing_box_init (Sec. 4.1)
- *   forward loop: save boundary -> update v -> update p -> inject source
- *                 -> extract wavefield (Sec. 2.1 update equations)
+ *   forward loop: save boundary -> update v (-> free-surface mirror) ->
+ *                 update p -> inject source (-> free-surface mirror) ->
+ *                 extract wavefield (Sec. 2.1 update equations)
  *   residual + misfit (Eq. objfwi, Sec. 2.2)
  *   reverse loop: adjoint source -> adjoint v/p -> remove source ->
  *                 reconstruct p, v -> re-impose boundary -> image/gradient
- *                 (Eqs. gradrhokappa, adj, rtmimage; Sec. 4.2)
+ *                 (Eqs. gradrhokappa, adj, rtmimage; Sec. 4.2), with the
+ *                 density part of the gradient on request (Sec. 2.2)
  *
  * Readings of the paper (where it is silent) are listed at each function
  * and collected in the design notes: zero-valued reads outside the grid,
  * edge-replicated model extension, arithmetic-mean buoyancy, the CPML
  * profile constants, Kaiser window b, the box radius margin, the boundary
- * band layout, the discrete misfit without a dt factor, and the exact
- * discrete adjoint (scatter-form transpose of every forward operation).
+ * band layout, the discrete misfit without a dt factor, the exact
+ * discrete adjoint (scatter-form transpose of every forward operation), the
+ * free surface's image zone and folded interpolation weights, and the CPML
+ * cells' model held fixed in the gradients.  Every function is pinned by a
+ * CPU test against something other than itself (no function is parity
+ * unpinned).
  *
  * Layout: n1 = z fastest, then x (n2), then y (n3); axis 0 = z, 1 = x,
  * 2 = y.  p lives on integer nodes; v_a lives half a cell up axis a and is
