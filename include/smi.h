@@ -280,6 +280,17 @@ int smi_server_info(smi_server *s, size_t *budget, size_t *in_use, long long *qu
 /* Finishes running requests, drops queued ones, joins the workers. */
 void smi_server_destroy(smi_server *s);
 
+/* Failure detection (no paper counterpart): exercises the give-up path of
+ * the bounded waits that the 3D tile kernels use for their tile copies.  One
+ * warp waits, with the kernels' own wait helper, on a barrier that nothing
+ * completes; after `polls` polls (polls < 0: the kernels' own limit) it
+ * records the give-up and returns, as a tile kernel would before the call
+ * reports SMI_ERR_TIMEOUT.  Returns SMI_ERR_TIMEOUT when the wait gave up (the
+ * expected outcome; the context stays usable), SMI_OK if the barrier
+ * completed, another SMI_ERR_* on a CUDA failure.  ms (may be NULL): the
+ * kernel's duration.  stream: cudaStream_t or NULL. */
+int smi_wait_check(void *stream, long long polls, double *ms);
+
 /* Measurements of the calling thread's last smi_forward / smi_rtm /
  * smi_fwi_gradient call. */
 int smi_last_stats(smi_stats *st);

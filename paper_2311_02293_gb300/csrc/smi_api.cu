@@ -904,6 +904,39 @@ int smi_box_table(const smi_model *model, const smi_geometry *geom, const smi_wa
     return rc ? rc : rc2;
 }
 
+int smi_wait_check(void *stream, long long polls, double *ms)
+{
+    t_err.clear();
+    if (polls < 0) polls = wait_polls_default();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    long long launches = 0;
+    LaunchCtx lc{st, &launches};
+    int rc;
+    {
+        Arena ar(st);
+        unsigned *d_err = ar.get<unsigned>(1);
+        if (!d_err) return fail(SMI_ERR_NOMEM, "device allocation failed");
+        launch_zero(lc, d_err, sizeof(unsigned));
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+        launch_wait_check(lc, d_err, polls);
+        cudaEventRecord(e1, st);
+        unsigned h_err = 0;
+        cudaMemcpyAsync(&h_err, d_err, sizeof h_err, cudaMemcpyDeviceToHost, st);
+        rc = finish_stream(st);
+        float t = 0.0f;
+        if (!rc) cudaEventElapsedTime(&t, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (ms) *ms = t;
+        if (!rc && h_err) rc = fail(SMI_ERR_TIMEOUT, "the bounded wait gave up after %lld polls (as designed)", polls);
+    }
+    int rc2 = finish_stream(st);
+    return rc ? rc : rc2;
+}
+
 int smi_last_stats(smi_stats *st)
 {
     if (!st) return fail(SMI_ERR_ARG, "null stats");

@@ -56,7 +56,7 @@ namespace s3 {
 #endif
 constexpr int TZ = 32, TX = SMI_TX, NTHR = 8 * TX;
 constexpr int ZW = 40;                 // z extent of haloed tiles: [z0-4, z0+36)
-constexpr long long kSpin = 1LL << 22; // bounded mbarrier polls
+constexpr long long kSpin = 1LL << 18; // bounded mbarrier polls: about 1 s on GB300 (a poll suspends ~3.8 us)
 
 enum { FWD = 0, ADJ = 1, REC = 2 };
 
@@ -111,9 +111,9 @@ __device__ __forceinline__ bool mbar_test(uint64_t *b, unsigned parity)
         : "=r"(ok) : "r"(sptr(b)), "r"(parity) : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity, long long polls = kSpin)
 {
-    for (long long i = 0; i < kSpin; i++)
+    for (long long i = 0; i < polls; i++)
         if (mbar_test(b, parity)) return true;
     return false;
 }
@@ -908,6 +908,21 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
 #endif
 }
 
+// Give-up path of the bounded waits: one warp waits, with the tile kernels'
+// own wait helper, on an mbarrier that nothing completes; when the polls run
+// out it records the give-up in err like a tile kernel does, and returns.
+__global__ void k_wait_check(unsigned *err, long long polls)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0u, polls);
+    if (!ok && threadIdx.x == 0) atomicOr(err, 1u);
+}
+
 }  // namespace s3
 
 
@@ -990,6 +1005,14 @@ void run_p(const LaunchCtx &lc, const Maps3 &m, const Maps3 *lpm, const Grid &g,
 }  // namespace
 
 // The 3D path indexes one shot's arrays with 32-bit offsets.
+void launch_wait_check(const LaunchCtx &lc, unsigned *err, long long polls)
+{
+    s3::k_wait_check<<<1, 32, 0, static_cast<cudaStream_t>(lc.stream)>>>(err, polls);
+    ++*lc.launches;
+}
+
+long long wait_polls_default() { return s3::kSpin; }
+
 bool stencil3d_supported(const Grid &g)
 {
     return g.ndim == 3 && (g.N == 2 || g.N == 4) && g.ntot < (1LL << 31) && encoder() != nullptr;

@@ -13,6 +13,12 @@ struct Maps3 {
     CUtensorMap p_halo, p_core, vz_core, vx_core, vy_core, vz_halo, vx_halo, rho_v, K_core;
 };
 
+// One warp waits with the tile kernels' bounded-wait helper on an mbarrier
+// that nothing completes, for `polls` polls, then sets bit 0 of err.
+void launch_wait_check(const LaunchCtx &lc, unsigned *err, long long polls);
+// The polls after which a tile kernel's wait gives up.
+long long wait_polls_default();
+
 // True when the 3D kernels can run (3D, order 4 or 8, tensor-map encoder found).
 bool stencil3d_supported(const Grid &g);
 

@@ -81,7 +81,7 @@ class smi_stats(ctypes.Structure):
 EXPORTS = ["smi_opts_default", "smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query",
            "smi_box_table", "smi_last_stats", "smi_last_error", "smi_version", "smi_forward_noalloc",
            "smi_forward_vjp", "smi_server_create", "smi_submit", "smi_wait", "smi_poll", "smi_cancel",
-           "smi_server_info", "smi_server_destroy", "smi_fwi_gradient_family"]
+           "smi_server_info", "smi_server_destroy", "smi_fwi_gradient_family", "smi_wait_check"]
 
 
 def _load():
@@ -98,6 +98,7 @@ def _load():
     L.smi_rtm.argtypes = common + [vp, vp]
     L.smi_fwi_gradient.argtypes = common + [vp, vp, vp]
     L.smi_fwi_gradient_family.argtypes = common + [vp, c_int, c_int, vp, vp, vp]
+    L.smi_wait_check.argtypes = [vp, ctypes.c_longlong, P(ctypes.c_double)]
     L.smi_forward_vjp.argtypes = common + [vp, vp]
     L.smi_query.argtypes = common + [c_int, P(ctypes.c_size_t), P(ctypes.c_size_t), P(ctypes.c_size_t)]
     L.smi_box_table.argtypes = common + [c_int, c_int, c_int, c_int, vp, vp]
@@ -105,7 +106,8 @@ def _load():
     L.smi_last_error.restype = ctypes.c_char_p
     L.smi_version.restype = ctypes.c_char_p
     for name in ("smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query", "smi_box_table",
-                 "smi_last_stats", "smi_forward_noalloc", "smi_forward_vjp", "smi_fwi_gradient_family"):
+                 "smi_last_stats", "smi_forward_noalloc", "smi_forward_vjp", "smi_fwi_gradient_family",
+                 "smi_wait_check"):
         getattr(L, name).restype = c_int
     return L
 
@@ -368,6 +370,14 @@ def smi_box_table(vp, rho, prob: Problem, srcs, recs, stf, shot: int, which: str
                               shot, {"source": 0, "receivers": 1}[which], n0, count,
                               lo.ctypes.data, hi.ctypes.data))
     return lo, hi
+
+
+def smi_wait_check(polls: int = -1, stream=None):
+    """(return code, kernel ms) of the bounded-wait give-up check; the
+    expected code is SMI_ERR_TIMEOUT (-6)."""
+    ms = ctypes.c_double()
+    rc = _lib.smi_wait_check(stream, int(polls), ctypes.byref(ms))
+    return rc, ms.value
 
 
 def smi_last_stats() -> dict:
