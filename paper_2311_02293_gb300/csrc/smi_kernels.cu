@@ -30,6 +30,12 @@ constexpr int kThreads = 256;
 constexpr int kCpmlChunk = SMI_CPML_U;     // nodes per thread along x, CPML kernel of the x piece
 constexpr int kCpmlChunkZ = SMI_CPML_UZ;   // nodes per lane along x, CPML kernel of the z piece (adjoint)
 constexpr int kMaxBlocksX = 152 * 16;
+#ifndef SMI_CPML_MINB_F
+#define SMI_CPML_MINB_F 4
+#endif
+#ifndef SMI_CPML_MINB_A
+#define SMI_CPML_MINB_A 7
+#endif
 
 __device__ __forceinline__ long long gidx(const Grid &g, int i1, int i2, int i3)
 {
@@ -628,10 +634,18 @@ __device__ __forceinline__ void cpml_zwarp(const Grid &g, const Fields &f, const
     }
 }
 
+// Resident 256-thread blocks per SM that the register budget must allow
+// (the CPML kernels are load-latency bound: more warps hide more latency).
+// Measured on the 340^3 RTM step, box off, 30 steps: without a bound
+// (62-95 registers) forward 18.3 ms, adjoint 24.2 ms; forward kinds 4
+// blocks (64 registers) and adjoint kinds 7 (36 registers, a few spilled)
+// 17.8 ms and 21.6 ms; adjoint 5 / 6 / 8 gave 22.4 / 22.2 / 21.7 ms.
+__host__ __device__ constexpr int cpml_min_blocks(int kind) { return kind >= kAV ? SMI_CPML_MINB_A : SMI_CPML_MINB_F; }
+
 // x piece: block = ZB z indices x 256/ZB y indices (ZB = 64 in 3D, 256 in 2D
 // where y has one index); blockIdx.y = chunk along x, blockIdx.z = shot.
 template <int N, int KIND>
-__global__ void __launch_bounds__(256) k_cpml_x(Grid g, Batch b, Fields f, Pieces P, int m)
+__global__ void __launch_bounds__(256, cpml_min_blocks(KIND)) k_cpml_x(Grid g, Batch b, Fields f, Pieces P, int m)
 {
     const Piece &p = P.q[1];
     const int zb = g.ndim == 3 ? 64 : 256;
@@ -648,7 +662,7 @@ __global__ void __launch_bounds__(256) k_cpml_x(Grid g, Batch b, Fields f, Piece
 // z piece: 8 warps a block, warp -> (z segment, y index); blockIdx.y =
 // chunk along x, blockIdx.z = shot.
 template <int N, int KIND>
-__global__ void __launch_bounds__(256) k_cpml_z(Grid g, Batch b, Fields f, Pieces P, int m)
+__global__ void __launch_bounds__(256, cpml_min_blocks(KIND)) k_cpml_z(Grid g, Batch b, Fields f, Pieces P, int m)
 {
     constexpr int BW = 32 - (2 * N - 1);     // owned lanes of a warp
     const Piece &p = P.q[0];

@@ -37,6 +37,13 @@ namespace {
 
 enum { FWD = 0, ADJ = 1, REC = 2 };
 
+// Resident 256-thread blocks per SM the register budget must allow: 4
+// (64 registers, a few spilled) for the forward and adjoint kernels, 3 for
+// reconstruction.  The kernels are load-latency bound; on the 301 x 1001
+// 40-shot gradient the budget moved the step from 37.5 (no bound, 88-96
+// registers, 3 blocks) to 49.3 Gpt-updates/s.
+__host__ __device__ constexpr int k2_min_blocks(int mode) { return mode == 2 ? 3 : 4; }
+
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void put(float (&a)[4], float4 v) { a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w; }
 __device__ __forceinline__ bool in_range(int v, int lo, int hi) { return v >= lo && v <= hi; }
@@ -136,7 +143,7 @@ __device__ __forceinline__ void adj_operand(const Grid &g, int oz, int ox, float
 // L_a+N-1 .. H_a-N along a (elsewhere v_a keeps its saved value), zero
 // outside the previous box.
 template <int N, int MODE>
-__global__ void __launch_bounds__(256) k2_v(Grid g, Batch b, Fields f, int step, int z0, int x0)
+__global__ void __launch_bounds__(256, k2_min_blocks(MODE)) k2_v(Grid g, Batch b, Fields f, int step, int z0, int x0)
 {
     Node2 n;
     if (!node2<MODE>(g, b, step, z0, x0, n)) return;
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(256) k2_v(Grid g, Batch b, Fields f, int step,
 // p^2 into the second half of acc), p^{it} = p^{it+1} + dt kappa div v -
 // dt stf w / dV, zero outside the previous box.
 template <int N, int MODE>
-__global__ void __launch_bounds__(256) k2_p(Grid g, Batch b, Fields f, int step, int z0, int x0, const float *lpall,
+__global__ void __launch_bounds__(256, k2_min_blocks(MODE)) k2_p(Grid g, Batch b, Fields f, int step, int z0, int x0, const float *lpall,
                                             float *acc, int img_mode, const float *stf, float src_scale)
 {
     Node2 n;
