@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-scale", type=float, default=0.5,
                     help="grid sizes and nt of the serving mix relative to the full mix")
-    ap.add_argument("--profile", choices=["fwd", "rtm", "family"],
+    ap.add_argument("--profile", choices=["fwd", "rtm", "family", "grad2d"],
                     help="profiling case instead: one untimed forward call (observed data), then one forward "
                          "or RTM call of a one-shot salt model, printing per-class times")
     ap.add_argument("--n", type=int, default=300, help="physical grid size of the profiling case (n^3)")
@@ -333,6 +333,9 @@ def run_profile(args):
         build.build()
     from paper_2311_02293_gb300 import smi
     dev = torch.device("cuda:0")
+    if args.profile == "grad2d":
+        run_profile_grad2d(args, torch, synth, smi, dev)
+        return
     w = synth.salt_3d(n=args.n, nt=args.nt, nshot=1)
     vp, rho, stf = (torch.from_numpy(a).to(dev) for a in (w.vp, w.rho, w.stf))
     prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, profile=True, use_box=not args.no_box,
@@ -385,6 +388,33 @@ def run_profile(args):
         line["ms_with_options"] = dict(zip(names, sq["ms"]))
         line["device_bytes"] = {"f32_every_step": st["device_bytes"], "with_options": sq["device_bytes"]}
     print(json.dumps(line), flush=True)
+
+
+def run_profile_grad2d(args, torch, synth, smi, dev):
+    """The 2D FWI gradient workload (layered-fault stand-in, 301 x 1001 at
+    12.5 m, order 8, 40 shots in one batch; --nt steps): observed data from
+    the true model, one warm gradient call, then one timed call; prints the
+    call time, the grid-point rate and the per-class CUDA-event times and
+    algorithmic bandwidths of the timed call."""
+    w = synth.layered_fault_2d(nt=args.nt, nshot=40)
+    vp, rho, stf, vpt = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (w.vp, w.rho, w.stf, w.vp_true))
+    prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, profile=True, use_box=not args.no_box)
+    dobs = smi.smi_forward(vpt, rho, prob, w.srcs, w.recs, stf, flat=True)
+    smi.smi_fwi_gradient(vp, rho, prob, w.srcs, w.recs, stf, dobs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    smi.smi_fwi_gradient(vp, rho, prob, w.srcs, w.recs, stf, dobs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = smi.smi_last_stats()
+    names = ["forward", "adjoint", "reconstruction"]
+    print(json.dumps({"profile": "grad2d", "n": list(w.n), "nt": args.nt, "nshot": 40, "box": not args.no_box,
+                      "ms_call": ms, "gpts": st["point_updates"] / (ms * 1e6), "ms": dict(zip(names, st["ms"])),
+                      "algorithmic_gbs": {c: (b / (m * 1e6) if m else None)
+                                          for c, b, m in zip(names, st["bytes"], st["ms"])},
+                      "kernel_launches": st["kernel_launches"]}), flush=True)
 
 
 def run_serve(args):
