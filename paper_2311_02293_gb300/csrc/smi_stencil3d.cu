@@ -48,9 +48,6 @@ namespace s3 {
 #ifndef SMI_YUNROLL
 #define SMI_YUNROLL 2        // y planes per unrolled group (divides 2N)
 #endif
-#ifndef SMI_WAVES
-#define SMI_WAVES 1
-#endif
 #ifdef SMI_TIMING
 #include <cstdio>
 #endif
@@ -176,9 +173,13 @@ struct Decomp {
     int nzt, nxt, nyc, cy, zb;
 };
 
-// Column tiles x y-chunks of a box.  The chunk count is chosen so that the
-// items fill whole waves of the persistent grid while chunks stay long (each
-// chunk re-reads about 2N+2 planes to start its pipeline).
+// Column tiles x y-chunks of a box.  Long chunks: each chunk pays a
+// pipeline start-up of about 2N planes, so a box is split into
+// min(ylen / 16, grid / columns) chunks a column, one wave of the persistent
+// grid.  When that wave leaves more than a tenth of the CTAs idle (the
+// 340^3 box makes 242 columns for a 608-CTA grid: 2 chunks fill 80 %), the
+// chunk count grows to the smallest that fills the waves to 90 % (5 there:
+// 99.5 %).
 __device__ __forceinline__ Decomp decomp(const int lo[3], const int hi[3], int grid)
 {
     Decomp d;
@@ -191,14 +192,23 @@ __device__ __forceinline__ Decomp decomp(const int lo[3], const int hi[3], int g
         d.cy = 1;
         return d;
     }
-    const int cols = d.nzt * d.nxt;
-    // Long chunks: each chunk pays a pipeline start-up of about 2N planes.
-    // Split columns only as far as the persistent grid holds SMI_WAVES
-    // waves of items, so that no wave runs nearly empty.
-    const int chunks = max(1, min(ylen / 16, (int)((long long)SMI_WAVES * grid / cols)));
-    const int best_cy = (ylen + chunks - 1) / chunks;
-    d.cy = best_cy;
-    d.nyc = (ylen + best_cy - 1) / best_cy;
+    const long long cols = (long long)d.nzt * d.nxt;
+    const int cmax = max(1, ylen / 16);
+    auto fill = [&](int c) {
+        const long long items = cols * c;
+        return (float)items / (float)(((items + grid - 1) / grid) * grid);
+    };
+    int chunks = max(1, min(cmax, (int)(grid / cols)));
+    if (fill(chunks) < 0.9f) {
+        for (int c = chunks + 1; c <= min(cmax, 4 * chunks + 4); c++) {
+            if (fill(c) >= 0.9f) {
+                chunks = c;
+                break;
+            }
+        }
+    }
+    d.cy = (ylen + chunks - 1) / chunks;
+    d.nyc = (ylen + d.cy - 1) / d.cy;
     return d;
 }
 
