@@ -50,3 +50,24 @@ def test_two_ranks_shard_and_aggregate():
 def test_single_rank_owns_every_shot():
     import bench
     assert bench.shard_shots(8, 1, 0, 10) == [0, 1, 2, 3, 4, 5, 6, 7, 0, 1]
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference times the FP64 oracle on the host cores (no
+    GPU) and prints one JSON line with the bench's metric, a cpu_baseline
+    describing the run and an e2e object without host-device copies."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "Gpt-updates/s" and d["higher_is_better"] is True
+    assert d["metric"].startswith("3D RTM grid-point updates/s") and d["value"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
