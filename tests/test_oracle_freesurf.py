@@ -160,3 +160,18 @@ def test_reconstruction_with_free_surface(name, make, use_box):
 def test_free_surface_needs_room_for_the_image():
     w = _near_surface_2d(8)
     assert O.check(_prob(w, freesurf=True, nb=3), w.vp, w.rho) == -1
+
+
+def test_decimated_reconstruction_with_free_surface():
+    """Decimated boundaries (Sec. 4.2) with the free surface: dr = 1 is the
+    exact reversal; dr = 2 and 4 stay within the interpolator's error, which
+    grows with dr (the image half nodes are part of the top band)."""
+    w = S.layered_fault_2d(nz=60, nx=120, nt=700, nshot=1, order=8)
+    errs = {}
+    for dr in (1, 2, 4):
+        prob = _prob(w, freesurf=True, dr=dr)
+        _, snap = O.forward(prob, w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], snapshots=True)
+        rec = O.reconstruct(prob, w.vp, w.rho, w.stf, w.srcs[0])
+        errs[dr] = np.linalg.norm(rec[1:] - snap[:-1]) / np.linalg.norm(snap[:-1])
+    assert errs[1] <= 1e-10
+    assert 1e-9 < errs[2] < errs[4] <= 1e-4
