@@ -4,6 +4,9 @@
   smallest grid the scheme admits (order nodes per axis).  Each is checked
   against the oracle, or against the same call without the degenerate
   shot.
+- The 3D random-medium forward workload at full size (400 x 400 x 200,
+  corner source, 200 x 200 receivers): every seismogram sample over the
+  first 150 steps.
 - The 3D salt RTM workload at its full size (300^3 + 20 CPML layers, order
   8, 150 x 150 receiver carpet), in the configuration the bench times:
   - every seismogram sample against the oracle over the first 120 steps
@@ -145,3 +148,14 @@ def test_salt_3d_full_grid_rtm_box_invariance(smi):
     err = float(torch.linalg.norm(i_box - i_all) / torch.linalg.norm(i_all))
     print(f"box on vs off: {err:.2e}")
     assert err <= 1e-6
+
+
+def test_random_3d_full_grid_seismograms(smi):
+    """The 3D forward workload's grid and geometry at full size (400 x 400 x
+    200 + 20 CPML layers, order 8, corner source, 200 x 200 receivers), first
+    150 steps: every sample against the oracle."""
+    w = S.random_smooth_3d(nt=150)
+    seis = smi.smi_forward(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs, _dev(w.stf))[0]
+    ref = O.forward(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0])
+    assert np.linalg.norm(ref) > 0
+    assert _rel(seis.cpu().numpy(), ref) <= SEIS_TOL
