@@ -134,3 +134,15 @@ def test_family_query_counts_the_extra_memory(smi):
     b2 = smi.smi_query(*args, kind="gradient")[2]
     b4 = smi.smi_query(*args, kind="gradient_family")[2]
     assert b4 > b2
+
+
+def test_family_gradient_with_host_buffers(smi, results):
+    """Host (numpy) model, wavelet and data in, host gradients out: the same
+    numbers as with device buffers."""
+    w, args, Jr, gv, gr = results["2d_o8_nobox"]
+    J0, a1, a2 = smi.smi_fwi_gradient_family(*args, family=2, log=True)
+    host = (w.vp, w.rho, args[2], w.srcs, w.recs, w.stf, args[6].cpu().numpy())
+    J1, b1, b2 = smi.smi_fwi_gradient_family(*host, family=2, log=True)
+    assert isinstance(b1, np.ndarray) and isinstance(b2, np.ndarray)
+    assert np.array_equal(a1.cpu().numpy(), b1) and np.array_equal(a2.cpu().numpy(), b2)
+    assert float(J0.item()) == float(J1[0])
