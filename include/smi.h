@@ -65,6 +65,12 @@ extern "C" {
 #define SMI_ERR_CUDA (-7)         /* a CUDA runtime call failed */
 #define SMI_ERR_UNSUPPORTED (-8)  /* a size outside this build (boundary bands of a step >= 2^31 values) */
 
+/* Kernel family (smi_opts.kernels). */
+#define SMI_KERNELS_AUTO 0        /* the fastest kernels that support the problem */
+#define SMI_KERNELS_GENERIC 1     /* the generic grid-stride kernels (CPML inline, 64-bit indexing) that
+                                     serve 3D fields of 2^31 points or more and smi_forward_noalloc; for
+                                     tests that check them against the oracle on small problems */
+
 /* Storage precision of the saved boundaries (Sec. 4.2). */
 #define SMI_PREC_F32 0
 #define SMI_PREC_F16 1            /* FP16 with one FP32 scale per step, face and axis */
@@ -121,6 +127,7 @@ typedef struct {
     int img_norm;             /* smi_rtm only: 0 the zero-lag cross-correlation (Eq. rtmimage); 1 each
                                  shot's image divided by its source illumination sum_t p_s^2 + eps,
                                  eps = 1e-3 of the shot's largest illumination (Sec. 2.3) */
+    int kernels;              /* SMI_KERNELS_AUTO (default) or SMI_KERNELS_GENERIC; else SMI_ERR_ARG */
 } smi_opts;
 
 /* Per-call measurements, filled for the calling thread's last call.  Index
@@ -191,6 +198,26 @@ int smi_fwi_gradient_family(const smi_model *model, const smi_geometry *geom, co
  * checkpoint; no wavefield history is kept. */
 int smi_forward_vjp(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
                     const smi_opts *opts, const float *adj_src, float *grad_vp);
+
+/* Adjoint of the forward map with respect to the wavelet (the transpose of
+ * smi_forward as a linear map stf -> seismograms, Eq. adj of Sec. 2.2 with
+ * the source term's adjoint read at the source): for adj_src d (seis layout,
+ * host or device) writes stf_adj[it] = sum over shots of the exact discrete
+ * adjoint pressure sampled with the source stencil, times dt / dV (nt floats,
+ * host or device).  Runs the adjoint propagation only (no forward run, no
+ * boundaries); the adjoint box (Sec. 4.1) is the receivers' box as in
+ * smi_fwi_gradient.  The dot-product identity <L f, d> = <f, L^T d> checks
+ * it against smi_forward.  wav->stf is validated but not read. */
+int smi_forward_adjoint(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                        const smi_opts *opts, const float *adj_src, float *stf_adj);
+
+/* FP64 inner product of two float arrays of n elements on the device (the
+ * reduction of the dot-product test and of misfits, Eq. objfwi): products
+ * and sums in FP64, partial sums added in a fixed order, so the result does
+ * not depend on scheduling.  a, b: device arrays of the current device
+ * (SMI_ERR_ARG otherwise); out: one double, host or device.  stream:
+ * cudaStream_t or NULL.  Blocking. */
+int smi_dot(const float *a, const float *b, size_t n, double *out, void *stream);
 
 /* Sizes a caller needs before a call: seismogram floats, image floats and
  * the device bytes the call will allocate (kind: 0 forward, 1 rtm, 2
@@ -263,13 +290,16 @@ typedef struct {
     char error[256];
 } smi_result;
 
-/* budget_bytes = 0: 80 % of the device's free memory at creation. */
+/* budget_bytes = 0: 80 % of the device's free memory at creation.  The
+ * device current at creation runs every request of the server. */
 smi_server *smi_server_create(size_t budget_bytes, int slots);
 /* Queues *req (copied); *ticket identifies it.  Returns SMI_ERR_ARG only for
  * a malformed call; request errors are reported by smi_wait. */
 int smi_submit(smi_server *s, const smi_request *req, long long *ticket);
 /* Waits for the request to finish (timeout_s < 0: no limit); SMI_ERR_TIMEOUT
- * if it is still queued or running after timeout_s. */
+ * if it is still queued or running after timeout_s.  Once it has returned a
+ * finished request's result, the ticket is released (the server keeps no
+ * record of it): later calls with that ticket return SMI_ERR_ARG. */
 int smi_wait(smi_server *s, long long ticket, double timeout_s, smi_result *res);
 /* *state: 0 queued, 1 running, 2 finished. */
 int smi_poll(smi_server *s, long long ticket, int *state);

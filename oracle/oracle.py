@@ -126,7 +126,7 @@ def lib():
         L.orc_forward.argtypes = [P, dp, dp, dp, dp, c_int, dp, dp, dp]
         L.orc_propagate.argtypes = [P, dp, dp] + [dp] * 10 + [c_int, c_int, dp, dp]
         L.orc_adjoint.argtypes = [P, dp, dp, dp, c_int, dp, dp, c_int, dp]
-        L.orc_gradient.argtypes = [P, dp, dp, dp, dp, c_int, dp, dp, c_int, c_int, dp, dp, dp, dp]
+        L.orc_gradient.argtypes = [P, dp, dp, dp, dp, c_int, dp, dp, c_int, c_int, dp, dp, dp, dp, dp]
         L.orc_reconstruct.argtypes = [P, dp, dp, dp, dp, dp]
         L.orc_check.argtypes = [P, dp, dp]
         L.orc_cpml_profile.argtypes = [P, dp, dp, c_int, c_int, dp, dp]
@@ -287,11 +287,14 @@ def adjoint(prob: Problem, vp, rho, src, rec, res, box_mode: int = 0) -> np.ndar
 
 
 def gradient(prob: Problem, vp, rho, stf, src, rec, dobs, mode: str = "fwi", recon: bool = True,
-             with_rho: bool = False):
+             with_rho: bool = False, phase_s: np.ndarray | None = None):
     """One shot of Algorithm 2.  mode 'fwi': (misfit, dJ/dVp, seis), and
     with_rho: (misfit, dJ/dVp, seis, dJ/drho at fixed Vp); mode 'rtm':
     (0.0, image, seis); mode 'rtm_norm': (0.0, image normalised by the source
-    illumination, seis).  Output arrays have prob.shape."""
+    illumination, seis).  Output arrays have prob.shape.  phase_s (optional,
+    float64 array of 4): receives the wall-clock seconds of the forward and
+    the reverse time loops after their first steps, then of the two first
+    steps (set-up excluded)."""
     keep, vp_p, rho_p = _model(prob, vp, rho)
     stf_a, stf_p = _d(stf)
     src_a, src_p = _pts(src)
@@ -308,7 +311,8 @@ def gradient(prob: Problem, vp, rho, stf, src, rec, dobs, mode: str = "fwi", rec
     _check(lib().orc_gradient(ctypes.byref(par), vp_p, rho_p, stf_p, src_p, len(rec_a), rec_p,
                               dobs_p, {"fwi": 0, "rtm": 1, "rtm_norm": 2}[mode], int(recon), ctypes.byref(J),
                               out.ctypes.data_as(dp), seis.ctypes.data_as(dp),
-                              g_rho.ctypes.data_as(dp) if with_rho else None))
+                              g_rho.ctypes.data_as(dp) if with_rho else None,
+                              phase_s.ctypes.data_as(dp) if phase_s is not None else None))
     if with_rho:
         return J.value, out, seis, g_rho
     return J.value, out, seis

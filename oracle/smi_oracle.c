@@ -39,9 +39,22 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
+
+/* Wall-clock seconds (phase timing of the CPU baseline; no effect on results). */
+static double wall_seconds(void)
+{
+#ifdef _OPENMP
+    return omp_get_wtime();
+#else
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return ts.tv_sec + 1e-9 * ts.tv_nsec;
+#endif
+}
 
 #define ORC_OK 0
 #define ORC_ERR_ARG (-1)
@@ -451,54 +464,98 @@ static void update_p(const grid_t *g, state_t *s, const int lo[3], const int hi[
     }
 }
 
-/* Transpose of update_p restricted to a box (exact discrete adjoint, written
- * as the scatter-form transpose of each assignment).  Adjoint variables:
- * pb (of p), vb (of v), psivb (of psi_v).  Visits nodes sequentially. */
-static void adjoint_update_p(const grid_t *g, state_t *ad, const int lo[3], const int hi[3])
+/* Transpose of update_p at one node (exact discrete adjoint, written as the
+ * scatter-form transpose of each assignment).  Adjoint variables: pb (of p),
+ * vb (of v), psivb (of psi_v).  Reads only the node's own pb and psivb and
+ * scatters into vb within N nodes of it along each axis. */
+static void adjoint_node_p(const grid_t *g, state_t *ad, int i1, int i2, int i3)
 {
-    for (int i3 = lo[2]; i3 <= hi[2]; i3++)
-    for (int i2 = lo[1]; i2 <= hi[1]; i2++)
-    for (int i1 = lo[0]; i1 <= hi[0]; i1++) {
-        int i[3] = {i1, i2, i3};
-        long k = IDX(g, i1, i2, i3);
-        double q = -g->dt * g->K[k] * ad->p[k];         /* adjoint of div at i */
-        for (int a = 0; a < g->ndim; a++) {
-            double e = ad->psiv[a][k] + q;                /* adjoint of new psi_v */
-            ad->psiv[a][k] = g->cpb[a][i[a]] * e;
-            double y = (q + g->cpa[a][i[a]] * e) / g->d[a];  /* adjoint of d_a v_a */
-            for (int l = 1; l <= g->N; l++) {
-                int ip[3] = {i[0], i[1], i[2]}, im[3] = {i[0], i[1], i[2]};
-                ip[a] += l - 1;
-                im[a] -= l;
-                fadd(g, ad->v[a], ip, g->a[l - 1] * y);
-                fadd(g, ad->v[a], im, -g->a[l - 1] * y);
-            }
+    int i[3] = {i1, i2, i3};
+    long k = IDX(g, i1, i2, i3);
+    double q = -g->dt * g->K[k] * ad->p[k];         /* adjoint of div at i */
+    for (int a = 0; a < g->ndim; a++) {
+        double e = ad->psiv[a][k] + q;                /* adjoint of new psi_v */
+        ad->psiv[a][k] = g->cpb[a][i[a]] * e;
+        double y = (q + g->cpa[a][i[a]] * e) / g->d[a];  /* adjoint of d_a v_a */
+        for (int l = 1; l <= g->N; l++) {
+            int ip[3] = {i[0], i[1], i[2]}, im[3] = {i[0], i[1], i[2]};
+            ip[a] += l - 1;
+            im[a] -= l;
+            fadd(g, ad->v[a], ip, g->a[l - 1] * y);
+            fadd(g, ad->v[a], im, -g->a[l - 1] * y);
         }
     }
+}
+
+/* Transpose of update_v at one node: reads the node's own vb and psipb and
+ * scatters into pb within N nodes of it along each axis. */
+static void adjoint_node_v(const grid_t *g, state_t *ad, int i1, int i2, int i3)
+{
+    int i[3] = {i1, i2, i3};
+    long k = IDX(g, i1, i2, i3);
+    for (int a = 0; a < g->ndim; a++) {
+        double y = -g->dt * g->bu[a][k] * ad->v[a][k];  /* adjoint of (d_a p + psi) */
+        double e = ad->psip[a][k] + y;                    /* adjoint of new psi_p */
+        ad->psip[a][k] = g->cvb[a][i[a]] * e;
+        double z = (y + g->cva[a][i[a]] * e) / g->d[a];   /* adjoint of d_a p */
+        for (int l = 1; l <= g->N; l++) {
+            int ip[3] = {i[0], i[1], i[2]}, im[3] = {i[0], i[1], i[2]};
+            ip[a] += l;
+            im[a] += 1 - l;
+            fadd(g, ad->p, ip, g->a[l - 1] * z);
+            fadd(g, ad->p, im, -g->a[l - 1] * z);
+        }
+    }
+}
+
+/* Visits every node of the box [lo, hi] with fn, threads sharing the work
+ * without two of them ever scattering into the same node: the outermost
+ * active axis c is cut into chunks of at least 2N nodes, and chunks 0, 2,
+ * 4, ... run in parallel, then chunks 1, 3, 5, ...  A node of chunk k
+ * scatters only within N nodes of it along c, and two chunks of one colour
+ * are separated by a whole chunk of the other colour (2N nodes or more), so
+ * their scatter targets are disjoint.  Within a chunk the nodes are visited
+ * in the plain loop order; only the order in which contributions from
+ * different chunks add up at a node differs from one sequential sweep (an
+ * FP64 rounding-order difference). */
+static void adjoint_sweep(const grid_t *g, state_t *ad, const int lo[3], const int hi[3],
+                          void (*fn)(const grid_t *, state_t *, int, int, int))
+{
+    const int c = g->ndim - 1;
+    const int len = hi[c] - lo[c] + 1;
+    if (len <= 0 || hi[0] < lo[0] || hi[1] < lo[1]) return;
+    int nth = 1;
+#ifdef _OPENMP
+    nth = omp_get_max_threads();
+#endif
+    int C = (len + 2 * nth - 1) / (2 * nth);
+    if (C < 2 * g->N) C = 2 * g->N;
+    if (g->periodic) C = len;         /* scatters wrap around: one sequential sweep */
+    const int nchunk = (len + C - 1) / C;
+    for (int colour = 0; colour < 2; colour++) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int ch = colour; ch < nchunk; ch += 2) {
+            int a[3] = {lo[0], lo[1], lo[2]}, b[3] = {hi[0], hi[1], hi[2]};
+            a[c] = lo[c] + ch * C;
+            b[c] = a[c] + C - 1 < hi[c] ? a[c] + C - 1 : hi[c];
+            for (int i3 = a[2]; i3 <= b[2]; i3++)
+            for (int i2 = a[1]; i2 <= b[1]; i2++)
+            for (int i1 = a[0]; i1 <= b[0]; i1++)
+                fn(g, ad, i1, i2, i3);
+        }
+    }
+}
+
+/* Transpose of update_p restricted to a box. */
+static void adjoint_update_p(const grid_t *g, state_t *ad, const int lo[3], const int hi[3])
+{
+    adjoint_sweep(g, ad, lo, hi, adjoint_node_p);
 }
 
 /* Transpose of update_v restricted to a box. */
 static void adjoint_update_v(const grid_t *g, state_t *ad, const int lo[3], const int hi[3])
 {
-    for (int i3 = lo[2]; i3 <= hi[2]; i3++)
-    for (int i2 = lo[1]; i2 <= hi[1]; i2++)
-    for (int i1 = lo[0]; i1 <= hi[0]; i1++) {
-        int i[3] = {i1, i2, i3};
-        long k = IDX(g, i1, i2, i3);
-        for (int a = 0; a < g->ndim; a++) {
-            double y = -g->dt * g->bu[a][k] * ad->v[a][k];  /* adjoint of (d_a p + psi) */
-            double e = ad->psip[a][k] + y;                    /* adjoint of new psi_p */
-            ad->psip[a][k] = g->cvb[a][i[a]] * e;
-            double z = (y + g->cva[a][i[a]] * e) / g->d[a];   /* adjoint of d_a p */
-            for (int l = 1; l <= g->N; l++) {
-                int ip[3] = {i[0], i[1], i[2]}, im[3] = {i[0], i[1], i[2]};
-                ip[a] += l;
-                im[a] += 1 - l;
-                fadd(g, ad->p, ip, g->a[l - 1] * z);
-                fadd(g, ad->p, im, -g->a[l - 1] * z);
-            }
-        }
-    }
+    adjoint_sweep(g, ad, lo, hi, adjoint_node_v);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -1059,10 +1116,16 @@ static int finish_rho(const grid_t *g, const double *vp, const double *acc, doub
  * receiver box when use_box is set (Sec. 4.1).
  * seis (optional): the forward seismograms [nt][nrec].
  * out_rho (optional, mode 0): dJ/drho at fixed Vp on the physical grid (see
- * accumulate_gb). */
+ * accumulate_gb).
+ * phase_s (optional, [4]): wall-clock seconds of the forward time loop after
+ * its first step, of the reverse time loop after its first step, of the
+ * forward loop's first step and of the reverse loop's first step (the first
+ * steps touch the freshly allocated fields); set-up and the final output pass
+ * are excluded. */
 int orc_gradient(const orc_par *par, const double *vp, const double *rho, const double *stf,
                  const double *src, int nrec, const double *rec, const double *dobs,
-                 int mode, int recon, double *misfit, double *out, double *seis_out, double *out_rho)
+                 int mode, int recon, double *misfit, double *out, double *seis_out, double *out_rho,
+                 double *phase_s)
 {
     grid_t g;
     int rc = grid_init(&g, par, vp, rho);
@@ -1115,7 +1178,9 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
     stencil_extent(&sst, 1, slo, shi);
     stencil_extent(rst, nrec, rlo, rhi);
     /* forward loop */
+    double t_fwd0 = wall_seconds(), t_fwd1 = t_fwd0;
     for (int it = 0; it < g.nt; it++) {
+        if (it == 1) t_fwd1 = wall_seconds();
         if (recon && it % g.dr == 0) band_copy(&g, s.v, bands + nband * (long)(it / g.dr), 0);
         int lo[3], hi[3];
         box_at(&g, slo, shi, it, lo, hi);
@@ -1128,6 +1193,11 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
         }
     }
     if (recon && (rc = forward_continue(&g, &s, slo, shi, bands, nband, nsamp))) goto done;
+    if (phase_s) {
+        double t = wall_seconds();
+        phase_s[0] = g.nt > 1 ? t - t_fwd1 : 0.0;
+        phase_s[2] = (g.nt > 1 ? t_fwd1 : t) - t_fwd0;
+    }
     /* residual and misfit */
     double J = 0.0;
     for (long k = 0; k < (long)g.nt * nrec; k++) {
@@ -1138,7 +1208,9 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
     if (seis_out) memcpy(seis_out, seis, sizeof(double) * (long)g.nt * nrec);
 
     /* reverse loop */
+    double t_rev0 = wall_seconds(), t_rev1 = t_rev0;
     for (int it = g.nt - 1; it >= 0; it--) {
+        if (it == g.nt - 2) t_rev1 = wall_seconds();
         if (!recon) {
             memcpy(s.p, store_p + g.ntot * (long)it, sizeof(double) * g.ntot);
             for (int a = 0; a < g.ndim; a++)
@@ -1153,7 +1225,9 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
         int box[2][3], prev[2][3];
         box_at(&g, slo, shi, it, box[0], box[1]);
         box_at(&g, slo, shi, it - 1, prev[0], prev[1]);
-        /* imaging / gradient at the physical nodes of the forward box */
+        /* imaging / gradient at the physical nodes of the forward box (each node
+         * writes only its own accumulators) */
+#pragma omp parallel for collapse(2) schedule(static)
         for (int i3 = g.L[2]; i3 <= g.H[2]; i3++)
         for (int i2 = g.L[1]; i2 <= g.H[1]; i2++)
         for (int i1 = g.L[0]; i1 <= g.H[0]; i1++) {
@@ -1184,6 +1258,11 @@ int orc_gradient(const orc_par *par, const double *vp, const double *rho, const 
             for (int a = 0; a < g.ndim; a++) vold[a] = it > 0 ? store_v[a] + g.ntot * (long)(it - 1) : NULL;
             accumulate_gb(&g, &ad, vsave, it > 0 ? vold : NULL, gb);
         }
+    }
+    if (phase_s) {
+        double t = wall_seconds();
+        phase_s[1] = g.nt > 1 ? t - t_rev1 : 0.0;
+        phase_s[3] = (g.nt > 1 ? t_rev1 : t) - t_rev0;
     }
     if (want_rho && (rc = finish_rho(&g, vp, acc, gb, out_rho))) goto done;
     {

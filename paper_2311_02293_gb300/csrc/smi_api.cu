@@ -44,6 +44,25 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// SMI_OK if p is null, host memory, managed memory or device memory of the
+// current device (the one that runs the call's kernels); SMI_ERR_ARG for
+// device memory of another device, which the kernels must not read.
+int check_same_device(const void *p, const char *name)
+{
+    if (!p) return SMI_OK;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return SMI_OK;                          // plain host memory
+    }
+    if (a.type != cudaMemoryTypeDevice) return SMI_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(SMI_ERR_CUDA, "cudaGetDevice failed");
+    if (a.device != dev)
+        return fail(SMI_ERR_ARG, "%s is memory of device %d but the current device is %d", name, a.device, dev);
+    return SMI_OK;
+}
+
 // Stream-ordered device allocations of one call, released in the destructor.
 struct Arena {
     cudaStream_t st;
@@ -132,10 +151,15 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     if (o->dr < 1) return fail(SMI_ERR_ARG, "dr must be >= 1");
     if (o->shell_prec < SMI_PREC_F32 || o->shell_prec > SMI_PREC_BF16)
         return fail(SMI_ERR_ARG, "shell_prec must be SMI_PREC_F32, F16 or BF16");
+    if (o->kernels < SMI_KERNELS_AUTO || o->kernels > SMI_KERNELS_GENERIC)
+        return fail(SMI_ERR_ARG, "kernels must be SMI_KERNELS_AUTO or SMI_KERNELS_GENERIC");
     const int N = o->order / 2;
     if (o->nb < N) return fail(SMI_ERR_ARG, "nb must be >= order/2");
     if (!m->vp || !m->rho) return fail(SMI_ERR_ARG, "model arrays are null");
     if (!w->stf) return fail(SMI_ERR_ARG, "wavelet is null");
+    if (int rc = check_same_device(m->vp, "vp")) return rc;
+    if (int rc = check_same_device(m->rho, "rho")) return rc;
+    if (int rc = check_same_device(w->stf, "stf")) return rc;
     if (w->nt < 1 || !(w->dt > 0.0) || !(w->fm >= 0.0)) return fail(SMI_ERR_ARG, "bad nt, dt or fm");
     if (geo->nshot < 1 || !geo->src || !geo->rec_offset) return fail(SMI_ERR_ARG, "bad geometry");
     S.ndim = m->ndim;
@@ -349,8 +373,10 @@ size_t per_shot_bytes(const Setup &S, int kind)
     size_t b = fields + slabs + (size_t)S.nt * maxrec * 4;
     if (kind != 0) {
         b += fields;                                                   // adjoint fields
-        b += (size_t)S.nsamp * S.bands.count * band_bytes(S.bands.prec);   // saved bands
-        b += (size_t)S.nsamp * 6 * 4;                                  // band scales
+        if (kind != 5) {
+            b += (size_t)S.nsamp * S.bands.count * band_bytes(S.bands.prec);   // saved bands
+            b += (size_t)S.nsamp * 6 * 4;                                  // band scales
+        }
         if (S.dr > 1) b += fields;                                     // state kept during the continuation
         b += (size_t)g.nphys * 4 * (kind == 1 && S.img_norm ? 2 : 1);  // accumulator (+ illumination)
         if (S.rho_grad) b += (size_t)g.ndim * g.ntot * 4;              // velocities of the previous step
@@ -431,7 +457,9 @@ int finish_stream(cudaStream_t st)
 }
 
 // kind: 0 forward, 1 rtm, 2 gradient, 3 vector-Jacobian product of the
-// forward map with respect to vp (adjoint source given).  family > 0 (kind
+// forward map with respect to vp (adjoint source given), 5 adjoint of the
+// forward map with respect to the wavelet (adjoint source given; img_out
+// receives nt floats; no forward run, no reconstruction).  family > 0 (kind
 // 2): the gradient of parametrisation family 1 (Vp, rho) or 2 (Vp, Ip), of
 // the logarithms when logp, into img_out and img2_out.
 int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet *w, const smi_opts *o,
@@ -455,9 +483,14 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         const Grid &g = S.g;
         LaunchCtx lc{st, &launches};
         const size_t nseis = (size_t)S.nt * S.nrec_total;
+        const size_t nimg = kind == 5 ? (size_t)S.nt : (size_t)g.nphys;   // floats of img_out
         S.rho_grad = kind == 2 && family > 0;
         if (kind == 0 && !seis_out) return fail(SMI_ERR_ARG, "seis is null");
-        if (kind != 0 && !dobs) return fail(SMI_ERR_ARG, kind == 3 ? "adj_src is null" : "dobs is null");
+        if (kind != 0 && !dobs) return fail(SMI_ERR_ARG, kind == 3 || kind == 5 ? "adj_src is null" : "dobs is null");
+        if ((rc = check_same_device(seis_out, "seis")) || (rc = check_same_device(dobs, "dobs")) ||
+            (rc = check_same_device(img_out, "image / gradient")) || (rc = check_same_device(img2_out, "grad2")) ||
+            (rc = check_same_device(misfit_out, "misfit")))
+            return rc;
 
         // outputs and observed data on the device
         float *d_seis_out = nullptr, *d_img = nullptr;
@@ -470,9 +503,10 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         } else {
             rc = classify_and_upload(ar, dobs, nseis, &d_dobs, st);
             if (rc) return rc;
-            if (img_out) d_img = is_device_ptr(img_out) ? img_out : ar.get<float>((size_t)g.nphys);
-            else d_img = ar.get<float>((size_t)g.nphys);
+            if (img_out) d_img = is_device_ptr(img_out) ? img_out : ar.get<float>(nimg);
+            else d_img = ar.get<float>(nimg);
         }
+        double *d_series = kind == 5 ? ar.get<double>((size_t)S.nt) : nullptr;   // wavelet adjoint (FP64)
         float *d_img2 = nullptr;
         RhoAcc R{};
         if (S.rho_grad) {
@@ -501,8 +535,8 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         if (!ar.ok) return fail(SMI_ERR_NOMEM, "device allocation failed");
         launch_zero(lc, d_flag, sizeof(unsigned));
         launch_zero(lc, d_wait, sizeof(unsigned));
-        const bool fast3 = stencil3d_supported(g);
-        const bool fast2 = stencil2d_supported(g);
+        const bool fast3 = o->kernels == SMI_KERNELS_AUTO && stencil3d_supported(g);
+        const bool fast2 = o->kernels == SMI_KERNELS_AUTO && stencil2d_supported(g);
         const bool norm = kind == 1 && S.img_norm;       // normalised RTM image
 
         size_t batch_peak = 0;                   // largest batch arena (fields, bands, accumulators)
@@ -533,7 +567,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             Bands bd = S.bands;
             float *res = nullptr, *acc = nullptr, *keep = nullptr;
             unsigned *norm_mx = nullptr;
-            double *partials = nullptr;
+            double *partials = nullptr, *part = nullptr;
             const int npart = 256;
             if (kind != 0) {
                 A.p = ba.get<float>((size_t)g.ntot * nb_shot);
@@ -542,11 +576,15 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     A.psip[a] = F.psip[a];
                     A.psiv[a] = F.psiv[a];
                 }
-                bd.data = ba.raw((size_t)nb_shot * S.nsamp * bd.count * band_bytes(bd.prec));
-                bd.scale = ba.get<float>((size_t)nb_shot * S.nsamp * 6);
-                if (S.dr > 1) keep = ba.get<float>((size_t)(1 + g.ndim) * g.ntot * nb_shot);
+                if (kind != 5) {
+                    bd.data = ba.raw((size_t)nb_shot * S.nsamp * bd.count * band_bytes(bd.prec));
+                    bd.scale = ba.get<float>((size_t)nb_shot * S.nsamp * 6);
+                    if (S.dr > 1) keep = ba.get<float>((size_t)(1 + g.ndim) * g.ntot * nb_shot);
+                    acc = ba.get<float>((size_t)g.nphys * nb_shot * (norm ? 2 : 1));   // [images | illuminations]
+                } else {
+                    part = ba.get<double>((size_t)nb_shot * S.nt);
+                }
                 res = ba.get<float>(std::max<long long>(1, batch_seis));
-                acc = ba.get<float>((size_t)g.nphys * nb_shot * (norm ? 2 : 1));   // [images | illuminations]
                 if (norm) norm_mx = ba.get<unsigned>(nb_shot);
                 partials = ba.get<double>(npart);
                 if (S.rho_grad)
@@ -597,7 +635,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             // the last stored sample (every time-interpolation window of the
             // reverse loop complete); the state after step nt-1 is kept.
             const size_t fbytes = sizeof(float) * g.ntot * nb_shot;
-            const int nsteps = kind != 0 ? S.nt_fwd : S.nt;
+            const int nsteps = kind == 5 ? 0 : kind != 0 ? S.nt_fwd : S.nt;
             for (int it = 0; it < nsteps; it++) {
                 if (kind != 0 && it % S.dr == 0) launch_save_bands(lc, g, b, F, bd, it / S.dr, d_absmax);
                 tm.begin(0);
@@ -644,14 +682,15 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     cudaMemcpyAsync(F.v[a], keep + (size_t)(1 + a) * g.ntot * nb_shot, fbytes,
                                     cudaMemcpyDeviceToDevice, st);
             }
-            if (batch_seis > 0) launch_nonfinite(lc, seis, batch_seis, d_flag);
+            if (batch_seis > 0 && kind != 5) launch_nonfinite(lc, seis, batch_seis, d_flag);
             launch_nonfinite(lc, F.p, g.ntot * nb_shot, d_flag);
             if (kind == 0) continue;
 
             // ---- residual, misfit ----
             if (batch_seis > 0) {
                 const float *dob = d_dobs + (size_t)S.nt * S.rec_offset[s0];
-                launch_residual(lc, seis, dob, batch_seis, kind == 2 ? 0 : 1, res, partials, npart);
+                launch_residual(lc, kind == 5 ? dob : seis, dob, batch_seis, kind == 2 ? 0 : 1, res, partials,
+                                npart);
                 if (kind == 2) launch_sum_partials(lc, partials, npart, d_misfit);
             }
             // ---- reverse loop ----
@@ -661,20 +700,15 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 launch_zero(lc, A.psip[a], sizeof(float) * g.slab_n[a] * nb_shot);
                 launch_zero(lc, A.psiv[a], sizeof(float) * g.slab_n[a] * nb_shot);
             }
-            launch_zero(lc, acc, sizeof(float) * g.nphys * nb_shot * (norm ? 2 : 1));
+            if (acc) launch_zero(lc, acc, sizeof(float) * g.nphys * nb_shot * (norm ? 2 : 1));
             if (S.rho_grad)
                 for (int a = 0; a < g.ndim; a++)
                     cudaMemcpyAsync(R.vprev[a], F.v[a], fbytes, cudaMemcpyDeviceToDevice, st);
             // 0: gradient, 1: image, 2: image and source illumination
             const int mode = (kind == 2 || kind == 3) ? 0 : (norm ? 2 : 1);
-            for (int it = S.nt - 1; it >= 0; it--) {
-                const int mrev = S.nt - 1 - it;
-                if (max_rec > 0) launch_adj_inject(lc, g, b, A.p, res, d_soff, S.nt, it);
-                // free surface (no-ops without): the transposed p mirror on the
-                // adjoint before anything reads it; p = 0 again at the surface node
-                // of the reversed source field; the transposed v_z mirror between
-                // the two adjoint stages
-                launch_free_surface(lc, g, A.p, nb_shot, kFsFoldP);
+            // one reverse step of the source field (reconstruction with the fused
+            // imaging / gradient accumulation), then its boundary re-imposed
+            auto reconstruct = [&](int it) {
                 tm.begin(2);
                 if (fast3) {
                     launch3_p(lc, mF, &mA, g, b, F, it, 2, d_wait, acc, mode, S.stf, (float)S.src_scale);
@@ -701,6 +735,17 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 tm.end();
                 if (S.dr == 1) launch_restore_bands(lc, g, b, F, bd, it);
                 else launch_restore_bands_interp(lc, g, b, F, bd, time_weights(it, S.dr, S.nsamp));
+            };
+            for (int it = S.nt - 1; it >= 0; it--) {
+                const int mrev = S.nt - 1 - it;
+                if (max_rec > 0) launch_adj_inject(lc, g, b, A.p, res, d_soff, S.nt, it);
+                // free surface (no-ops without): the transposed p mirror on the
+                // adjoint before anything reads it; p = 0 again at the surface node
+                // of the reversed source field; the transposed v_z mirror between
+                // the two adjoint stages
+                launch_free_surface(lc, g, A.p, nb_shot, kFsFoldP);
+                if (kind == 5) launch_src_adjoint(lc, g, b, A.p, part, S.nt, it, S.src_scale);   // wavelet adjoint
+                else reconstruct(it);
                 tm.begin(1);
                 int blo[3], bhi[3];
                 batch_box(S.box_rec, mrev, blo, bhi);
@@ -734,6 +779,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     int lo[3], hi[3];
                     box_bounds(g, S.box_rec.data() + 6 * (s0 + s), mrev, lo, hi);
                     account(g, lo, hi, 1, t_stats);
+                    if (kind == 5) continue;
                     box_bounds(g, S.box_src.data() + 6 * (s0 + s), it, lo, hi);
                     for (int a = 0; a < 3; a++) {
                         lo[a] = std::max(lo[a], g.L[a]);
@@ -742,6 +788,10 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     account(g, lo, hi, 2, t_stats);
                 }
             }
+            if (kind == 5) {
+                launch_sum_series(lc, part, nb_shot, S.nt, d_series, s0 > 0);
+                continue;
+            }
             launch_nonfinite(lc, acc, g.nphys * nb_shot, d_flag);
             if (norm) launch_reduce_norm(lc, g, acc, nb_shot, norm_mx, d_img, s0 > 0);
             else launch_reduce_shots(lc, g, acc, nb_shot, d_img, s0 > 0);
@@ -749,12 +799,16 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         }
         if (S.rho_grad) launch_finalize_family(lc, g, S.vp, S.rho, d_img, R, family, logp, d_img, d_img2);
         else if (kind == 2 || kind == 3) launch_finalize_grad(lc, g.nphys, S.vp, g.dt, d_img);
+        else if (kind == 5) {
+            launch_to_float(lc, d_series, S.nt, d_img);
+            launch_nonfinite(lc, d_img, S.nt, d_flag);
+        }
 
         // outputs back to the host where needed
         if (kind == 0 && d_seis_out != seis_out)
             cudaMemcpyAsync(seis_out, d_seis_out, nseis * sizeof(float), cudaMemcpyDeviceToHost, st);
         if (kind != 0 && img_out && d_img != img_out)
-            cudaMemcpyAsync(img_out, d_img, (size_t)g.nphys * sizeof(float), cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(img_out, d_img, nimg * sizeof(float), cudaMemcpyDeviceToHost, st);
         if (d_img2 && d_img2 != img2_out)
             cudaMemcpyAsync(img2_out, d_img2, (size_t)g.nphys * sizeof(float), cudaMemcpyDeviceToHost, st);
         if (kind == 2 && misfit_out) {
@@ -770,7 +824,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         tm.collect(t_stats);
         t_stats.kernel_launches = launches;
         t_stats.device_bytes = (double)(ar.peak + batch_peak);
-        t_stats.band_values = kind == 0 ? 0 : S.bands.count;
+        t_stats.band_values = kind == 0 || kind == 5 ? 0 : S.bands.count;
     }
     // the arena's frees are stream ordered; make them complete before return
     if (!rc) rc = finish_stream(st);
@@ -804,6 +858,7 @@ void smi_opts_default(smi_opts *o)
     o->max_batch = 0;
     o->profile = 0;
     o->img_norm = 0;
+    o->kernels = SMI_KERNELS_AUTO;
 }
 
 int smi_forward(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
@@ -840,6 +895,43 @@ int smi_forward_vjp(const smi_model *model, const smi_geometry *geom, const smi_
 {
     if (!grad_vp) return fail(SMI_ERR_ARG, "grad_vp is null");
     return run(3, model, geom, wav, opts, adj_src, nullptr, grad_vp, nullptr);
+}
+
+int smi_forward_adjoint(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                        const smi_opts *opts, const float *adj_src, float *stf_adj)
+{
+    if (!stf_adj) return fail(SMI_ERR_ARG, "stf_adj is null");
+    return run(5, model, geom, wav, opts, adj_src, nullptr, stf_adj, nullptr);
+}
+
+int smi_dot(const float *a, const float *b, size_t n, double *out, void *stream)
+{
+    t_err.clear();
+    if (!out || (n > 0 && (!a || !b))) return fail(SMI_ERR_ARG, "null argument");
+    if (n > 0 && (!is_device_ptr(a) || !is_device_ptr(b)))
+        return fail(SMI_ERR_ARG, "smi_dot needs device arrays");
+    int rc;
+    if ((rc = check_same_device(a, "a")) || (rc = check_same_device(b, "b")) || (rc = check_same_device(out, "out")))
+        return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    long long launches = 0;
+    LaunchCtx lc{st, &launches};
+    {
+        Arena ar(st);
+        const int npart = 512;
+        double *partials = ar.get<double>(npart), *d_out = ar.get<double>(1);
+        if (!ar.ok) return fail(SMI_ERR_NOMEM, "device allocation failed");
+        launch_zero(lc, d_out, sizeof(double));
+        if (n > 0) {
+            launch_dot(lc, a, b, (long long)n, partials, npart);
+            launch_sum_partials(lc, partials, npart, d_out);
+        }
+        cudaMemcpyAsync(out, d_out, sizeof(double), is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        st);
+        rc = finish_stream(st);
+    }
+    int rc2 = finish_stream(st);
+    return rc ? rc : rc2;
 }
 
 int smi_query(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,

@@ -154,6 +154,16 @@ void launch_restore_bands_interp(const LaunchCtx &lc, const Grid &g, const Batch
 void launch_residual(const LaunchCtx &lc, const float *seis, const float *dobs, long long n,
                      int mode, float *res, double *partials, int npart);
 void launch_sum_partials(const LaunchCtx &lc, const double *partials, int npart, double *out);
+// Wavelet adjoint: part[s][it] = scale * sum over shot s's source stencil of
+// w * lp / kappa (FP64), the transpose of the source injection.
+void launch_src_adjoint(const LaunchCtx &lc, const Grid &g, const Batch &b, const float *lp, double *part, int nt,
+                        int it, double scale);
+// out[it] (+)= sum_s part[s][it] in shot order (FP64).
+void launch_sum_series(const LaunchCtx &lc, const double *part, int nshot, int nt, double *out, int accumulate);
+void launch_to_float(const LaunchCtx &lc, const double *a, int n, float *out);
+// FP64 partial dot products of a and b, npart of them (blocks), summed by
+// launch_sum_partials in block order.
+void launch_dot(const LaunchCtx &lc, const float *a, const float *b, long long n, double *partials, int npart);
 void launch_adj_inject(const LaunchCtx &lc, const Grid &g, const Batch &b, float *lp,
                        const float *res, const long long *seis_off, int nt, int it);
 void launch_adj_v(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, long long work);

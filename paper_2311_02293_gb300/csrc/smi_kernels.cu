@@ -829,6 +829,69 @@ __global__ void k_adj_inject(Grid g, Batch b, float *lp, const float *res, const
             }
 }
 
+// Adjoint of the wavelet samples (the transpose of k_inject_source): the
+// source of step it enters p^{it+1} as dt stf[it] w / dV, so its adjoint is
+// dt / dV sum_w w pbar over the source stencil, with pbar = lambda_p / kappa
+// (the library's adjoint pressure is kappa times the plain adjoint).  One
+// block per shot; part[s][it] = the shot's sample, summed in FP64.
+__global__ void k_src_adjoint(Grid g, Batch b, const float *lp, double *part, int nt, int it, double scale)
+{
+    __shared__ double red[kThreads];
+    const int s = blockIdx.x;
+    const Stencil &st = b.src[s];
+    const int n = st.cnt[0] * st.cnt[1] * st.cnt[2];
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int a0 = t % st.cnt[0], r = t / st.cnt[0];
+        const int a1 = r % st.cnt[1], a2 = r / st.cnt[1];
+        const long long k = gidx(g, st.first[0] + a0, st.first[1] + a1, st.first[2] + a2);
+        const double w = (double)st.w[0][a0] * (double)st.w[1][a1] * (double)st.w[2][a2];
+        acc += w * (double)lp[s * g.ntot + k] / (double)g.K[k];
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(long long)s * nt + it] = scale * red[0];
+}
+
+// out[it] (+)= sum_s part[s][it], shots in order.
+__global__ void k_sum_series(const double *part, int nshot, int nt, double *out, int accumulate)
+{
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= nt) return;
+    double v = accumulate ? out[it] : 0.0;
+    for (int s = 0; s < nshot; s++) v += part[(long long)s * nt + it];
+    out[it] = v;
+}
+
+__global__ void k_to_float(const double *a, int n, float *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)a[i];
+}
+
+// FP64 partial sums of a[i] * b[i], one per block (grid-stride; the
+// partials are summed in block order afterwards, so the result does not
+// depend on scheduling).
+__global__ void k_dot(const float *a, const float *b, long long n, double *partials)
+{
+    __shared__ double red[kThreads];
+    double acc = 0.0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        acc += (double)a[t] * (double)b[t];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
 // ---------------------------------------------------------------------------
 // Boundary bands.  blockIdx.y = region r = 2 axis + side, blockIdx.z =
 // shot; a thread moves kBandVals values of the region (stride 256, all
@@ -1501,6 +1564,31 @@ void launch_residual(const LaunchCtx &lc, const float *seis, const float *dobs, 
                      float *res, double *partials, int npart)
 {
     k_residual<<<npart, kThreads, 0, S(lc)>>>(seis, dobs, n, mode, res, partials);
+    ++*lc.launches;
+}
+
+void launch_src_adjoint(const LaunchCtx &lc, const Grid &g, const Batch &b, const float *lp, double *part, int nt,
+                        int it, double scale)
+{
+    k_src_adjoint<<<b.nshot, kThreads, 0, S(lc)>>>(g, b, lp, part, nt, it, scale);
+    ++*lc.launches;
+}
+
+void launch_sum_series(const LaunchCtx &lc, const double *part, int nshot, int nt, double *out, int accumulate)
+{
+    k_sum_series<<<(nt + kThreads - 1) / kThreads, kThreads, 0, S(lc)>>>(part, nshot, nt, out, accumulate);
+    ++*lc.launches;
+}
+
+void launch_to_float(const LaunchCtx &lc, const double *a, int n, float *out)
+{
+    k_to_float<<<(n + kThreads - 1) / kThreads, kThreads, 0, S(lc)>>>(a, n, out);
+    ++*lc.launches;
+}
+
+void launch_dot(const LaunchCtx &lc, const float *a, const float *b, long long n, double *partials, int npart)
+{
+    k_dot<<<npart, kThreads, 0, S(lc)>>>(a, b, n, partials);
     ++*lc.launches;
 }
 

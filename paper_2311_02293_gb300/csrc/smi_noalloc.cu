@@ -66,6 +66,9 @@ int scratch_address(void **out)
     return SMI_OK;
 }
 
+// Device (or managed) memory that the current device, which owns the
+// scratch array and runs the kernels, may use: device memory of another
+// device is refused.
 bool on_device(const void *p)
 {
     cudaPointerAttributes a;
@@ -73,7 +76,10 @@ bool on_device(const void *p)
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    if (a.type != cudaMemoryTypeDevice) return false;
+    int dev = -1;
+    return cudaGetDevice(&dev) == cudaSuccess && a.device == dev;
 }
 
 // Bump allocator over the scratch array (256-byte aligned pieces).
@@ -208,7 +214,8 @@ int forward_noalloc(const smi_model *m, const smi_geometry *geo, const smi_wavel
                    "(use smi_forward)", count.off, kScratchBytes);
 
     if (!on_device(m->vp) || !on_device(m->rho) || !on_device(w->stf) || !on_device(seis))
-        return err(SMI_ERR_ARG, "smi_forward_noalloc needs device pointers for vp, rho, stf and seis");
+        return err(SMI_ERR_ARG, "smi_forward_noalloc needs device pointers of the current device for vp, rho, "
+                                "stf and seis");
 
     void *base = nullptr;
     int rc = scratch_address(&base);

@@ -42,6 +42,7 @@ struct Job {
 struct smi_server {
     size_t budget = 0, in_use = 0;
     int slots = 1;
+    int device = 0;               // device current at creation: the workers run their requests there
     bool stop = false;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -70,6 +71,7 @@ struct smi_server {
 
     void worker()
     {
+        cudaSetDevice(device);
         cudaStream_t st = nullptr;
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         for (;;) {
@@ -121,6 +123,7 @@ smi_server *smi_server_create(size_t budget_bytes, int slots)
         cudaMemGetInfo(&free_b, &total_b);
         budget_bytes = (size_t)(0.8 * (double)free_b);
     }
+    cudaGetDevice(&s->device);
     s->budget = budget_bytes;
     s->slots = slots;
     for (int k = 0; k < slots; k++) s->workers.emplace_back([s] { s->worker(); });
@@ -159,12 +162,18 @@ int smi_wait(smi_server *s, long long ticket, double timeout_s, smi_result *res)
 {
     if (!s) return SMI_ERR_ARG;
     std::unique_lock<std::mutex> lk(s->mu);
-    auto it = s->jobs.find(ticket);
-    if (it == s->jobs.end()) return SMI_ERR_ARG;
-    const auto done = [&] { return s->jobs[ticket].state == 2; };
+    if (s->jobs.find(ticket) == s->jobs.end()) return SMI_ERR_ARG;
+    // a finished job leaves the map once its result is returned, so a waiter
+    // that wakes up to find it gone lost the race to another waiter
+    const auto done = [&] {
+        auto f = s->jobs.find(ticket);
+        return f == s->jobs.end() || f->second.state == 2;
+    };
     if (timeout_s < 0) s->cv_done.wait(lk, done);
     else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), done)) return SMI_ERR_TIMEOUT;
-    const Job &j = s->jobs[ticket];
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end()) return SMI_ERR_ARG;
+    const Job &j = it->second;
     if (res) {
         res->status = j.status;
         res->device_bytes = j.bytes;
@@ -174,6 +183,7 @@ int smi_wait(smi_server *s, long long ticket, double timeout_s, smi_result *res)
         strncpy(res->error, j.error.c_str(), sizeof res->error - 1);
         res->error[sizeof res->error - 1] = 0;
     }
+    s->jobs.erase(it);                // the result is delivered: release the ticket
     return SMI_OK;
 }
 

@@ -67,7 +67,7 @@ class smi_opts(ctypes.Structure):
                 ("dr", ctypes.c_int), ("use_box", ctypes.c_int), ("shell_prec", ctypes.c_int),
                 ("kaiser_b", ctypes.c_double), ("cpml_R", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("max_batch", ctypes.c_int),
-                ("profile", ctypes.c_int), ("img_norm", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("img_norm", ctypes.c_int), ("kernels", ctypes.c_int)]
 
 
 class smi_stats(ctypes.Structure):
@@ -81,7 +81,9 @@ class smi_stats(ctypes.Structure):
 EXPORTS = ["smi_opts_default", "smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query",
            "smi_box_table", "smi_last_stats", "smi_last_error", "smi_version", "smi_forward_noalloc",
            "smi_forward_vjp", "smi_server_create", "smi_submit", "smi_wait", "smi_poll", "smi_cancel",
-           "smi_server_info", "smi_server_destroy", "smi_fwi_gradient_family", "smi_wait_check"]
+           "smi_server_info", "smi_server_destroy", "smi_fwi_gradient_family", "smi_wait_check",
+           "smi_forward_adjoint", "smi_dot"]
+KERNELS = {"auto": 0, "generic": 1}
 
 
 def _load():
@@ -100,6 +102,8 @@ def _load():
     L.smi_fwi_gradient_family.argtypes = common + [vp, c_int, c_int, vp, vp, vp]
     L.smi_wait_check.argtypes = [vp, ctypes.c_longlong, P(ctypes.c_double)]
     L.smi_forward_vjp.argtypes = common + [vp, vp]
+    L.smi_forward_adjoint.argtypes = common + [vp, vp]
+    L.smi_dot.argtypes = [vp, vp, ctypes.c_size_t, P(ctypes.c_double), vp]
     L.smi_query.argtypes = common + [c_int, P(ctypes.c_size_t), P(ctypes.c_size_t), P(ctypes.c_size_t)]
     L.smi_box_table.argtypes = common + [c_int, c_int, c_int, c_int, vp, vp]
     L.smi_last_stats.argtypes = [P(smi_stats)]
@@ -107,7 +111,7 @@ def _load():
     L.smi_version.restype = ctypes.c_char_p
     for name in ("smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query", "smi_box_table",
                  "smi_last_stats", "smi_forward_noalloc", "smi_forward_vjp", "smi_fwi_gradient_family",
-                 "smi_wait_check"):
+                 "smi_wait_check", "smi_forward_adjoint", "smi_dot"):
         getattr(L, name).restype = c_int
     return L
 
@@ -136,6 +140,22 @@ def _as_f32(x):
     return a, a.ctypes.data, False
 
 
+def _on_model_device(fn):
+    """Run a wrapper with the device of its CUDA model array current, so that
+    the stream it passes and the device the library launches on are the ones
+    that own the arrays (the library refuses device memory of another
+    device)."""
+    import contextlib
+    import functools
+
+    @functools.wraps(fn)
+    def wrapped(vp, *args, **kw):
+        ctx = torch.cuda.device(vp.device) if _is_torch(vp) and vp.is_cuda else contextlib.nullcontext()
+        with ctx:
+            return fn(vp, *args, **kw)
+    return wrapped
+
+
 def _f64_host(x):
     if _is_torch(x):
         x = x.detach().cpu().numpy()
@@ -160,6 +180,7 @@ class Problem:
     dr: int = 1             # boundary decimation ratio (Sec. 4.2)
     img_norm: bool = False  # smi_rtm: normalise each shot's image by its source illumination
     freesurf: bool = False  # free surface on the top face (image method, Sec. 2.1)
+    kernels: str = "auto"   # "generic": the generic grid-stride kernels (tests)
 
 
 def _geometry(srcs, recs):
@@ -208,6 +229,7 @@ def _opts(prob: Problem, stream):
     o.dr = int(prob.dr)
     o.img_norm = int(prob.img_norm)
     o.freesurf = int(prob.freesurf)
+    o.kernels = KERNELS[prob.kernels]
     if stream is not None:
         o.stream = stream
     elif torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
@@ -245,6 +267,7 @@ def _split(flat, nt, off):
 
 
 # ---------------------------------------------------------------------------
+@_on_model_device
 def smi_forward(vp, rho, prob: Problem, srcs, recs, stf, stream=None, flat=False, out=None):
     """Seismograms of every shot (Sec. 2.1; Algorithm 2 forward loop).
     Returns a list of (nt, nrec_s) arrays (or the flat buffer if flat)."""
@@ -258,11 +281,17 @@ def smi_forward(vp, rho, prob: Problem, srcs, recs, stf, stream=None, flat=False
     return out if flat else _split(out, prob.nt, off)
 
 
+@_on_model_device
 def smi_forward_noalloc(vp, rho, prob: Problem, srcs, recs, stf, out, stream=None, flat=False):
     """smi_forward without device allocations: working memory comes from a
     fixed array inside the library (for callers that may not allocate device
     memory).  vp, rho, stf and the preallocated output `out` must be CUDA
-    tensors; calls that overlap on the GPU race on that shared array."""
+    tensors; calls that overlap on the GPU race on that shared array.  The
+    arrays are passed as they are: a tensor that is not CUDA, float32 and
+    contiguous is refused (converting it would allocate device memory)."""
+    for name, t in (("vp", vp), ("rho", rho), ("stf", stf), ("out", out)):
+        if not (_is_torch(t) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError(f"smi_forward_noalloc: {name} must be a contiguous float32 CUDA tensor")
     m, keep_m, cuda, shape = _model(vp, rho, prob.d)
     geo, keep_g, off = _geometry(srcs, recs)
     ks, ps, _ = _as_f32(stf)
@@ -282,6 +311,7 @@ def _dobs_flat(dobs, cuda, device):
     return _as_f32(dobs.reshape(-1) if hasattr(dobs, "reshape") else dobs)
 
 
+@_on_model_device
 def smi_rtm(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None, out=None):
     """Zero-lag cross-correlation image summed over shots (Eq. rtmimage)."""
     m, keep_m, cuda, shape = _model(vp, rho, prob.d)
@@ -295,6 +325,7 @@ def smi_rtm(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None, out=None
     return img.reshape(shape)
 
 
+@_on_model_device
 def smi_fwi_gradient(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None, out=None):
     """(misfit, dJ/dVp) summed over shots (Eqs. objfwi, gradrhokappa)."""
     m, keep_m, cuda, shape = _model(vp, rho, prob.d)
@@ -310,6 +341,7 @@ def smi_fwi_gradient(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None,
     return J, g.reshape(shape)
 
 
+@_on_model_device
 def smi_fwi_gradient_family(vp, rho, prob: Problem, srcs, recs, stf, dobs, family: int = 1, log: bool = False,
                             stream=None):
     """(misfit, dJ/dVp, dJ/drho) for family 1, (misfit, dJ/dVp, dJ/dIp) for
@@ -329,6 +361,7 @@ def smi_fwi_gradient_family(vp, rho, prob: Problem, srcs, recs, stf, dobs, famil
     return J, g1.reshape(shape), g2.reshape(shape)
 
 
+@_on_model_device
 def smi_forward_vjp(vp, rho, prob: Problem, srcs, recs, stf, adj_src, stream=None, out=None):
     """dL/dVp for an upstream gradient adj_src = dL/dseis (seismogram layout)."""
     m, keep_m, cuda, shape = _model(vp, rho, prob.d)
@@ -342,6 +375,37 @@ def smi_forward_vjp(vp, rho, prob: Problem, srcs, recs, stf, adj_src, stream=Non
     return g.reshape(shape)
 
 
+@_on_model_device
+def smi_forward_adjoint(vp, rho, prob: Problem, srcs, recs, stf, adj_src, stream=None, out=None):
+    """Adjoint of the forward map stf -> seismograms at adj_src (seismogram
+    layout): nt samples, summed over shots (the dot-product test's L^T d)."""
+    m, keep_m, cuda, shape = _model(vp, rho, prob.d)
+    geo, keep_g, off = _geometry(srcs, recs)
+    ks, ps, _ = _as_f32(stf)
+    kd, pd, _ = _dobs_flat(adj_src, cuda, None)
+    w = smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
+    o = _opts(prob, stream)
+    r, pr = _out(out, int(prob.nt), cuda, vp.device if cuda else None)
+    _check(_lib.smi_forward_adjoint(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w), ctypes.byref(o), pd, pr))
+    return r
+
+
+def smi_dot(a, b, stream=None) -> float:
+    """FP64 inner product of two float32 CUDA tensors, reduced on the device."""
+    if not (_is_torch(a) and _is_torch(b) and a.is_cuda and b.is_cuda):
+        raise ValueError("smi_dot needs CUDA tensors")
+    ka, pa, _ = _as_f32(a.reshape(-1))
+    kb, pb, _ = _as_f32(b.reshape(-1))
+    if ka.numel() != kb.numel():
+        raise ValueError("smi_dot: sizes differ")
+    out = ctypes.c_double()
+    with torch.cuda.device(a.device):
+        st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        _check(_lib.smi_dot(pa, pb, ka.numel(), ctypes.byref(out), st))
+    return out.value
+
+
+@_on_model_device
 def smi_query(vp, rho, prob: Problem, srcs, recs, stf, kind: str = "forward", stream=None):
     """(seis_elems, image_elems, device_bytes) of a call."""
     m, keep_m, cuda, shape = _model(vp, rho, prob.d)
@@ -356,6 +420,7 @@ def smi_query(vp, rho, prob: Problem, srcs, recs, stf, kind: str = "forward", st
     return a.value, b.value, c.value
 
 
+@_on_model_device
 def smi_box_table(vp, rho, prob: Problem, srcs, recs, stf, shot: int, which: str, n0: int,
                   count: int, stream=None):
     """Device-computed computing-box bounds (lo, hi), each (count, 3) int32."""

@@ -19,7 +19,9 @@ int main(void)
 {
     smi_opts o;
     smi_opts_default(&o);
-    if (o.order != 4 || o.nb != 20 || o.dr != 1 || o.use_box != 1 || o.freesurf != 0) return 10;
+    if (o.order != 4 || o.nb != 20 || o.dr != 1 || o.use_box != 1 || o.freesurf != 0 ||
+        o.kernels != SMI_KERNELS_AUTO)
+        return 10;
     if (!strstr(smi_version(), "sm_103a")) return 11;
     /* every entry point is declared with C linkage: take their addresses */
     typedef void (*fn)(void);
@@ -27,7 +29,7 @@ int main(void)
                 (fn)smi_forward_vjp, (fn)smi_query, (fn)smi_box_table, (fn)smi_forward_noalloc,
                 (fn)smi_wait_check, (fn)smi_last_stats, (fn)smi_last_error, (fn)smi_server_create,
                 (fn)smi_submit, (fn)smi_wait, (fn)smi_poll, (fn)smi_cancel, (fn)smi_server_info,
-                (fn)smi_server_destroy};
+                (fn)smi_server_destroy, (fn)smi_forward_adjoint, (fn)smi_dot};
     for (size_t k = 0; k < sizeof fns / sizeof fns[0]; k++)
         if (!fns[k]) return 12;
     /* argument errors come back as codes with a message, before device work */

@@ -267,3 +267,58 @@ def test_normalised_rtm_image_parity(smi, case):
                       [_dev(d.astype(np.float32)) for d in dobs])
     ref = sum(O.gradient(_oprob(w), w.vp, w.rho, w.stf, s, recs[0], d, mode="rtm_norm")[1] for s, d in zip(srcs, dobs))
     assert _rel(img.cpu().numpy(), ref) <= IMG_TOL
+
+
+@pytest.mark.parametrize("case", sorted(SMALL))
+def test_generic_kernels_parity(smi, case):
+    """The generic grid-stride kernels (opts.kernels = SMI_KERNELS_GENERIC:
+    the path of 3D fields of 2^31 points or more and of
+    smi_forward_noalloc, CPML inline) against the oracle: seismograms, FWI
+    gradient, misfit and RTM image."""
+    w = SMALL[case]()
+    vp, rho, stf = _dev(w.vp), _dev(w.rho), _dev(w.stf)
+    prob = _gprob(smi, w, kernels="generic")
+    seis = smi.smi_forward(vp, rho, prob, w.srcs, w.recs, stf)[0].cpu().numpy()
+    ref = O.forward(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0])
+    assert _rel(seis, ref) <= SEIS_TOL
+    dobs = _observed(w)
+    J, g = smi.smi_fwi_gradient(vp, rho, prob, w.srcs, w.recs, stf, _dev(dobs))
+    Jr, gr, ur = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
+    assert _misfit_ok(float(J.item()), Jr, ur)
+    assert _rel(g.cpu().numpy(), gr) <= IMG_TOL
+    img = smi.smi_rtm(vp, rho, prob, w.srcs, w.recs, stf, _dev(dobs))
+    _, ir, _ = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs, mode="rtm")
+    assert _rel(img.cpu().numpy(), ir) <= IMG_TOL
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_generic_kernels_box_off_long_3d(smi, order):
+    """The generic adjoint and reconstruction kernels with the box off over
+    hundreds of steps, energy in the CPML slabs and corners."""
+    w = S.tiny_3d(nz=18, nx=16, ny=14, nt=300, nb=8, order=order, off_grid=True)
+    dobs = _observed(w)
+    prob = _gprob(smi, w, kernels="generic", use_box=False)
+    J, g = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), prob, w.srcs, w.recs, _dev(w.stf), _dev(dobs))
+    Jr, gr, ur = O.gradient(_oprob(w, use_box=False), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
+    assert _misfit_ok(float(J.item()), Jr, ur)
+    assert _rel(g.cpu().numpy(), gr) <= IMG_TOL
+
+
+def test_16bit_boundaries_3d_against_the_oracle(smi):
+    """FP16 / BF16 boundary storage in 3D (salt model at 60^3 + 20 CPML
+    layers, order 8, 200 steps, one shot): the image and gradient error of
+    each storage precision measured against the FP64 oracle itself (not
+    against FP32 storage).  Bars as in 2D; the measured values are printed."""
+    w = S.salt_3d(n=60, nt=200, nshot=1)
+    w.stf = S.ricker(w.nt + 40, w.dt, w.fm)[40:].copy()
+    dobs = _observed(w)
+    vp, rho, stf, d = _dev(w.vp), _dev(w.rho), _dev(w.stf), _dev(dobs)
+    _, gr, _ = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
+    _, ir, _ = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs, mode="rtm")
+    for prec, tol in (("f32", IMG_TOL), ("f16", 5e-3), ("bf16", 3e-2)):
+        prob = _gprob(smi, w, shell_prec=prec)
+        _, g = smi.smi_fwi_gradient(vp, rho, prob, w.srcs, w.recs, stf, d)
+        img = smi.smi_rtm(vp, rho, prob, w.srcs, w.recs, stf, d)
+        eg, ei = _rel(g.cpu().numpy(), gr), _rel(img.cpu().numpy(), ir)
+        print(f"3D {prec} boundary storage vs oracle: gradient {eg:.2e}, image {ei:.2e}")
+        assert eg <= tol and ei <= tol

@@ -75,9 +75,68 @@ def test_noalloc_rejects_problems_beyond_its_capacity(smi):
 
 
 def test_noalloc_rejects_host_arrays(smi):
+    """The library itself refuses host pointers (called through the C ABI,
+    past the Python wrapper's own check)."""
+    import ctypes
     w = _cases()[1]
     prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb)
-    out = np.zeros(w.nt * len(w.recs[0]), np.float32)
-    with pytest.raises(smi.SmiError) as e:
-        smi.smi_forward_noalloc(w.vp, w.rho, prob, w.srcs, w.recs, w.stf, out=out)
-    assert e.value.code == -1 and "device pointers" in e.value.message
+    m, keep_m, _, _ = smi._model(w.vp, w.rho, prob.d)
+    geo, keep_g, off = smi._geometry(w.srcs, w.recs)
+    ks, ps, _ = smi._as_f32(w.stf)
+    wav = smi.smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
+    o = smi._opts(prob, None)
+    out = np.zeros(w.nt * int(off[-1]), np.float32)
+    rc = smi.lib().smi_forward_noalloc(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(wav), ctypes.byref(o),
+                                       out.ctypes.data)
+    assert rc == -1 and "device pointers" in smi.lib().smi_last_error().decode()
+
+
+def test_noalloc_wrapper_refuses_conversions(smi):
+    """A float64 or non-contiguous tensor would need a converted copy, which
+    allocates device memory: the wrapper refuses it instead."""
+    import torch
+    w = _cases()[1]
+    prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb)
+    vp, rho, stf = _dev(w.vp), _dev(w.rho), _dev(w.stf)
+    out = torch.empty(w.nt * len(w.recs[0]), device="cuda")
+    with pytest.raises(ValueError):
+        smi.smi_forward_noalloc(vp.double(), rho, prob, w.srcs, w.recs, stf, out=out)
+    with pytest.raises(ValueError):
+        smi.smi_forward_noalloc(vp.transpose(0, 2), rho, prob, w.srcs, w.recs, stf, out=out)
+
+
+def test_noalloc_free_surface_no_box_unequal_receivers(smi):
+    """The host branches of the entry point that the other cases miss: the
+    free surface, the computing box off, and shots with different receiver
+    counts (per-shot offsets into the output), against smi_forward."""
+    import torch
+    w = S.tiny_2d(nz=40, nx=50, nt=180, nb=8, order=8, src=(6, 20))
+    srcs = np.array([w.srcs[0], w.srcs[0] + np.array([0.0, 120.0, 0.0])])
+    recs = [w.recs[0], w.recs[0][::3].copy()]
+    assert len(recs[0]) != len(recs[1])
+    prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, use_box=False, freesurf=True)
+    vp, rho, stf = _dev(w.vp), _dev(w.rho), _dev(w.stf)
+    ref = smi.smi_forward(vp, rho, prob, srcs, recs, stf, flat=True)
+    out = torch.full_like(ref, float("nan"))
+    smi.smi_forward_noalloc(vp, rho, prob, srcs, recs, stf, out=out, flat=True)
+    torch.cuda.synchronize()
+    a, b = out.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(a))
+    assert np.linalg.norm(a - b) <= SEIS_TOL * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_noalloc_matches_the_oracle(smi, k):
+    """The entry point's seismograms (its own generic kernels) against the
+    FP64 oracle directly, shot by shot, at the seismogram bar."""
+    import torch
+    from oracle import oracle as O
+    w = _cases()[k]
+    prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb)
+    out = torch.empty(w.nt * sum(len(r) for r in w.recs), device="cuda")
+    seis = smi.smi_forward_noalloc(_dev(w.vp), _dev(w.rho), prob, w.srcs, w.recs, _dev(w.stf), out=out)
+    oprob = O.Problem(w.n, w.d, w.nt, w.dt, order=w.order, nb=w.nb, fm=w.fm)
+    for s in range(len(w.srcs)):
+        ref = O.forward(oprob, w.vp, w.rho, w.stf, w.srcs[s], w.recs[s])
+        a = seis[s].cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(a - ref) <= SEIS_TOL * np.linalg.norm(ref)
