@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--n", type=int, default=300, help="physical grid size of the profiling case (n^3)")
     ap.add_argument("--no-box", action="store_true", help="profiling case without the computing box")
     ap.add_argument("--freesurf", action="store_true", help="profiling case with the free surface (Sec. 2.1)")
+    ap.add_argument("--kernels", default="auto", choices=["auto", "twopass", "generic"],
+                    help="3D kernel family (auto: the single-pass step; twopass: velocity and pressure passes)")
     return ap.parse_args()
 
 
@@ -251,7 +253,7 @@ def run_ours(args):
 
     w = synth.salt_3d(nt=args.nt)
     prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, shell_prec=args.shell,
-                       profile=True, dr=args.dr)
+                       profile=True, dr=args.dr, kernels=args.kernels)
     vp = torch.from_numpy(w.vp).to(dev)
     rho = torch.from_numpy(w.rho).to(dev)
     stf = torch.from_numpy(w.stf).to(dev)
@@ -368,7 +370,7 @@ def run_profile(args):
     w = synth.salt_3d(n=args.n, nt=args.nt, nshot=1)
     vp, rho, stf = (torch.from_numpy(a).to(dev) for a in (w.vp, w.rho, w.stf))
     prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, profile=True, use_box=not args.no_box,
-                       freesurf=args.freesurf)
+                       freesurf=args.freesurf, kernels=args.kernels)
     seis = smi.smi_forward(vp, rho, prob, w.srcs, w.recs, stf)
     torch.cuda.synchronize()
     if args.profile == "family":
@@ -400,6 +402,7 @@ def run_profile(args):
     st = smi.smi_last_stats()
     names = ["forward", "adjoint", "reconstruction"]
     line = {"profile": args.profile, "n": args.n, "nt": args.nt, "box": not args.no_box, "freesurf": args.freesurf,
+            "kernels": args.kernels,
             "ms": dict(zip(names, st["ms"])),
             "algorithmic_gbs": {c: (b / (m * 1e6) if m else None) for c, b, m in zip(names, st["bytes"], st["ms"])},
             "kernel_launches": st["kernel_launches"]}

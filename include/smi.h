@@ -70,6 +70,9 @@ extern "C" {
 #define SMI_KERNELS_GENERIC 1     /* the generic grid-stride kernels (CPML inline, 64-bit indexing) that
                                      serve 3D fields of 2^31 points or more and smi_forward_noalloc; for
                                      tests that check them against the oracle on small problems */
+#define SMI_KERNELS_TWOPASS 2     /* 3D: the two-pass tile kernels (a velocity pass, then a pressure pass,
+                                     z / x CPML in band kernels) that serve the free surface, instead of
+                                     the single-pass step; for comparisons and tests */
 
 /* Storage precision of the saved boundaries (Sec. 4.2). */
 #define SMI_PREC_F32 0
@@ -127,7 +130,8 @@ typedef struct {
     int img_norm;             /* smi_rtm only: 0 the zero-lag cross-correlation (Eq. rtmimage); 1 each
                                  shot's image divided by its source illumination sum_t p_s^2 + eps,
                                  eps = 1e-3 of the shot's largest illumination (Sec. 2.3) */
-    int kernels;              /* SMI_KERNELS_AUTO (default) or SMI_KERNELS_GENERIC; else SMI_ERR_ARG */
+    int kernels;              /* SMI_KERNELS_AUTO (default), SMI_KERNELS_GENERIC or SMI_KERNELS_TWOPASS;
+                                 else SMI_ERR_ARG */
 } smi_opts;
 
 /* Per-call measurements, filled for the calling thread's last call.  Index

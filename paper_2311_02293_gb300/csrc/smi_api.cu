@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "smi_box.h"
+#include "smi_fused3d.h"
 #include "smi_internal.h"
 #include "smi_stencil3d.h"
 
@@ -98,6 +99,7 @@ struct Setup {
     int dr = 1, nsamp = 0, nt_fwd = 0;     // boundary decimation: stored samples, forward steps
     int img_norm = 0;                      // normalised RTM image
     bool rho_grad = false;                 // gradient with the density part (parametrisation families)
+    bool fused = false;                    // 3D forward / adjoint steps by the single-pass kernel
     long long nrec_total = 0;
     std::vector<int> rec_offset;
     std::vector<Stencil> src_st, rec_st;
@@ -151,8 +153,8 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     if (o->dr < 1) return fail(SMI_ERR_ARG, "dr must be >= 1");
     if (o->shell_prec < SMI_PREC_F32 || o->shell_prec > SMI_PREC_BF16)
         return fail(SMI_ERR_ARG, "shell_prec must be SMI_PREC_F32, F16 or BF16");
-    if (o->kernels < SMI_KERNELS_AUTO || o->kernels > SMI_KERNELS_GENERIC)
-        return fail(SMI_ERR_ARG, "kernels must be SMI_KERNELS_AUTO or SMI_KERNELS_GENERIC");
+    if (o->kernels < SMI_KERNELS_AUTO || o->kernels > SMI_KERNELS_TWOPASS)
+        return fail(SMI_ERR_ARG, "kernels must be SMI_KERNELS_AUTO, SMI_KERNELS_GENERIC or SMI_KERNELS_TWOPASS");
     const int N = o->order / 2;
     if (o->nb < N) return fail(SMI_ERR_ARG, "nb must be >= order/2");
     if (!m->vp || !m->rho) return fail(SMI_ERR_ARG, "model arrays are null");
@@ -209,6 +211,7 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     fd_coefficients(N, coef);
     for (int a = 0; a < 3; a++)
         for (int l = 0; l < kMaxHalf; l++) g.c[a][l] = (a < m->ndim && l < N) ? (float)(coef[l] / hh[a]) : 0.0f;
+    S.fused = o->kernels == SMI_KERNELS_AUTO && fused3d_supported(g);
 
     // inputs on the device
     const size_t nphys = (size_t)g.nphys;
@@ -366,13 +369,14 @@ size_t band_bytes(int prec) { return prec == SMI_PREC_F32 ? 4 : 2; }
 size_t per_shot_bytes(const Setup &S, int kind)
 {
     const Grid &g = S.g;
-    size_t fields = (size_t)(1 + g.ndim) * g.ntot * 4;
+    const size_t fields = (size_t)(1 + g.ndim) * g.ntot * 4;
+    const int nbuf = S.fused ? 2 : 1;          // the single-pass step reads one state buffer, writes the other
     size_t slabs = 0;
-    for (int a = 0; a < g.ndim; a++) slabs += 2 * (size_t)g.slab_n[a] * 4;
+    for (int a = 0; a < g.ndim; a++) slabs += 2 * (size_t)(S.fused && a < 2 ? g.ntot : g.slab_n[a]) * 4;
     const long long maxrec = S.nrec_total;     // upper bound of one shot's receivers
-    size_t b = fields + slabs + (size_t)S.nt * maxrec * 4;
+    size_t b = nbuf * (fields + slabs) + (size_t)S.nt * maxrec * 4;
     if (kind != 0) {
-        b += fields;                                                   // adjoint fields
+        b += nbuf * fields;                                            // adjoint fields
         if (kind != 5) {
             b += (size_t)S.nsamp * S.bands.count * band_bytes(S.bands.prec);   // saved bands
             b += (size_t)S.nsamp * 6 * 4;                                  // band scales
@@ -535,8 +539,9 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         if (!ar.ok) return fail(SMI_ERR_NOMEM, "device allocation failed");
         launch_zero(lc, d_flag, sizeof(unsigned));
         launch_zero(lc, d_wait, sizeof(unsigned));
-        const bool fast3 = o->kernels == SMI_KERNELS_AUTO && stencil3d_supported(g);
-        const bool fast2 = o->kernels == SMI_KERNELS_AUTO && stencil2d_supported(g);
+        const bool fast3 = o->kernels != SMI_KERNELS_GENERIC && stencil3d_supported(g);
+        const bool fast2 = o->kernels != SMI_KERNELS_GENERIC && stencil2d_supported(g);
+        const bool fused = S.fused;
         const bool norm = kind == 1 && S.img_norm;       // normalised RTM image
 
         size_t batch_peak = 0;                   // largest batch arena (fields, bands, accumulators)
@@ -555,12 +560,20 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             Arena ba(st);
             int *d_roff = ba.get<int>(roff.size());
             long long *d_soff = ba.get<long long>(soff.size());
-            Fields F{}, A{};
-            F.p = ba.get<float>((size_t)g.ntot * nb_shot);
-            for (int a = 0; a < g.ndim; a++) {
-                F.v[a] = ba.get<float>((size_t)g.ntot * nb_shot);
-                F.psip[a] = ba.get<float>((size_t)g.slab_n[a] * nb_shot);
-                F.psiv[a] = ba.get<float>((size_t)g.slab_n[a] * nb_shot);
+            // F, A: the current source-field and adjoint states; with the
+            // single-pass step, F2 and A2 are the buffers it writes (swapped
+            // after every step).  Memory variables of the single-pass step:
+            // z and x full-size, y in the y-slab layout.
+            Fields F{}, A{}, F2{}, A2{};
+            auto mem_n = [&](int a) { return (size_t)(fused && a < 2 ? g.ntot : g.slab_n[a]) * nb_shot; };
+            for (Fields *f : {&F, &F2}) {
+                if (f == &F2 && !fused) break;
+                f->p = ba.get<float>((size_t)g.ntot * nb_shot);
+                for (int a = 0; a < g.ndim; a++) {
+                    f->v[a] = ba.get<float>((size_t)g.ntot * nb_shot);
+                    f->psip[a] = ba.get<float>(mem_n(a));
+                    f->psiv[a] = ba.get<float>(mem_n(a));
+                }
             }
             float *seis = (kind == 0) ? d_seis_out + (size_t)S.nt * S.rec_offset[s0]
                                       : ba.get<float>(std::max<long long>(1, batch_seis));
@@ -570,11 +583,15 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             double *partials = nullptr, *part = nullptr;
             const int npart = 256;
             if (kind != 0) {
-                A.p = ba.get<float>((size_t)g.ntot * nb_shot);
-                for (int a = 0; a < g.ndim; a++) {
-                    A.v[a] = ba.get<float>((size_t)g.ntot * nb_shot);
-                    A.psip[a] = F.psip[a];
-                    A.psiv[a] = F.psiv[a];
+                for (int k = 0; k < (fused ? 2 : 1); k++) {   // the adjoint reuses the forward's memory variables
+                    Fields &a_ = k ? A2 : A;
+                    const Fields &f_ = k ? F2 : F;
+                    a_.p = ba.get<float>((size_t)g.ntot * nb_shot);
+                    for (int a = 0; a < g.ndim; a++) {
+                        a_.v[a] = ba.get<float>((size_t)g.ntot * nb_shot);
+                        a_.psip[a] = f_.psip[a];
+                        a_.psiv[a] = f_.psiv[a];
+                    }
                 }
                 if (kind != 5) {
                     bd.data = ba.raw((size_t)nb_shot * S.nsamp * bd.count * band_bytes(bd.prec));
@@ -594,9 +611,27 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             batch_peak = std::max(batch_peak, ba.peak);
             cudaMemcpyAsync(d_roff, roff.data(), sizeof(int) * roff.size(), cudaMemcpyHostToDevice, st);
             cudaMemcpyAsync(d_soff, soff.data(), sizeof(long long) * soff.size(), cudaMemcpyHostToDevice, st);
-            Maps3 mF{}, mA{};
+            Maps3 mF{}, mA{}, mF2{}, mA2{};
             if (fast3 && (!make_maps3(mF, g, F, nb_shot) || (kind != 0 && !make_maps3(mA, g, A, nb_shot))))
                 return fail(SMI_ERR_CUDA, "tensor map encoding failed");
+            MapsF fF{}, fF2{}, fA{}, fA2{};
+            MapsM fM{};
+            if (fused && (!make_maps3(mF2, g, F2, nb_shot) || !make_maps_fused(fF, g, F, nb_shot) ||
+                          !make_maps_fused(fF2, g, F2, nb_shot) || !make_maps_model(fM, g) ||
+                          (kind != 0 && (!make_maps3(mA2, g, A2, nb_shot) || !make_maps_fused(fA, g, A, nb_shot) ||
+                                         !make_maps_fused(fA2, g, A2, nb_shot)))))
+                return fail(SMI_ERR_CUDA, "tensor map encoding failed");
+            // after a single-pass step the written buffers become the current ones
+            auto swap_F = [&] {
+                std::swap(F, F2);
+                std::swap(mF, mF2);
+                std::swap(fF, fF2);
+            };
+            auto swap_A = [&] {
+                std::swap(A, A2);
+                std::swap(mA, mA2);
+                std::swap(fA, fA2);
+            };
             Batch b{};
             b.nshot = nb_shot;
             b.box_src = S.d_box_src + 6 * s0;
@@ -623,11 +658,14 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     }
                 }
             };
-            launch_zero(lc, F.p, sizeof(float) * g.ntot * nb_shot);
-            for (int a = 0; a < g.ndim; a++) {
-                launch_zero(lc, F.v[a], sizeof(float) * g.ntot * nb_shot);
-                launch_zero(lc, F.psip[a], sizeof(float) * g.slab_n[a] * nb_shot);
-                launch_zero(lc, F.psiv[a], sizeof(float) * g.slab_n[a] * nb_shot);
+            for (const Fields *f : {&F, &F2}) {
+                if (f == &F2 && !fused) break;
+                launch_zero(lc, f->p, sizeof(float) * g.ntot * nb_shot);
+                for (int a = 0; a < g.ndim; a++) {
+                    launch_zero(lc, f->v[a], sizeof(float) * g.ntot * nb_shot);
+                    launch_zero(lc, f->psip[a], sizeof(float) * mem_n(a));
+                    launch_zero(lc, f->psiv[a], sizeof(float) * mem_n(a));
+                }
             }
 
             // ---- forward loop (Algorithm 2) ----
@@ -643,7 +681,10 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 batch_box(S.box_src, it, blo, bhi);
                 // free surface (no-ops without): the v_z mirror after the velocity
                 // update, the p mirror after the pressure update and the source
-                if (fast3) {
+                if (fused) {
+                    launch3_fused(lc, fF, fM, g, b, F, F2, it, 0, d_wait);
+                    swap_F();
+                } else if (fast3) {
                     launch3_v(lc, mF, g, b, F, it, 0, d_wait);
                     launch_fwd_corrections(lc, g, b, F, it, true, blo, bhi);
                     launch_free_surface(lc, g, F.v[0], nb_shot, kFsMirrorV);
@@ -694,11 +735,14 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 if (kind == 2) launch_sum_partials(lc, partials, npart, d_misfit);
             }
             // ---- reverse loop ----
-            launch_zero(lc, A.p, sizeof(float) * g.ntot * nb_shot);
-            for (int a = 0; a < g.ndim; a++) {
-                launch_zero(lc, A.v[a], sizeof(float) * g.ntot * nb_shot);
-                launch_zero(lc, A.psip[a], sizeof(float) * g.slab_n[a] * nb_shot);
-                launch_zero(lc, A.psiv[a], sizeof(float) * g.slab_n[a] * nb_shot);
+            for (const Fields *f : {&A, &A2}) {
+                if (f == &A2 && !fused) break;
+                launch_zero(lc, f->p, sizeof(float) * g.ntot * nb_shot);
+                for (int a = 0; a < g.ndim; a++) {
+                    launch_zero(lc, f->v[a], sizeof(float) * g.ntot * nb_shot);
+                    launch_zero(lc, f->psip[a], sizeof(float) * mem_n(a));
+                    launch_zero(lc, f->psiv[a], sizeof(float) * mem_n(a));
+                }
             }
             if (acc) launch_zero(lc, acc, sizeof(float) * g.nphys * nb_shot * (norm ? 2 : 1));
             if (S.rho_grad)
@@ -749,7 +793,10 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 tm.begin(1);
                 int blo[3], bhi[3];
                 batch_box(S.box_rec, mrev, blo, bhi);
-                if (fast3) {
+                if (fused) {
+                    launch3_fused(lc, fA, fM, g, b, A, A2, mrev, 1, d_wait);
+                    swap_A();
+                } else if (fast3) {
                     launch_adj_corrections(lc, g, b, A, mrev, true, blo, bhi);
                     launch3_v(lc, mA, g, b, A, mrev, 1, d_wait);
                     launch_free_surface(lc, g, A.v[0], nb_shot, kFsFoldV);

@@ -19,6 +19,11 @@ void launch_wait_check(const LaunchCtx &lc, unsigned *err, long long polls);
 // The polls after which a tile kernel's wait gives up.
 long long wait_polls_default();
 
+// 4D tensor map (z, x, y, shot) over nshot padded fields starting at base,
+// with a box of bz (z) x bx (x) x 1 x 1 and zero fill out of bounds; false if
+// the encoder is missing or refuses the map.
+bool make_tile_map(CUtensorMap *tm, const Grid &g, const float *base, int nshot, int bz, int bx);
+
 // True when the 3D kernels can run (3D, order 4 or 8, tensor-map encoder found).
 bool stencil3d_supported(const Grid &g);
 

@@ -60,11 +60,18 @@ SMALL = {
 }
 
 
-@pytest.mark.parametrize("case", sorted(SMALL))
+# 3D runs the single-pass step by default; "twopass" forces the two-pass tile
+# kernels with the CPML band kernels (the free-surface path).
+KERNELS = {"2d_o4_off": ["auto"], "2d_o8_on": ["auto"], "3d_o4_off": ["auto", "twopass"],
+           "3d_o8_on": ["auto", "twopass"]}
+CASE_KERNELS = [(c, k) for c in sorted(SMALL) for k in KERNELS[c]]
+
+
+@pytest.mark.parametrize("case,kernels", CASE_KERNELS)
 @pytest.mark.parametrize("use_box", [True, False])
-def test_forward_parity(smi, case, use_box):
+def test_forward_parity(smi, case, kernels, use_box):
     w = SMALL[case]()
-    seis = smi.smi_forward(_dev(w.vp), _dev(w.rho), _gprob(smi, w, use_box=use_box), w.srcs,
+    seis = smi.smi_forward(_dev(w.vp), _dev(w.rho), _gprob(smi, w, use_box=use_box, kernels=kernels), w.srcs,
                            w.recs, _dev(w.stf))[0].cpu().numpy()
     ref = O.forward(_oprob(w, use_box=use_box), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0])
     assert _rel(seis, ref) <= SEIS_TOL
@@ -119,23 +126,23 @@ def _observed(w, scale=0.8):
     return (scale * ref + 0.02 * np.abs(ref).max() * rng.standard_normal(ref.shape)).astype(np.float32)
 
 
-@pytest.mark.parametrize("case", sorted(SMALL))
+@pytest.mark.parametrize("case,kernels", CASE_KERNELS)
 @pytest.mark.parametrize("use_box", [True, False])
-def test_gradient_parity(smi, case, use_box):
+def test_gradient_parity(smi, case, kernels, use_box):
     w = SMALL[case]()
     dobs = _observed(w)
-    J, g = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), _gprob(smi, w, use_box=use_box), w.srcs,
+    J, g = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), _gprob(smi, w, use_box=use_box, kernels=kernels), w.srcs,
                                 w.recs, _dev(w.stf), _dev(dobs))
     Jr, gr, ur = O.gradient(_oprob(w, use_box=use_box), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
     assert _misfit_ok(float(J.item()), Jr, ur)
     assert _rel(g.cpu().numpy(), gr) <= IMG_TOL
 
 
-@pytest.mark.parametrize("case", sorted(SMALL))
-def test_rtm_parity(smi, case):
+@pytest.mark.parametrize("case,kernels", CASE_KERNELS)
+def test_rtm_parity(smi, case, kernels):
     w = SMALL[case]()
     dobs = _observed(w, scale=1.0)
-    img = smi.smi_rtm(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs, _dev(w.stf),
+    img = smi.smi_rtm(_dev(w.vp), _dev(w.rho), _gprob(smi, w, kernels=kernels), w.srcs, w.recs, _dev(w.stf),
                       _dev(dobs))
     _, ir, _ = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs, mode="rtm")
     assert _rel(img.cpu().numpy(), ir) <= IMG_TOL
@@ -235,19 +242,20 @@ def test_errors_are_reported(smi):
     assert e.value.code == -1
 
 
-@pytest.mark.parametrize("order", [4, 8])
-def test_long_adjoint_through_cpml_corners_3d(smi, order):
+@pytest.mark.parametrize("order,kernels", [(4, "auto"), (8, "auto"), (8, "twopass")])
+def test_long_adjoint_through_cpml_corners_3d(smi, order, kernels):
     """Hundreds of steps with most of the energy inside the CPML slabs and
     their edges/corners: the transposed CPML terms of the adjoint must stay
     exact there (an inexact transpose drifts and can become unstable)."""
     w = S.tiny_3d(nz=18, nx=16, ny=14, nt=450, nb=8, order=order, off_grid=True)
     dobs = _observed(w)
-    J, g = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs,
+    J, g = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), _gprob(smi, w, kernels=kernels), w.srcs, w.recs,
                                 _dev(w.stf), _dev(dobs))
     Jr, gr, ur = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
     assert _misfit_ok(float(J.item()), Jr, ur)
     assert _rel(g.cpu().numpy(), gr) <= IMG_TOL
-    img = smi.smi_rtm(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs, _dev(w.stf), _dev(dobs))
+    img = smi.smi_rtm(_dev(w.vp), _dev(w.rho), _gprob(smi, w, kernels=kernels), w.srcs, w.recs, _dev(w.stf),
+                      _dev(dobs))
     _, ir, _ = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs, mode="rtm")
     assert _rel(img.cpu().numpy(), ir) <= IMG_TOL
 
@@ -322,3 +330,32 @@ def test_16bit_boundaries_3d_against_the_oracle(smi):
         eg, ei = _rel(g.cpu().numpy(), gr), _rel(img.cpu().numpy(), ir)
         print(f"3D {prec} boundary storage vs oracle: gradient {eg:.2e}, image {ei:.2e}")
         assert eg <= tol and ei <= tol
+
+
+@pytest.mark.parametrize("order", [4, 8])
+@pytest.mark.parametrize("use_box", [True, False])
+def test_single_pass_matches_two_pass(smi, order, use_box):
+    """The single-pass 3D step against the two-pass tile kernels on a grid of
+    several tiles in every direction (tile columns in and out of the CPML
+    bands, several y-chunks, two shots in one batch): seismograms, gradient
+    and image agree to FP32 rounding."""
+    import torch
+    w = S.tiny_3d(nz=70, nx=50, ny=44, nt=160, nb=10, order=order, off_grid=True)
+    moved = w.srcs.copy()
+    moved[:, 1] += 7 * w.d[1]
+    srcs = np.concatenate([w.srcs, moved])
+    recs = [w.recs[0], w.recs[0][::2].copy()]
+    vp, rho, stf = _dev(w.vp), _dev(w.rho), _dev(w.stf)
+    out = {}
+    for k in ("auto", "twopass"):
+        prob = _gprob(smi, w, use_box=use_box, kernels=k)
+        seis = smi.smi_forward(vp, rho, prob, srcs, recs, stf, flat=True)
+        dobs = (0.8 * seis).contiguous()
+        dobs[: dobs.numel() // 3] *= 0.5
+        J, g = smi.smi_fwi_gradient(vp, rho, prob, srcs, recs, stf, dobs)
+        img = smi.smi_rtm(vp, rho, prob, srcs, recs, stf, dobs)
+        out[k] = [t.double().cpu().numpy() for t in (seis, g, img)] + [float(J.item())]
+        torch.cuda.synchronize()
+    for a, b in zip(out["auto"][:3], out["twopass"][:3]):
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+    assert abs(out["auto"][3] - out["twopass"][3]) <= 1e-5 * abs(out["twopass"][3])
