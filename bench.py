@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--shell", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--dr", type=int, default=1, help="boundary decimation ratio (Sec. 4.2; 1 = every step)")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-other", action="store_true", help="skip the 3D forward and 2D gradient workloads")
+    ap.add_argument("--other-nt3", type=int, default=3000, help="time steps of the 3D forward workload")
+    ap.add_argument("--other-nt2", type=int, default=3000, help="time steps of the 2D gradient workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nt", type=int, default=2500, help="time steps (full workload: 2500)")
     ap.add_argument("--serve", action="store_true",
@@ -205,6 +208,59 @@ def cpu_baseline_sample(w, nsteps: int = 3):
                       f"{wall:.1f} s in all"}
 
 
+def other_workloads(smi, synth, torch, dev, peak: float, args) -> dict:
+    """The two other GPU workloads, each timed once with CUDA events after an
+    untimed warm-up call, outside the main timed region:
+      - 3D forward with the computing box: 400 x 400 x 200 + 20 CPML layers,
+        order 8, nt 3000, corner source, 200 x 200 receivers;
+      - 2D FWI gradient: 301 x 1001 + 20 layers, order 8, nt 3000, 40 shots
+        in one batch, observed data from the true model.
+    Each reports grid-point updates/s (box points) and the roofline of its
+    dominant stencil class (algorithmic bytes / that class's event time)."""
+    out = {}
+
+    def roof(st):
+        ms, by = np.array(st["ms"]), np.array(st["bytes"])
+        dom = int(np.argmax(ms))
+        ach = by[dom] / (ms[dom] / 1e3) / 1e9
+        return {"class": ["forward", "adjoint", "reconstruction"][dom], "achieved_gbs": float(ach),
+                "frac": float(ach / peak), "per_class_gbs": [float(b / (m / 1e3) / 1e9) if m > 0 else None
+                                                              for b, m in zip(by, ms)]}
+
+    def timed(f):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        f()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    w = synth.random_smooth_3d(nt=args.other_nt3)
+    vp, rho, stf = (torch.from_numpy(a).to(dev) for a in (w.vp, w.rho, w.stf))
+    prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, profile=True)
+    warm = smi.Problem(w.d, min(w.nt, 200), w.dt, w.fm, order=w.order, nb=w.nb)
+    smi.smi_forward(vp, rho, warm, w.srcs, w.recs, stf[:warm.nt].contiguous())
+    ms = timed(lambda: smi.smi_forward(vp, rho, prob, w.srcs, w.recs, stf))
+    st = smi.smi_last_stats()
+    out["forward_3d_random_400x400x200_nt%d" % w.nt] = {
+        "gpts": st["point_updates"] / (ms * 1e6), "ms": ms, "roofline": roof(st),
+        "effective_gpts": float(np.prod([n + 2 * w.nb for n in w.n]) * w.nt / (ms * 1e6))}
+    del vp, rho, stf
+
+    w = synth.layered_fault_2d(nt=args.other_nt2, nshot=40)
+    vp, rho, stf, vpt = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (w.vp, w.rho, w.stf, w.vp_true))
+    prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, profile=True)
+    dobs = smi.smi_forward(vpt, rho, prob, w.srcs, w.recs, stf, flat=True)
+    smi.smi_fwi_gradient(vp, rho, prob, w.srcs[:2], w.recs[:2], stf, dobs[: 2 * w.nt * len(w.recs[0])])
+    ms = timed(lambda: smi.smi_fwi_gradient(vp, rho, prob, w.srcs, w.recs, stf, dobs))
+    st = smi.smi_last_stats()
+    out["gradient_2d_layered_301x1001_40shots_nt%d" % w.nt] = {
+        "gpts": st["point_updates"] / (ms * 1e6), "ms": ms, "shots_per_s": 40 / (ms / 1e3), "roofline": roof(st)}
+    torch.cuda.synchronize()
+    return out
+
+
 def run_reference(args):
     world, rank, local = dist_env()
     if rank != 0:
@@ -331,6 +387,10 @@ def run_ours(args):
         e2e = {"value": eunits / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(himg.numel() * 4), "steps": args.e2e_steps}
 
+    others = None
+    if rank == 0 and world == 1 and not args.no_other:
+        others = other_workloads(smi, synth, torch, dev, measured_peaks()[0], args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(w)
@@ -347,7 +407,8 @@ def run_ours(args):
                            "parallelism": f"replicas x{world} (shots sharded)"},
                 "effective_gpts": float(eff),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
+                "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+                "other_workloads": others}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -62,3 +62,53 @@ def test_poisson_replay_reports_latency(env):
     mix = serve.run_mix(reqs[:6], dev, slots=3, rate=20.0)
     assert mix["failed"] == 0
     assert 0 < mix["p50_s"] <= mix["p99_s"] and mix["requests_per_s"] > 0
+
+
+def test_served_fp16_results_against_the_oracle(env):
+    """One small request of each kind served with FP16 boundaries (the
+    serving configuration) in one concurrent mix: each result's error against
+    the FP64 oracle and against the plain FP32 method on the same GPU (direct
+    call, FP32 boundaries).  Bars: seismograms 1e-4 (boundary storage does
+    not enter the forward run); images and gradients 5e-3 against the oracle,
+    the FP16 bar of the parity tests.  The measured values are printed."""
+    import torch
+    from oracle import oracle as O
+    from paper_2311_02293_gb300 import synth as S
+    serve, _, dev = env
+    smi = serve.smi
+    w2 = S.layered_fault_2d(nz=60, nx=150, nt=300, nshot=1, order=8)
+    w3 = S.salt_3d(n=40, nt=160, nshot=1)
+    w3.stf = S.ricker(w3.nt + 40, w3.dt, w3.fm)[40:].copy()
+    cases = [("gradient", w2), ("forward", w3), ("rtm", w3)]
+    reqs = []
+    for kind, w in cases:
+        prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, shell_prec="f16")
+        r = serve.Request(kind, w, prob)
+        reqs.append(r)
+    serve._prepare(reqs, dev)
+    refs, plain = [], []
+    for r in reqs:
+        w = r.w
+        op = O.Problem(w.n, w.d, w.nt, w.dt, order=w.order, nb=w.nb, fm=w.fm)
+        vp_t = w.vp_true if w.vp_true is not None else w.vp
+        d64 = O.forward(op, vp_t, w.rho, w.stf, w.srcs[0], w.recs[0])
+        if r.kind != "forward":                 # observed data from the oracle, never from the GPU
+            r.dobs = torch.from_numpy(d64.astype(np.float32).reshape(-1)).to(dev)
+        p32 = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb)
+        vp, rho, _ = r._dev
+        if r.kind == "forward":
+            refs.append(O.forward(op, w.vp, w.rho, w.stf, w.srcs[0], w.recs[0]).reshape(-1))
+            plain.append(smi.smi_forward(vp, rho, p32, w.srcs, w.recs, r._stf, flat=True))
+        elif r.kind == "rtm":
+            refs.append(O.gradient(op, w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], d64, mode="rtm")[1].reshape(-1))
+            plain.append(smi.smi_rtm(vp, rho, p32, w.srcs, w.recs, r._stf, r.dobs).reshape(-1))
+        else:
+            refs.append(O.gradient(op, w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], d64)[1].reshape(-1))
+            plain.append(smi.smi_fwi_gradient(vp, rho, p32, w.srcs, w.recs, r._stf, r.dobs)[1].reshape(-1))
+    mix = serve.run_mix(reqs, dev, slots=3)
+    assert mix["failed"] == 0
+    for r, out, ref, p in zip(reqs, mix["outputs"], refs, plain):
+        e_ref = float(np.linalg.norm(out.double().cpu().numpy() - ref) / np.linalg.norm(ref))
+        e_p = _rel(out, p)
+        print(f"served FP16 {r.kind} ({r.w.ndim}D): vs oracle {e_ref:.2e}, vs plain FP32 {e_p:.2e}")
+        assert e_ref <= (1e-4 if r.kind == "forward" else 5e-3)
