@@ -203,6 +203,33 @@ int smi_fwi_gradient_family(const smi_model *model, const smi_geometry *geom, co
 int smi_forward_vjp(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
                     const smi_opts *opts, const float *adj_src, float *grad_vp);
 
+/* Forward modelling that keeps its checkpoint for one later reverse pass
+ * (the boundary-saving strategy of Sec. 4.2 as the checkpoint of automatic
+ * differentiation): writes the seismograms like smi_forward and returns in
+ * *tape the saved boundaries (every dr-th step, opts->shell_prec storage),
+ * the wavefield state after the last step and the set-up tables, all on the
+ * device, for every shot at once (SMI_ERR_NOMEM if they do not fit).
+ * smi_tape_vjp then runs only the reverse loop (adjoint, source-field
+ * reconstruction, gradient accumulation): three modellings per gradient in
+ * all instead of the four of smi_forward followed by smi_forward_vjp.  The
+ * model, wavelet and stream arrays the call read must stay valid until
+ * smi_tape_free.  On error *tape is NULL. */
+typedef struct smi_tape smi_tape;
+int smi_forward_tape(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                     const smi_opts *opts, float *seis, smi_tape **tape);
+
+/* dL/dVp (grad_vp, n1*n2*n3 floats, host or device) for the upstream
+ * gradient adj_src = dL/dseis (seis layout, host or device) of the
+ * smi_forward_tape call that made the tape, exactly as smi_forward_vjp
+ * computes it, without a forward run.  stream: cudaStream_t or NULL.  A tape
+ * serves one reverse pass (the pass consumes the kept state): a second call
+ * returns SMI_ERR_ARG. */
+int smi_tape_vjp(smi_tape *tape, const float *adj_src, float *grad_vp, void *stream);
+
+/* Frees a tape's device memory (synchronising with the device); NULL is a
+ * no-op. */
+void smi_tape_free(smi_tape *tape);
+
 /* Adjoint of the forward map with respect to the wavelet (the transpose of
  * smi_forward as a linear map stf -> seismograms, Eq. adj of Sec. 2.2 with
  * the source term's adjoint read at the source): for adj_src d (seis layout,

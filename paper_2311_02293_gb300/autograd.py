@@ -3,11 +3,13 @@ exact discrete adjoint (SMIwiz, arXiv 2311.02293, Secs. 2.2 and 4.2).
 
 ``seismograms(vp, rho, prob, srcs, recs, stf)`` returns the flat seismogram
 tensor of all shots (shot s occupies nt * nrec_s samples, receiver fastest).
-Its backward pass calls ``smi_forward_vjp``: the forward modelling is run
-again saving the boundaries, and the adjoint field driven by the upstream
-gradient accumulates dL/dVp -- the saved boundaries are the checkpoint
-(Sec. 4.2), no wavefield history is stored.  The density is held fixed (no
-gradient).  Inputs must be CUDA tensors.
+The forward pass runs ``smi_forward_tape``, which keeps the saved boundaries
+and the final wavefield state on the device (the boundary-saving strategy of
+Sec. 4.2 is the checkpoint; no wavefield history is stored); the backward
+pass runs only the reverse loop from that tape (``Tape.vjp``: adjoint field
+driven by the upstream gradient, source field reconstructed backwards,
+dL/dVp accumulated) -- three modellings per gradient, no forward re-run.
+The density is held fixed (no gradient).  Inputs must be CUDA tensors.
 """
 from __future__ import annotations
 
@@ -19,19 +21,20 @@ from . import smi
 class SeismogramFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, vp, rho, prob, srcs, recs, stf):
-        seis = smi.smi_forward(vp, rho, prob, srcs, recs, stf, flat=True)
-        ctx.save_for_backward(vp, rho, stf)
-        ctx.prob, ctx.srcs, ctx.recs = prob, srcs, recs
+        if ctx.needs_input_grad[0]:
+            seis, ctx.tape = smi.smi_forward_tape(vp.detach(), rho.detach(), prob, srcs, recs, stf.detach())
+        else:
+            seis, ctx.tape = smi.smi_forward(vp, rho, prob, srcs, recs, stf, flat=True), None
         return seis
 
     @staticmethod
     def backward(ctx, grad_seis):
-        vp, rho, stf = ctx.saved_tensors
         grad_vp = None
-        if ctx.needs_input_grad[0]:
+        if ctx.tape is not None:
             g = grad_seis.detach().contiguous().float()
-            grad_vp = smi.smi_forward_vjp(vp.detach(), rho.detach(), ctx.prob, ctx.srcs, ctx.recs,
-                                          stf.detach(), g).to(vp.dtype)
+            grad_vp = ctx.tape.vjp(g)
+            ctx.tape.free()
+            ctx.tape = None
         return grad_vp, None, None, None, None, None
 
 

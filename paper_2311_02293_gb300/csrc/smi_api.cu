@@ -86,6 +86,12 @@ struct Arena {
         return p;
     }
     template <class T> T *get(size_t n) { return static_cast<T *>(raw(n * sizeof(T))); }
+    // Hands the allocations over to dst (a tape); the arena frees nothing then.
+    void release_to(std::vector<std::pair<void *, size_t>> &dst)
+    {
+        dst.insert(dst.end(), ptrs.begin(), ptrs.end());
+        ptrs.clear();
+    }
     ~Arena()
     {
         for (auto &pr : ptrs) cudaFreeAsync(pr.first, st);
@@ -112,6 +118,27 @@ struct Setup {
     int *d_box_src = nullptr, *d_box_rec = nullptr;
     int *d_tab_src = nullptr, *d_tab_rec = nullptr;   // [nshot][nt_fwd+1][6] box tables
     Bands bands{};
+};
+
+// What a forward call with a tape (smi_forward_tape) keeps on the device for
+// a later reverse-only call (smi_tape_vjp): the set-up (extended model,
+// tables), the saved boundaries and the state after the last forward step
+// of one batch holding every shot, and the reverse loop's buffers.
+struct TapeState {
+    Setup S;
+    smi_opts o{};
+    std::vector<std::pair<void *, size_t>> mem;   // owned device allocations
+    Fields F{}, F2{}, A{}, A2{};
+    Bands bd{};
+    float *res = nullptr, *acc = nullptr;
+    double *partials = nullptr;
+    int *d_roff = nullptr;
+    long long *d_soff = nullptr;
+    std::vector<int> roff;
+    std::vector<long long> soff;
+    int max_rec = 0;
+    long long batch_seis = 0;
+    bool done = false;                            // the reverse pass ran (a tape serves one)
 };
 
 int classify_and_upload(Arena &ar, const float *p, size_t n, const float **dev, cudaStream_t st)
@@ -466,9 +493,13 @@ int finish_stream(cudaStream_t st)
 // receives nt floats; no forward run, no reconstruction).  family > 0 (kind
 // 2): the gradient of parametrisation family 1 (Vp, rho) or 2 (Vp, Ip), of
 // the logarithms when logp, into img_out and img2_out.
+// kind 6: forward modelling with boundary saving that writes the seismograms
+// and keeps its state in *tape_out (one batch of all shots); kind 7: the
+// reverse pass of kind 3 (vector-Jacobian product) from tape_in, no forward
+// run.
 int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet *w, const smi_opts *o,
         const float *dobs, float *seis_out, float *img_out, double *misfit_out, float *img2_out = nullptr,
-        int family = 0, int logp = 0)
+        int family = 0, int logp = 0, TapeState *tape_out = nullptr, TapeState *tape_in = nullptr)
 {
     t_err.clear();
     memset(&t_stats, 0, sizeof t_stats);
@@ -479,18 +510,21 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
     int rc;
     {
         Arena ar(st);
-        rc = validate_and_setup(m, geo, w, o, ar, st, &launches, S);
+        if (kind == 7) S = tape_in->S;        // set-up kept by the tape
+        else rc = validate_and_setup(m, geo, w, o, ar, st, &launches, S);
         if (rc) {
             cudaStreamSynchronize(st);
             return rc;
         }
         const Grid &g = S.g;
         LaunchCtx lc{st, &launches};
+        const bool out_seis = kind == 0 || kind == 6;   // the call writes seismograms
         const size_t nseis = (size_t)S.nt * S.nrec_total;
         const size_t nimg = kind == 5 ? (size_t)S.nt : (size_t)g.nphys;   // floats of img_out
         S.rho_grad = kind == 2 && family > 0;
-        if (kind == 0 && !seis_out) return fail(SMI_ERR_ARG, "seis is null");
-        if (kind != 0 && !dobs) return fail(SMI_ERR_ARG, kind == 3 || kind == 5 ? "adj_src is null" : "dobs is null");
+        if (out_seis && !seis_out) return fail(SMI_ERR_ARG, "seis is null");
+        if (!out_seis && !dobs)
+            return fail(SMI_ERR_ARG, kind == 3 || kind == 5 || kind == 7 ? "adj_src is null" : "dobs is null");
         if ((rc = check_same_device(seis_out, "seis")) || (rc = check_same_device(dobs, "dobs")) ||
             (rc = check_same_device(img_out, "image / gradient")) || (rc = check_same_device(img2_out, "grad2")) ||
             (rc = check_same_device(misfit_out, "misfit")))
@@ -502,7 +536,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         double *d_misfit = ar.get<double>(1);
         if (!d_misfit) return fail(SMI_ERR_NOMEM, "device allocation failed");
         launch_zero(lc, d_misfit, sizeof(double));
-        if (kind == 0) {
+        if (out_seis) {
             d_seis_out = is_device_ptr(seis_out) ? seis_out : ar.get<float>(nseis);
         } else {
             rc = classify_and_upload(ar, dobs, nseis, &d_dobs, st);
@@ -529,6 +563,9 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         int B = (int)std::max<size_t>(1, (size_t)(0.8 * (double)free_b) / per);
         B = std::min(B, S.nshot);
         if (o->max_batch > 0) B = std::min(B, o->max_batch);
+        if (kind == 6 && B < S.nshot)
+            return fail(SMI_ERR_NOMEM, "a tape keeps every shot's state on the device: %d of %d shots fit", B, S.nshot);
+        if (kind == 7) B = S.nshot;
 
         Timer tm;
         tm.on = o->profile != 0;
@@ -557,6 +594,11 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 max_rec = std::max(max_rec, roff[s + 1] - roff[s]);
             }
             const long long batch_seis = (long long)S.nt * roff[nb_shot];
+            if (kind == 7) {
+                roff = tape_in->roff;
+                soff = tape_in->soff;
+                max_rec = tape_in->max_rec;
+            }
             Arena ba(st);
             int *d_roff = ba.get<int>(roff.size());
             long long *d_soff = ba.get<long long>(soff.size());
@@ -567,7 +609,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             Fields F{}, A{}, F2{}, A2{};
             auto mem_n = [&](int a) { return (size_t)(fused && a < 2 ? g.ntot : g.slab_n[a]) * nb_shot; };
             for (Fields *f : {&F, &F2}) {
-                if (f == &F2 && !fused) break;
+                if ((f == &F2 && !fused) || kind == 7) break;
                 f->p = ba.get<float>((size_t)g.ntot * nb_shot);
                 for (int a = 0; a < g.ndim; a++) {
                     f->v[a] = ba.get<float>((size_t)g.ntot * nb_shot);
@@ -575,14 +617,21 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     f->psiv[a] = ba.get<float>(mem_n(a));
                 }
             }
-            float *seis = (kind == 0) ? d_seis_out + (size_t)S.nt * S.rec_offset[s0]
-                                      : ba.get<float>(std::max<long long>(1, batch_seis));
+            float *seis = out_seis ? d_seis_out + (size_t)S.nt * S.rec_offset[s0]
+                                   : ba.get<float>(std::max<long long>(1, batch_seis));
             Bands bd = S.bands;
             float *res = nullptr, *acc = nullptr, *keep = nullptr;
             unsigned *norm_mx = nullptr;
             double *partials = nullptr, *part = nullptr;
             const int npart = 256;
-            if (kind != 0) {
+            if (kind == 7) {                                 // the state the forward call kept
+                const TapeState &T = *tape_in;
+                F = T.F; F2 = T.F2; A = T.A; A2 = T.A2;
+                bd = T.bd;
+                res = T.res;
+                acc = T.acc;
+                partials = T.partials;
+            } else if (kind != 0) {
                 for (int k = 0; k < (fused ? 2 : 1); k++) {   // the adjoint reuses the forward's memory variables
                     Fields &a_ = k ? A2 : A;
                     const Fields &f_ = k ? F2 : F;
@@ -609,8 +658,13 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             }
             if (!ba.ok) return fail(SMI_ERR_NOMEM, "device allocation for a batch of %d shots failed", nb_shot);
             batch_peak = std::max(batch_peak, ba.peak);
-            cudaMemcpyAsync(d_roff, roff.data(), sizeof(int) * roff.size(), cudaMemcpyHostToDevice, st);
-            cudaMemcpyAsync(d_soff, soff.data(), sizeof(long long) * soff.size(), cudaMemcpyHostToDevice, st);
+            if (kind == 7) {
+                d_roff = tape_in->d_roff;
+                d_soff = tape_in->d_soff;
+            } else {
+                cudaMemcpyAsync(d_roff, roff.data(), sizeof(int) * roff.size(), cudaMemcpyHostToDevice, st);
+                cudaMemcpyAsync(d_soff, soff.data(), sizeof(long long) * soff.size(), cudaMemcpyHostToDevice, st);
+            }
             Maps3 mF{}, mA{}, mF2{}, mA2{};
             if (fast3 && (!make_maps3(mF, g, F, nb_shot) || (kind != 0 && !make_maps3(mA, g, A, nb_shot))))
                 return fail(SMI_ERR_CUDA, "tensor map encoding failed");
@@ -659,7 +713,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 }
             };
             for (const Fields *f : {&F, &F2}) {
-                if (f == &F2 && !fused) break;
+                if ((f == &F2 && !fused) || kind == 7) break;
                 launch_zero(lc, f->p, sizeof(float) * g.ntot * nb_shot);
                 for (int a = 0; a < g.ndim; a++) {
                     launch_zero(lc, f->v[a], sizeof(float) * g.ntot * nb_shot);
@@ -673,7 +727,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             // the last stored sample (every time-interpolation window of the
             // reverse loop complete); the state after step nt-1 is kept.
             const size_t fbytes = sizeof(float) * g.ntot * nb_shot;
-            const int nsteps = kind == 5 ? 0 : kind != 0 ? S.nt_fwd : S.nt;
+            const int nsteps = kind == 5 || kind == 7 ? 0 : kind != 0 ? S.nt_fwd : S.nt;
             for (int it = 0; it < nsteps; it++) {
                 if (kind != 0 && it % S.dr == 0) launch_save_bands(lc, g, b, F, bd, it / S.dr, d_absmax);
                 tm.begin(0);
@@ -723,15 +777,32 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     cudaMemcpyAsync(F.v[a], keep + (size_t)(1 + a) * g.ntot * nb_shot, fbytes,
                                     cudaMemcpyDeviceToDevice, st);
             }
-            if (batch_seis > 0 && kind != 5) launch_nonfinite(lc, seis, batch_seis, d_flag);
+            if (batch_seis > 0 && kind != 5 && kind != 7) launch_nonfinite(lc, seis, batch_seis, d_flag);
             launch_nonfinite(lc, F.p, g.ntot * nb_shot, d_flag);
             if (kind == 0) continue;
+            if (kind == 6) {                       // keep the state for the reverse pass
+                TapeState &T = *tape_out;
+                T.F = F; T.F2 = F2; T.A = A; T.A2 = A2;
+                T.bd = bd;
+                T.res = res;
+                T.acc = acc;
+                T.partials = partials;
+                T.d_roff = d_roff;
+                T.d_soff = d_soff;
+                T.roff = roff;
+                T.soff = soff;
+                T.max_rec = max_rec;
+                T.batch_seis = batch_seis;
+                batch_peak = std::max(batch_peak, ba.peak);
+                ba.release_to(T.mem);
+                continue;
+            }
 
             // ---- residual, misfit ----
             if (batch_seis > 0) {
                 const float *dob = d_dobs + (size_t)S.nt * S.rec_offset[s0];
-                launch_residual(lc, kind == 5 ? dob : seis, dob, batch_seis, kind == 2 ? 0 : 1, res, partials,
-                                npart);
+                launch_residual(lc, kind == 5 || kind == 7 ? dob : seis, dob, batch_seis, kind == 2 ? 0 : 1, res,
+                                partials, npart);
                 if (kind == 2) launch_sum_partials(lc, partials, npart, d_misfit);
             }
             // ---- reverse loop ----
@@ -749,7 +820,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 for (int a = 0; a < g.ndim; a++)
                     cudaMemcpyAsync(R.vprev[a], F.v[a], fbytes, cudaMemcpyDeviceToDevice, st);
             // 0: gradient, 1: image, 2: image and source illumination
-            const int mode = (kind == 2 || kind == 3) ? 0 : (norm ? 2 : 1);
+            const int mode = (kind == 2 || kind == 3 || kind == 7) ? 0 : (norm ? 2 : 1);
             // one reverse step of the source field (reconstruction with the fused
             // imaging / gradient accumulation), then its boundary re-imposed
             auto reconstruct = [&](int it) {
@@ -845,16 +916,16 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             // batch buffers are released (stream-ordered) when `ba` goes out of scope
         }
         if (S.rho_grad) launch_finalize_family(lc, g, S.vp, S.rho, d_img, R, family, logp, d_img, d_img2);
-        else if (kind == 2 || kind == 3) launch_finalize_grad(lc, g.nphys, S.vp, g.dt, d_img);
+        else if (kind == 2 || kind == 3 || kind == 7) launch_finalize_grad(lc, g.nphys, S.vp, g.dt, d_img);
         else if (kind == 5) {
             launch_to_float(lc, d_series, S.nt, d_img);
             launch_nonfinite(lc, d_img, S.nt, d_flag);
         }
 
         // outputs back to the host where needed
-        if (kind == 0 && d_seis_out != seis_out)
+        if (out_seis && d_seis_out != seis_out)
             cudaMemcpyAsync(seis_out, d_seis_out, nseis * sizeof(float), cudaMemcpyDeviceToHost, st);
-        if (kind != 0 && img_out && d_img != img_out)
+        if (!out_seis && img_out && d_img != img_out)
             cudaMemcpyAsync(img_out, d_img, nimg * sizeof(float), cudaMemcpyDeviceToHost, st);
         if (d_img2 && d_img2 != img2_out)
             cudaMemcpyAsync(img2_out, d_img2, (size_t)g.nphys * sizeof(float), cudaMemcpyDeviceToHost, st);
@@ -872,6 +943,16 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         t_stats.kernel_launches = launches;
         t_stats.device_bytes = (double)(ar.peak + batch_peak);
         t_stats.band_values = kind == 0 || kind == 5 ? 0 : S.bands.count;
+        if (kind == 6) {
+            if (!rc) {
+                tape_out->S = S;
+                ar.release_to(tape_out->mem);      // the set-up tables stay with the tape
+            } else {
+                // the batch allocations were handed over: give them back to be freed
+                for (auto &pr : tape_out->mem) cudaFreeAsync(pr.first, st);
+                tape_out->mem.clear();
+            }
+        }
     }
     // the arena's frees are stream ordered; make them complete before return
     if (!rc) rc = finish_stream(st);
@@ -886,6 +967,10 @@ void record_error(const char *msg) { t_err = msg; }
 }  // namespace smi
 
 using namespace smi;
+
+struct smi_tape {
+    TapeState st;
+};
 
 extern "C" {
 
@@ -942,6 +1027,42 @@ int smi_forward_vjp(const smi_model *model, const smi_geometry *geom, const smi_
 {
     if (!grad_vp) return fail(SMI_ERR_ARG, "grad_vp is null");
     return run(3, model, geom, wav, opts, adj_src, nullptr, grad_vp, nullptr);
+}
+
+int smi_forward_tape(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                     const smi_opts *opts, float *seis, smi_tape **tape)
+{
+    if (!tape) return fail(SMI_ERR_ARG, "tape is null");
+    *tape = nullptr;
+    if (!opts) return fail(SMI_ERR_ARG, "null options");
+    auto *t = new smi_tape();
+    const int rc = run(6, model, geom, wav, opts, nullptr, seis, nullptr, nullptr, nullptr, 0, 0, &t->st, nullptr);
+    if (rc) {
+        delete t;
+        return rc;
+    }
+    t->st.o = *opts;
+    *tape = t;
+    return SMI_OK;
+}
+
+int smi_tape_vjp(smi_tape *tape, const float *adj_src, float *grad_vp, void *stream)
+{
+    if (!tape || !grad_vp) return fail(SMI_ERR_ARG, "null argument");
+    if (tape->st.done) return fail(SMI_ERR_ARG, "this tape's reverse pass has already run (a tape serves one)");
+    smi_opts o = tape->st.o;
+    o.stream = stream;
+    const int rc = run(7, nullptr, nullptr, nullptr, &o, adj_src, nullptr, grad_vp, nullptr, nullptr, 0, 0, nullptr,
+                       &tape->st);
+    tape->st.done = true;                  // the reverse pass consumed the kept source field
+    return rc;
+}
+
+void smi_tape_free(smi_tape *tape)
+{
+    if (!tape) return;
+    for (auto &pr : tape->st.mem) cudaFree(pr.first);
+    delete tape;
 }
 
 int smi_forward_adjoint(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,

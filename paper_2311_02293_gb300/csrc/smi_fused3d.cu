@@ -54,6 +54,9 @@
 #ifndef SMI_FMINB
 #define SMI_FMINB 3          // resident CTAs per SM the register budget must allow
 #endif
+#ifndef SMI_FUNROLL
+#define SMI_FUNROLL 1        // y planes per unrolled group (the body is large: keep it in the instruction cache)
+#endif
 
 namespace smi {
 namespace s3 {
@@ -135,7 +138,7 @@ struct FCtx {
 // values (out-of-box nodes keep their old values) and, in the adjoint, the
 // pressure-part operand R_z = lv + Av (lv + chi); own quads write v (and the
 // memory variable) to nxt.
-template <int N, int MODE>
+template <int N, int MODE, bool BAND>
 __device__ __forceinline__ void vz_quad(const Grid &g, const FCtx &c, const FTabs &tb, const float *slot, int z,
                                         int x, int y, bool own, const Fields &cur, const Fields &nxt, float (&out)[4])
 {
@@ -152,8 +155,8 @@ __device__ __forceinline__ void vz_quad(const Grid &g, const FCtx &c, const FTab
     }
     const bool inxy = in_range(x, c.lo[1], c.hi[1]) && in_range(y, c.lo[2], c.hi[2]);
     const long long o = c.sh + foff(g, z, x, y);
-    const bool sq = c.zb && zquad_slab(g, z);      // the quad itself has slab nodes
-    if (MODE == ADJ && c.zb && (z - 4 < g.nb || z + 7 >= g.ne[0] - g.nb - 1)) {
+    const bool sq = BAND && c.zb && zquad_slab(g, z);      // the quad itself has slab nodes
+    if (MODE == ADJ && BAND && c.zb && (z - 4 < g.nb || z + 7 >= g.ne[0] - g.nb - 1)) {
         // transposed CPML operand over the window: lp + Ap (lp + phi) at slab nodes
         float ph[12];
         const float *pp = cur.psiv[0] + c.sh + foff(g, z - 4, x, y);
@@ -216,7 +219,7 @@ __device__ __forceinline__ void vz_quad(const Grid &g, const FCtx &c, const FTab
 }
 
 // v_x on the quad z..z+3 at column x (x0-N <= x <= x0+TX+N-2) of plane y.
-template <int N, int MODE>
+template <int N, int MODE, bool BAND>
 __device__ __forceinline__ void vx_quad(const Grid &g, const FCtx &c, const FTabs &tb, const float *slot, int z,
                                         int x, int y, bool own, const Fields &cur, const Fields &nxt, float (&out)[4])
 {
@@ -226,7 +229,7 @@ __device__ __forceinline__ void vx_quad(const Grid &g, const FCtx &c, const FTab
 #pragma unroll
     for (int t = 0; t < 2 * N; t++) put(Xr[t], lds4(slot + Lay::PB + (x - c.x0 + N + t) * 32 + zc));
     const bool iny = in_range(y, c.lo[2], c.hi[2]);
-    if (MODE == ADJ && c.xb) {
+    if (MODE == ADJ && BAND && c.xb) {
         // transposed CPML operand at the taps in the x slab
         const bool oky = in_range(y, 0, g.ne[2] - 1) && z < g.px;
 #pragma unroll
@@ -257,7 +260,7 @@ __device__ __forceinline__ void vx_quad(const Grid &g, const FCtx &c, const FTab
     bool m[4];
 #pragma unroll
     for (int r = 0; r < 4; r++) m[r] = mx && in_range(z + r, c.lo[0], c.hi[0]);
-    const bool sx = c.xb && in_range(x, 0, g.ne[1] - 1) && slab_at(g, 1, x);
+    const bool sx = BAND && c.xb && in_range(x, 0, g.ne[1] - 1) && slab_at(g, 1, x);
     const long long o = c.sh + foff(g, z, x, y);
     float mem[4] = {0.f, 0.f, 0.f, 0.f};
     const bool okq = sx && in_range(y, 0, g.ne[2] - 1) && z < g.px;
@@ -339,7 +342,7 @@ __device__ __forceinline__ void vy_update(const Grid &g, const FCtx &c, int oz, 
 
 // p on the own quad at plane y from the three derivatives of v (adjoint:
 // of the R operands), with the CPML terms of the three axes.
-template <int MODE>
+template <int MODE, bool BAND>
 __device__ __forceinline__ void p_update(const Grid &g, const FCtx &c, const FTabs &tb, int oz, int ox, int y,
                                          bool memq, float (&dz)[4], float (&dx)[4], float (&dy)[4],
                                          const float (&pold)[4], const float (&K)[4], const Fields &cur,
@@ -351,7 +354,7 @@ __device__ __forceinline__ void p_update(const Grid &g, const FCtx &c, const FTa
 #pragma unroll
     for (int r = 0; r < 4; r++) m[r] = in_range(oz + r, c.lo[0], c.hi[0]);
     const long long o = c.sh + foff(g, oz, ox, y);
-    if (c.zb && zquad_slab(g, oz)) {             // z memory variable at the quad's slab nodes
+    if (BAND && c.zb && zquad_slab(g, oz)) {     // z memory variable at the quad's slab nodes
         float mem[4];
         ld4(mem, cur.psiv[0] + o);
 #pragma unroll
@@ -367,7 +370,7 @@ __device__ __forceinline__ void p_update(const Grid &g, const FCtx &c, const FTa
         }
         st4(nxt.psiv[0] + o, mem);
     }
-    if (c.xb && slab_at(g, 1, ox)) {
+    if (BAND && c.xb && slab_at(g, 1, ox)) {
         float mem[4];
         ld4(mem, cur.psiv[1] + o);
         const int t = ox - c.x0 + 8;
@@ -406,11 +409,130 @@ __device__ __forceinline__ void p_update(const Grid &g, const FCtx &c, const FTa
     st4(nxt.p + o, np);
 }
 
+// ---------------------------------------------------------------------------
+// Work of one launch: the tile columns of one class (interior: no stencil of
+// the tile reaches a z or x slab; band: the others) times y-chunks of the
+// box.  A column is a band column when its z window [z0-8, z0+39] or x
+// window [x0-8, x0+TX+7] meets a slab; interior z tiles (and x tiles) form
+// one contiguous range, so the interior columns are a rectangle.
+__device__ __forceinline__ bool band_z(const Grid &g, int z0) { return z0 - 8 < g.nb || z0 + 39 >= g.ne[0] - g.nb - 1; }
+__device__ __forceinline__ bool band_x(const Grid &g, int x0)
+{
+    return x0 - 8 < g.nb || x0 + TX + 7 >= g.ne[1] - g.nb - 1;
+}
+
+struct CDecomp {
+    int zbase, nzt, nxt, iz0, iz1, ix0, ix1, ncol, nyc, cy;
+};
+
+__device__ __forceinline__ CDecomp cdecomp(const Grid &g, const int lo[3], const int hi[3], int grid, bool band)
+{
+    CDecomp d;
+    d.zbase = lo[0] & ~31;
+    const int ylen = hi[2] - lo[2] + 1;
+    d.nzt = hi[0] >= lo[0] ? (hi[0] - d.zbase) / TZ + 1 : 0;
+    d.nxt = hi[1] >= lo[1] ? (hi[1] - lo[1]) / TX + 1 : 0;
+    d.iz0 = d.iz1 = d.ix0 = d.ix1 = 0;
+    d.ncol = 0;
+    d.nyc = 0;
+    d.cy = 1;
+    if (d.nzt == 0 || d.nxt == 0 || ylen <= 0) return d;
+    d.iz0 = d.nzt;
+    for (int i = 0; i < d.nzt; i++)
+        if (!band_z(g, d.zbase + TZ * i)) {
+            if (d.iz0 == d.nzt) d.iz0 = i;
+            d.iz1 = i + 1;
+        }
+    if (d.iz0 == d.nzt) d.iz0 = d.iz1 = 0;
+    d.ix0 = d.nxt;
+    for (int i = 0; i < d.nxt; i++)
+        if (!band_x(g, lo[1] + TX * i)) {
+            if (d.ix0 == d.nxt) d.ix0 = i;
+            d.ix1 = i + 1;
+        }
+    if (d.ix0 == d.nxt) d.ix0 = d.ix1 = 0;
+    const int nint = (d.iz1 - d.iz0) * (d.ix1 - d.ix0);
+    d.ncol = band ? d.nzt * d.nxt - nint : nint;
+    if (d.ncol == 0) return d;
+    // chunks along y: as many as fill the persistent grid's waves to 90 %
+    const long long cols = d.ncol;
+    const int cmax = max(1, ylen / 16);
+    auto fill = [&](int c) {
+        const long long items = cols * c;
+        return (float)items / (float)(((items + grid - 1) / grid) * grid);
+    };
+    int chunks = max(1, min(cmax, (int)(grid / cols)));
+    if (fill(chunks) < 0.9f) {
+        for (int c = chunks + 1; c <= min(cmax, 4 * chunks + 4); c++) {
+            if (fill(c) >= 0.9f) {
+                chunks = c;
+                break;
+            }
+        }
+    }
+    d.cy = (ylen + chunks - 1) / chunks;
+    d.nyc = (ylen + d.cy - 1) / d.cy;
+    return d;
+}
+
+// Column k (0 .. ncol-1) of the class -> tile indices (zi, xi).
+__device__ __forceinline__ void class_column(const CDecomp &d, bool band, int k, int &zi, int &xi)
+{
+    const int nix = d.ix1 - d.ix0;
+    if (!band) {
+        zi = d.iz0 + k / nix;
+        xi = d.ix0 + k % nix;
+        return;
+    }
+    for (zi = 0; zi < d.nzt; zi++) {
+        const bool zint = zi >= d.iz0 && zi < d.iz1;
+        const int cnt = zint ? d.nxt - nix : d.nxt;
+        if (k < cnt) {
+            xi = (zint && k >= d.ix0) ? k - d.ix0 + d.ix1 : k;
+            return;
+        }
+        k -= cnt;
+    }
+    xi = 0;
+}
+
+// Item w of a class's launch (shots in order), false past the end.
+__device__ __forceinline__ bool get_citem(const Grid &g, const Batch &b, int mode, int step, bool band, long long w,
+                                          Item &it)
+{
+    const int target = (int)gridDim.x;
+    for (int s = 0; s < b.nshot; s++) {
+        int lo[3], hi[3], plo[3] = {0, 0, 0}, phi[3] = {-1, -1, -1};
+        item_box(g, b, mode, s, step, lo, hi, plo, phi);
+        const CDecomp d = cdecomp(g, lo, hi, target, band);
+        const long long n = (long long)d.ncol * d.nyc;
+        if (w < n) {
+            const int k = (int)(w % d.ncol), ci = (int)(w / d.ncol);
+            int zi, xi;
+            class_column(d, band, k, zi, xi);
+            it.s = s;
+            it.z0 = d.zbase + TZ * zi;
+            it.x0 = lo[1] + TX * xi;
+            it.ya = lo[2] + ci * d.cy;
+            it.yb = min(hi[2], it.ya + d.cy - 1);
+            for (int a = 0; a < 3; a++) {
+                it.lo[a] = lo[a];
+                it.hi[a] = hi[a];
+                it.plo[a] = plo[a];
+                it.phi[a] = phi[a];
+            }
+            return true;
+        }
+        w -= n;
+    }
+    return false;
+}
+
 // ===========================================================================
 // The fused step.  MODE FWD: the forward scheme with the forward CPML (box
 // of the source); MODE ADJ: the adjoint in lambda form with the transposed
 // CPML (box of the receivers after `step` reverse steps).
-template <int N, int MODE>
+template <int N, int MODE, bool BAND>
 __global__ void __launch_bounds__(NTHR, SMI_FMINB)
 k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUtensorMap tm_pB,
          const __grid_constant__ CUtensorMap tm_vzA, const __grid_constant__ CUtensorMap tm_vxB,
@@ -435,7 +557,7 @@ k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUte
     unsigned parity = 0;
 
     Item it;
-    for (long long w = blockIdx.x; get_item(g, b, MODE, step, w, it); w += gridDim.x) {
+    for (long long w = blockIdx.x; get_citem(g, b, MODE, step, BAND, w, it); w += gridDim.x) {
         FCtx c;
         c.s = it.s;
         c.z0 = it.z0;
@@ -445,15 +567,15 @@ k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUte
             c.hi[a] = it.hi[a];
         }
         c.sh = (long long)it.s * g.ntot;
-        c.zb = c.z0 - 8 < g.nb || c.z0 + 39 >= g.ne[0] - g.nb - 1;
-        c.xb = c.x0 - 8 < g.nb || c.x0 + TX + 7 >= g.ne[1] - g.nb - 1;
+        c.zb = BAND && band_z(g, c.z0);
+        c.xb = BAND && band_x(g, c.x0);
         const int ya = it.ya, yb = it.yb;
         const int oz = c.z0 + 4 * tzi, ox = c.x0 + txi;
         const bool memq = oz < g.ne[0] && ox < g.ne[1];
         const int own = txi * TZ + 4 * tzi;        // own quad in the core tiles
 
         // CPML coefficient tables of a band tile (published by the barrier below)
-        if (c.zb || c.xb) {
+        if (BAND) {
             for (int i = tid; i < 4 * 48; i += NTHR) {
                 const int k = i / 48, j = i % 48, zz = c.z0 - 8 + j;
                 const float *src = k == 0 ? g.cpa[0] : k == 1 ? g.cpb[0] : k == 2 ? g.cva[0] : g.cvb[0];
@@ -564,20 +686,20 @@ k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUte
             }
             float t4[4];
             // ---- v_z at plane y: own quad, then the z halo (warp 3) ----
-            vz_quad<N, MODE>(g, c, tb, slot, oz, ox, y, true, cur, nxt, t4);
+            vz_quad<N, MODE, BAND>(g, c, tb, slot, oz, ox, y, true, cur, nxt, t4);
             sts4(vzn + txi * 40 + 4 * tzi + 4, t4);
             if (tid >= NTHR - 32) {
                 const int t = tid - (NTHR - 32), hx = t & (TX - 1), hz = (t >= TX) ? c.z0 + TZ : c.z0 - 4;
-                vz_quad<N, MODE>(g, c, tb, slot, hz, c.x0 + hx, y, false, cur, nxt, t4);
+                vz_quad<N, MODE, BAND>(g, c, tb, slot, hz, c.x0 + hx, y, false, cur, nxt, t4);
                 sts4(vzn + hx * 40 + (hz - c.z0 + 4), t4);
             }
             // ---- v_x at plane y: own quad, then the x halo (warps 0, 1) ----
-            vx_quad<N, MODE>(g, c, tb, slot, oz, ox, y, true, cur, nxt, t4);
+            vx_quad<N, MODE, BAND>(g, c, tb, slot, oz, ox, y, true, cur, nxt, t4);
             sts4(vxn + (txi + N) * 32 + 4 * tzi, t4);
             if (tid < 8 * (2 * N - 1)) {
                 const int zq = tid & 7, col = tid >> 3;
                 const int hx = col < N ? c.x0 - N + col : c.x0 + TX + col - N;
-                vx_quad<N, MODE>(g, c, tb, slot, c.z0 + 4 * zq, hx, y, false, cur, nxt, t4);
+                vx_quad<N, MODE, BAND>(g, c, tb, slot, c.z0 + 4 * zq, hx, y, false, cur, nxt, t4);
                 sts4(vxn + (hx - c.x0 + N) * 32 + 4 * zq, t4);
             }
             // ---- v_y at plane y+N-1 (own quad) ----
@@ -646,7 +768,7 @@ k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUte
                 }
                 put(K, lds4(slot + Lay::KC + own));
                 put(p0, lds4(slot + Lay::P0 + own));
-                p_update<MODE>(g, c, tb, oz, ox, y, memq, dz, dx, dy, p0, K, cur, nxt);
+                p_update<MODE, BAND>(g, c, tb, oz, ox, y, memq, dz, dx, dy, p0, K, cur, nxt);
             }
             // all reads of plane y's slot and of the new v tiles are done
             if (__syncthreads_or(!ok)) {
@@ -656,7 +778,7 @@ k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUte
             if (tid == 0 && rr.issued < yb) issue(rr.issued + 1);
             if (rr.issued < yb) rr.issued++;
         };
-        constexpr int G = Q % SMI_YUNROLL == 0 ? SMI_YUNROLL : Q;
+        constexpr int G = Q % SMI_FUNROLL == 0 ? SMI_FUNROLL : Q;
         while (y <= yb && !stop) {
             Unroll<0, G>::run(body, y, yb, stop);
             rotate_queue<G>(pq);
@@ -678,23 +800,33 @@ k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUte
 // Host side.
 namespace {
 
-template <int N, int MODE>
-void run_fused(const LaunchCtx &lc, const MapsF &mc, const MapsM &mm, const Grid &g, const Batch &b, Fields cur,
+template <int N, int MODE, bool BAND>
+void run_class(const LaunchCtx &lc, const MapsF &mc, const MapsM &mm, const Grid &g, const Batch &b, Fields cur,
                Fields nxt, int step, unsigned *err)
 {
     constexpr int smem = s3::FLay<N>::SMEM;
     static const int grid = [] {
-        cudaFuncSetAttribute(s3::k3_fused<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(s3::k3_fused<N, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(s3::k3_fused<N, MODE, BAND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(s3::k3_fused<N, MODE, BAND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         int per = 0, dev = 0, sms = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, s3::k3_fused<N, MODE>, s3::NTHR, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, s3::k3_fused<N, MODE, BAND>, s3::NTHR, smem);
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         return std::max(1, per) * std::max(1, sms);
     }();
-    s3::k3_fused<N, MODE><<<grid, s3::NTHR, smem, static_cast<cudaStream_t>(lc.stream)>>>(
+    s3::k3_fused<N, MODE, BAND><<<grid, s3::NTHR, smem, static_cast<cudaStream_t>(lc.stream)>>>(
         mc.pA, mc.pB, mc.vzA, mc.vxB, mc.vy, mc.pc, mm.rA, mm.rB, mm.rc, mm.Kc, g, b, cur, nxt, step, err);
     ++*lc.launches;
+}
+
+// The two classes write disjoint nodes and read only `cur`: no ordering
+// between them is needed.
+template <int N, int MODE>
+void run_fused(const LaunchCtx &lc, const MapsF &mc, const MapsM &mm, const Grid &g, const Batch &b, Fields cur,
+               Fields nxt, int step, unsigned *err)
+{
+    run_class<N, MODE, true>(lc, mc, mm, g, b, cur, nxt, step, err);
+    run_class<N, MODE, false>(lc, mc, mm, g, b, cur, nxt, step, err);
 }
 
 }  // namespace

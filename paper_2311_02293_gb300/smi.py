@@ -82,7 +82,7 @@ EXPORTS = ["smi_opts_default", "smi_forward", "smi_rtm", "smi_fwi_gradient", "sm
            "smi_box_table", "smi_last_stats", "smi_last_error", "smi_version", "smi_forward_noalloc",
            "smi_forward_vjp", "smi_server_create", "smi_submit", "smi_wait", "smi_poll", "smi_cancel",
            "smi_server_info", "smi_server_destroy", "smi_fwi_gradient_family", "smi_wait_check",
-           "smi_forward_adjoint", "smi_dot"]
+           "smi_forward_adjoint", "smi_dot", "smi_forward_tape", "smi_tape_vjp", "smi_tape_free"]
 KERNELS = {"auto": 0, "generic": 1, "twopass": 2}
 
 
@@ -103,6 +103,10 @@ def _load():
     L.smi_wait_check.argtypes = [vp, ctypes.c_longlong, P(ctypes.c_double)]
     L.smi_forward_vjp.argtypes = common + [vp, vp]
     L.smi_forward_adjoint.argtypes = common + [vp, vp]
+    L.smi_forward_tape.argtypes = common + [vp, P(ctypes.c_void_p)]
+    L.smi_tape_vjp.argtypes = [vp, vp, vp, vp]
+    L.smi_tape_free.argtypes = [vp]
+    L.smi_tape_free.restype = None
     L.smi_dot.argtypes = [vp, vp, ctypes.c_size_t, P(ctypes.c_double), vp]
     L.smi_query.argtypes = common + [c_int, P(ctypes.c_size_t), P(ctypes.c_size_t), P(ctypes.c_size_t)]
     L.smi_box_table.argtypes = common + [c_int, c_int, c_int, c_int, vp, vp]
@@ -111,7 +115,7 @@ def _load():
     L.smi_version.restype = ctypes.c_char_p
     for name in ("smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query", "smi_box_table",
                  "smi_last_stats", "smi_forward_noalloc", "smi_forward_vjp", "smi_fwi_gradient_family",
-                 "smi_wait_check", "smi_forward_adjoint", "smi_dot"):
+                 "smi_wait_check", "smi_forward_adjoint", "smi_dot", "smi_forward_tape", "smi_tape_vjp"):
         getattr(L, name).restype = c_int
     return L
 
@@ -373,6 +377,60 @@ def smi_forward_vjp(vp, rho, prob: Problem, srcs, recs, stf, adj_src, stream=Non
     g, pg = _out(out, int(np.prod(shape)), cuda, vp.device if cuda else None)
     _check(_lib.smi_forward_vjp(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w), ctypes.byref(o), pd, pg))
     return g.reshape(shape)
+
+
+class Tape:
+    """The device checkpoint of one smi_forward_tape call (saved boundaries,
+    final state, set-up tables), owned by this object; it keeps the model and
+    wavelet tensors the call read alive until it is freed."""
+
+    def __init__(self, ptr, keep, shape, device):
+        self._p = ptr
+        self._keep = keep
+        self.shape = shape
+        self.device = device
+
+    def vjp(self, adj_src, stream=None, out=None):
+        """dL/dVp for dL/dseis = adj_src (seismogram layout); one call per tape."""
+        if not self._p:
+            raise ValueError("the tape was freed")
+        cuda = self.device is not None
+        kd, pd, _ = _dobs_flat(adj_src, cuda, None)
+        g, pg = _out(out, int(np.prod(self.shape)), cuda, self.device)
+        ctx = torch.cuda.device(self.device) if cuda else __import__("contextlib").nullcontext()
+        with ctx:
+            st = stream if stream is not None else (
+                torch.cuda.current_stream().cuda_stream if cuda else None)
+            _check(_lib.smi_tape_vjp(self._p, pd, pg, st))
+        return g.reshape(self.shape)
+
+    def free(self):
+        if self._p:
+            _lib.smi_tape_free(self._p)
+            self._p = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # pragma: no cover - interpreter shutdown
+            pass
+
+
+@_on_model_device
+def smi_forward_tape(vp, rho, prob: Problem, srcs, recs, stf, stream=None):
+    """(flat seismograms, Tape): smi_forward that keeps its checkpoint for one
+    later reverse pass (Tape.vjp)."""
+    m, keep_m, cuda, shape = _model(vp, rho, prob.d)
+    geo, keep_g, off = _geometry(srcs, recs)
+    ks, ps, _ = _as_f32(stf)
+    w = smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
+    o = _opts(prob, stream)
+    out, pout = _out(None, int(prob.nt * off[-1]), cuda, vp.device if cuda else None)
+    t = ctypes.c_void_p()
+    _check(_lib.smi_forward_tape(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w), ctypes.byref(o), pout,
+                                 ctypes.byref(t)))
+    return out, Tape(t.value, (keep_m, ks), shape, vp.device if cuda else None)
 
 
 @_on_model_device

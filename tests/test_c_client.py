@@ -29,7 +29,8 @@ int main(void)
                 (fn)smi_forward_vjp, (fn)smi_query, (fn)smi_box_table, (fn)smi_forward_noalloc,
                 (fn)smi_wait_check, (fn)smi_last_stats, (fn)smi_last_error, (fn)smi_server_create,
                 (fn)smi_submit, (fn)smi_wait, (fn)smi_poll, (fn)smi_cancel, (fn)smi_server_info,
-                (fn)smi_server_destroy, (fn)smi_forward_adjoint, (fn)smi_dot};
+                (fn)smi_server_destroy, (fn)smi_forward_adjoint, (fn)smi_dot, (fn)smi_forward_tape, (fn)smi_tape_vjp,
+                (fn)smi_tape_free};
     for (size_t k = 0; k < sizeof fns / sizeof fns[0]; k++)
         if (!fns[k]) return 12;
     /* argument errors come back as codes with a message, before device work */
