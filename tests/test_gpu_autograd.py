@@ -109,3 +109,45 @@ def test_autograd_gradient_descent_reduces_misfit(mods):
             step = 20.0 / vp.grad.abs().max()          # at most 20 m/s per cell
             vp -= step * vp.grad
     assert history[-1] < history[0]
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_tape_reverse_pass_runs_no_forward_modelling(mods, case):
+    """smi_forward_tape keeps the saved boundaries and the final state; the
+    reverse pass from the tape takes no forward step (the call's stats count
+    adjoint and reconstruction steps only) and equals smi_forward_vjp, which
+    models the forward again; a tape serves one reverse pass."""
+    import torch
+    smi, _ = mods
+    w = CASES[case]()
+    gp, _ = _probs(smi, w)
+    vp, rho, stf = _dev(w.vp), _dev(w.rho), _dev(w.stf)
+    rng = np.random.default_rng(13)
+    g = _dev(rng.standard_normal(w.nt * len(w.recs[0])).astype(np.float32))
+    seis, tape = smi.smi_forward_tape(vp, rho, gp, w.srcs, w.recs, stf)
+    ref_seis = smi.smi_forward(vp, rho, gp, w.srcs, w.recs, stf, flat=True)
+    assert torch.equal(seis, ref_seis)
+    gv = tape.vjp(g)
+    st = smi.smi_last_stats()
+    assert st["steps"][0] == 0 and st["steps"][1] == w.nt and st["steps"][2] == w.nt
+    ref = smi.smi_forward_vjp(vp, rho, gp, w.srcs, w.recs, stf, g)
+    assert float(torch.linalg.norm(gv - ref) / torch.linalg.norm(ref)) <= 1e-6
+    with pytest.raises(smi.SmiError):
+        tape.vjp(g)
+    tape.free()
+
+
+def test_autograd_backward_uses_the_tape(mods):
+    """The autograd Function's gradient (tape reverse pass) equals the
+    gradient of smi_fwi_gradient for the same misfit."""
+    import torch
+    smi, ag = mods
+    w = CASES["3d"]()
+    gp, op = _probs(smi, w)
+    dobs = (0.7 * O.forward(op, w.vp, w.rho, w.stf, w.srcs[0], w.recs[0])).astype(np.float32)
+    vp = _dev(w.vp).requires_grad_(True)
+    J = ag.misfit(vp, _dev(w.rho), gp, w.srcs, w.recs, _dev(w.stf), _dev(dobs).reshape(-1))
+    J.backward()
+    Jr, gr = smi.smi_fwi_gradient(vp.detach(), _dev(w.rho), gp, w.srcs, w.recs, _dev(w.stf), _dev(dobs))
+    assert abs(float(J.item()) - float(Jr.item())) <= 1e-6 * abs(float(Jr.item()))
+    assert float(torch.linalg.norm(vp.grad - gr) / torch.linalg.norm(gr)) <= 1e-5
