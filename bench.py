@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-scale", type=float, default=0.5,
                     help="grid sizes and nt of the serving mix relative to the full mix")
+    ap.add_argument("--serve-slots", type=int, default=4, help="concurrent request slots of the server")
     ap.add_argument("--profile", choices=["fwd", "rtm", "family", "grad2d"],
                     help="profiling case instead: one untimed forward call (observed data), then one forward "
                          "or RTM call of a one-shot salt model, printing per-class times")
@@ -526,20 +527,24 @@ def run_serve(args):
     serve._prepare(reqs, dev)
     serve._prepare(plain, dev)
     serve.run_alone(plain[:4], dev)                        # warm-up
+    clocks = Clocks(dev.index)
+    clocks.start()
     _, t_alone = serve.run_alone(plain, dev)
     rate1 = len(plain) / t_alone
     out = {}
     for name, factor in (("rate_1.2x", 1.2), ("rate_0.5x", 0.5)):
-        m = serve.run_mix(reqs, dev, slots=4, rate=factor * rate1)
+        m = serve.run_mix(reqs, dev, slots=args.serve_slots, rate=factor * rate1)
         out[name] = {"requests_per_s": m["requests_per_s"], "gradient_shots_per_s": m["gradient_shots_per_s"],
                      "p50_s": m["p50_s"], "p99_s": m["p99_s"], "failed": m["failed"], "seconds": m["seconds"]}
+    clk = clocks.stop()
     ngrad = sum(1 for r in plain if r.kind == "gradient")
     kinds = {k: sum(1 for r in reqs if r.kind == k) for k in ("gradient", "forward", "rtm")}
     line = {"metric": "served gradient shots/s (request server, FP16 boundaries)",
             "value": out["rate_1.2x"]["gradient_shots_per_s"], "unit": "gradient shots/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"serving_mix_{len(reqs)}req_scale{args.serve_scale}", "kinds": kinds,
-                       "slots": 4, "arrivals": "poisson"},
+                       "slots": args.serve_slots, "arrivals": "poisson", "boundaries": "f16 served, f32 one at a time"},
+            "clocks": clk,
             "one_at_a_time_fp32": {"requests_per_s": rate1, "gradient_shots_per_s": ngrad / t_alone,
                                    "seconds": t_alone},
             "served": out}

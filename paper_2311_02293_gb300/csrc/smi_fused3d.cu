@@ -65,7 +65,10 @@ constexpr int FD1 = SMI_FD1;
 constexpr int FCORE = TZ * TX;
 
 // Shared-memory slot of one p-plane y (floats; every piece a multiple of 32).
-template <int N> struct FLay {
+// Band tiles add the CPML memory variables of plane y: the p-grid ones (z:
+// psiv[0], x: psiv[1]) in the geometry of the p tiles and the v-grid ones (z:
+// psip[0], x: psip[1]) in that of the old v_z / v_x tiles.
+template <int N, bool BAND = false> struct FLay {
     static constexpr int PB_X = TX + 4 * N - 2;   // p rows x0-2N+1 .. x0+TX+2N-2 (for D_x at the v_x halo)
     static constexpr int VX_X = TX + 2 * N - 1;   // v_x rows x0-N .. x0+TX+N-2
     static constexpr int RB_X = TX + 2 * N;       // rho rows x0-N .. x0+TX+N-1
@@ -80,12 +83,19 @@ template <int N> struct FLay {
     static constexpr int VY = P0 + FCORE;         // v_y old, plane y+N-1
     static constexpr int RY = VY + FCORE;         // rho, plane y+N
     static constexpr int PQ = RY + FCORE;         // p old, plane y+2N-1 (enters the queue)
-    static constexpr int SLOT = PQ + FCORE;
-    static constexpr unsigned BYTES = (unsigned)SLOT * 4u;
+    static constexpr int ZA = PQ + FCORE;         // band: z memory variable on the p grid, PA geometry
+    static constexpr int XB = ZA + 48 * TX;       // band: x memory variable on the p grid, PB geometry
+    static constexpr int ZV = XB + 32 * PB_X;     // band: z memory variable on the v grid, VZ geometry
+    static constexpr int XV = ZV + 40 * TX;       // band: x memory variable on the v grid, VX geometry
+    static constexpr int SLOT = BAND ? XV + 32 * VX_X : ZA;
+    static constexpr unsigned BYTES = (unsigned)ZA * 4u;            // fields and model (every tile)
+    static constexpr unsigned ZBYTES = (unsigned)(48 * TX + 40 * TX) * 4u;      // z memory variables
+    static constexpr unsigned XBYTES = (unsigned)(32 * PB_X + 32 * VX_X) * 4u;  // x memory variables
     static constexpr int VZN = 40 * TX;           // new v_z (adjoint: R_z), z0-4 .. z0+35
     static constexpr int VXN = 32 * VX_X;         // new v_x (adjoint: R_x), VX_X rows
     static constexpr int SMEM = (FD1 * SLOT + VZN + VXN) * 4;
-    static_assert(PB % 32 == 0 && VZ % 32 == 0 && VX % 32 == 0 && RA % 32 == 0 && RB % 32 == 0 && KC % 32 == 0,
+    static_assert(PB % 32 == 0 && VZ % 32 == 0 && VX % 32 == 0 && RA % 32 == 0 && RB % 32 == 0 && KC % 32 == 0 &&
+                      ZA % 32 == 0 && XB % 32 == 0 && ZV % 32 == 0 && XV % 32 == 0 && SLOT % 32 == 0,
                   "slot pieces must stay 128-byte aligned for TMA");
 };
 
@@ -140,36 +150,25 @@ struct FCtx {
 // memory variable) to nxt.
 template <int N, int MODE, bool BAND>
 __device__ __forceinline__ void vz_quad(const Grid &g, const FCtx &c, const FTabs &tb, const float *slot, int z,
-                                        int x, int y, bool own, const Fields &cur, const Fields &nxt, float (&out)[4])
+                                        int cx, const bool (&m)[4], bool wr, long long o, const Fields &nxt,
+                                        float (&out)[4])
 {
-    using Lay = FLay<N>;
-    const int cx = x - c.x0;                       // 0 .. TX-1
+    using Lay = FLay<N, BAND>;
     const int zi = z - c.z0 + 4;                   // index in the 40/44-row layouts
     float W[12];
     {
-        const float *row = slot + Lay::PA + cx * 48 + (z - c.z0 + 4);
+        const float *row = slot + Lay::PA + cx * 48 + zi;
         float4 a0 = lds4(row), a1 = lds4(row + 4), a2 = lds4(row + 8);
         W[0] = a0.x; W[1] = a0.y; W[2] = a0.z; W[3] = a0.w;
         W[4] = a1.x; W[5] = a1.y; W[6] = a1.z; W[7] = a1.w;
         W[8] = a2.x; W[9] = a2.y; W[10] = a2.z; W[11] = a2.w;
     }
-    const bool inxy = in_range(x, c.lo[1], c.hi[1]) && in_range(y, c.lo[2], c.hi[2]);
-    const long long o = c.sh + foff(g, z, x, y);
     const bool sq = BAND && c.zb && zquad_slab(g, z);      // the quad itself has slab nodes
     if (MODE == ADJ && BAND && c.zb && (z - 4 < g.nb || z + 7 >= g.ne[0] - g.nb - 1)) {
         // transposed CPML operand over the window: lp + Ap (lp + phi) at slab nodes
-        float ph[12];
-        const float *pp = cur.psiv[0] + c.sh + foff(g, z - 4, x, y);
-        const bool okxy = in_range(x, 0, g.ne[1] - 1) && in_range(y, 0, g.ne[2] - 1);
+        const float *ph = slot + Lay::ZA + cx * 48 + zi;
 #pragma unroll
-        for (int q = 0; q < 3; q++) {
-            // z - 4 + 4q is a multiple of 4 and px of 8: each piece lies wholly inside or outside the row
-            const bool okz = okxy && z - 4 + 4 * q >= 0 && z + 4 * q <= g.px;
-            float4 v = okz ? *reinterpret_cast<const float4 *>(pp + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
-            ph[4 * q] = v.x; ph[4 * q + 1] = v.y; ph[4 * q + 2] = v.z; ph[4 * q + 3] = v.w;
-        }
-#pragma unroll
-        for (int i = 0; i < 12; i++) W[i] += tb.z[0][z - c.z0 + 4 + i] * (W[i] + ph[i]);
+        for (int i = 0; i < 12; i++) W[i] += tb.z[0][zi + i] * (W[i] + ph[i]);
     }
     float rz[5], v[4];
     {
@@ -186,17 +185,14 @@ __device__ __forceinline__ void vz_quad(const Grid &g, const FCtx &c, const FTab
         for (int l = 1; l <= N; l++) d += g.c[0][l - 1] * (W[4 + r + l] - W[4 + r - l + 1]);
         D[r] = d;
     }
-    bool m[4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) m[r] = inxy && in_range(z + r, c.lo[0], c.hi[0]);
     float mem[4] = {0.f, 0.f, 0.f, 0.f};
-    const bool okq = sq && in_range(x, 0, g.ne[1] - 1) && in_range(y, 0, g.ne[2] - 1) && z >= 0 && z < g.px;
-    if (okq) ld4(mem, cur.psip[0] + o);
+    if (sq) put(mem, lds4(slot + Lay::ZV + cx * 40 + zi));
     float nv[4];
 #pragma unroll
     for (int r = 0; r < 4; r++) {
-        const float bz = buoy(rz[r], rz[r + 1], z + r + 1 >= g.ne[0]);
-        const int t = z - c.z0 + 8 + r;            // table index of node z+r
+        // interior tiles never hold the last node of the axis (1 / rho there)
+        const float bz = BAND ? buoy(rz[r], rz[r + 1], z + r + 1 >= g.ne[0]) : __fdividef(2.0f, rz[r] + rz[r + 1]);
+        const int t = zi + 4 + r;                  // table index of node z+r
         const bool sl = sq && slab_at(g, 0, z + r);
         if (MODE == FWD) {
             float dd = D[r];
@@ -212,42 +208,40 @@ __device__ __forceinline__ void vz_quad(const Grid &g, const FCtx &c, const FTab
             out[r] = sl ? nv[r] + tb.z[2][t] * (nv[r] + mem[r]) : nv[r];
         }
     }
-    if (own && z < g.ne[0] && inxy) {
+    if (wr) {
         st4(nxt.v[0] + o, nv);
-        if (okq) st4(nxt.psip[0] + o, mem);
+        if (sq) st4(nxt.psip[0] + o, mem);
     }
 }
 
 // v_x on the quad z..z+3 at column x (x0-N <= x <= x0+TX+N-2) of plane y.
 template <int N, int MODE, bool BAND>
-__device__ __forceinline__ void vx_quad(const Grid &g, const FCtx &c, const FTabs &tb, const float *slot, int z,
-                                        int x, int y, bool own, const Fields &cur, const Fields &nxt, float (&out)[4])
+__device__ __forceinline__ void vx_quad(const Grid &g, const FCtx &c, const FTabs &tb, const float *slot, int zc,
+                                        int x, const bool (&m)[4], bool wr, long long o, const Fields &nxt,
+                                        float (&out)[4])
 {
-    using Lay = FLay<N>;
-    const int zc = z - c.z0;                       // 0 .. 28
+    using Lay = FLay<N, BAND>;
+    const int xr = x - c.x0 + N;                   // row in the VX / RB layouts
     float Xr[2 * N][4];                            // p at x-N+1 .. x+N
 #pragma unroll
-    for (int t = 0; t < 2 * N; t++) put(Xr[t], lds4(slot + Lay::PB + (x - c.x0 + N + t) * 32 + zc));
-    const bool iny = in_range(y, c.lo[2], c.hi[2]);
+    for (int t = 0; t < 2 * N; t++) put(Xr[t], lds4(slot + Lay::PB + (xr + t) * 32 + zc));
     if (MODE == ADJ && BAND && c.xb) {
-        // transposed CPML operand at the taps in the x slab
-        const bool oky = in_range(y, 0, g.ne[2] - 1) && z < g.px;
+        // transposed CPML operand at the taps (Ap = 0 off the slab)
 #pragma unroll
         for (int t = 0; t < 2 * N; t++) {
-            const int xt = x - N + 1 + t;
-            if (oky && in_range(xt, 0, g.ne[1] - 1) && slab_at(g, 1, xt)) {
+            const float A = tb.x[0][xr + t + 8 - 2 * N + 1];
+            if (A != 0.f) {
                 float ph[4];
-                ld4(ph, cur.psiv[1] + c.sh + foff(g, z, xt, y));
-                const float A = tb.x[0][xt - c.x0 + 8];
+                put(ph, lds4(slot + Lay::XB + (xr + t) * 32 + zc));
 #pragma unroll
                 for (int r = 0; r < 4; r++) Xr[t][r] += A * (Xr[t][r] + ph[r]);
             }
         }
     }
     float r0[4], r1[4], v[4];
-    put(r0, lds4(slot + Lay::RB + (x - c.x0 + N) * 32 + zc));
-    put(r1, lds4(slot + Lay::RB + (x - c.x0 + N + 1) * 32 + zc));
-    put(v, lds4(slot + Lay::VX + (x - c.x0 + N) * 32 + zc));
+    put(r0, lds4(slot + Lay::RB + xr * 32 + zc));
+    put(r1, lds4(slot + Lay::RB + (xr + 1) * 32 + zc));
+    put(v, lds4(slot + Lay::VX + xr * 32 + zc));
     float D[4];
 #pragma unroll
     for (int r = 0; r < 4; r++) {
@@ -256,38 +250,32 @@ __device__ __forceinline__ void vx_quad(const Grid &g, const FCtx &c, const FTab
         for (int l = 1; l <= N; l++) d += g.c[1][l - 1] * (Xr[N - 1 + l][r] - Xr[N - l][r]);
         D[r] = d;
     }
-    const bool mx = in_range(x, c.lo[1], c.hi[1]) && iny;
-    bool m[4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) m[r] = mx && in_range(z + r, c.lo[0], c.hi[0]);
     const bool sx = BAND && c.xb && in_range(x, 0, g.ne[1] - 1) && slab_at(g, 1, x);
-    const long long o = c.sh + foff(g, z, x, y);
     float mem[4] = {0.f, 0.f, 0.f, 0.f};
-    const bool okq = sx && in_range(y, 0, g.ne[2] - 1) && z < g.px;
-    if (okq) ld4(mem, cur.psip[1] + o);
+    if (sx) put(mem, lds4(slot + Lay::XV + xr * 32 + zc));
     const int t = x - c.x0 + 8;
-    const bool lastx = x + 1 >= g.ne[1];
+    const bool lastx = BAND && x + 1 >= g.ne[1];
     float nv[4];
 #pragma unroll
     for (int r = 0; r < 4; r++) {
-        const float bx = buoy(r0[r], r1[r], lastx);
+        const float bx = BAND ? buoy(r0[r], r1[r], lastx) : __fdividef(2.0f, r0[r] + r1[r]);
         if (MODE == FWD) {
             float dd = D[r];
-            if (okq && m[r]) {
+            if (sx && m[r]) {
                 mem[r] = tb.x[3][t] * mem[r] + tb.x[2][t] * dd;
                 dd += mem[r];
             }
             nv[r] = m[r] ? v[r] - g.dt * bx * dd : v[r];
             out[r] = nv[r];
         } else {
-            if (okq && m[r]) mem[r] = tb.x[3][t] * (mem[r] + v[r]);
+            if (sx && m[r]) mem[r] = tb.x[3][t] * (mem[r] + v[r]);
             nv[r] = m[r] ? v[r] - g.dt * bx * D[r] : v[r];
-            out[r] = okq ? nv[r] + tb.x[2][t] * (nv[r] + mem[r]) : nv[r];
+            out[r] = sx ? nv[r] + tb.x[2][t] * (nv[r] + mem[r]) : nv[r];
         }
     }
-    if (own && z < g.ne[0] && mx) {
+    if (wr) {
         st4(nxt.v[1] + o, nv);
-        if (okq) st4(nxt.psip[1] + o, mem);
+        if (sx) st4(nxt.psip[1] + o, mem);
     }
 }
 
@@ -341,25 +329,22 @@ __device__ __forceinline__ void vy_update(const Grid &g, const FCtx &c, int oz, 
 }
 
 // p on the own quad at plane y from the three derivatives of v (adjoint:
-// of the R operands), with the CPML terms of the three axes.
-template <int MODE, bool BAND>
-__device__ __forceinline__ void p_update(const Grid &g, const FCtx &c, const FTabs &tb, int oz, int ox, int y,
-                                         bool memq, float (&dz)[4], float (&dx)[4], float (&dy)[4],
-                                         const float (&pold)[4], const float (&K)[4], const Fields &cur,
-                                         const Fields &nxt)
+// of the R operands), with the CPML terms of the three axes.  m: the quad's
+// box mask (all false: nothing is updated and nxt keeps its equal value).
+template <int N, int MODE, bool BAND>
+__device__ __forceinline__ void p_update(const Grid &g, const FCtx &c, const FTabs &tb, const float *slot, int oz,
+                                         int ox, int y, int txi, int tzi, const bool (&m)[4], long long o,
+                                         float (&dz)[4], float (&dx)[4], float (&dy)[4], const float (&pold)[4],
+                                         const float (&K)[4], const Fields &cur, const Fields &nxt)
 {
-    const bool mxy = memq && in_range(ox, c.lo[1], c.hi[1]) && in_range(y, c.lo[2], c.hi[2]);
-    if (!mxy) return;                            // nothing of the quad is updated: nxt keeps its (equal) value
-    bool m[4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) m[r] = in_range(oz + r, c.lo[0], c.hi[0]);
-    const long long o = c.sh + foff(g, oz, ox, y);
+    using Lay = FLay<N, BAND>;
+    if (!(m[0] || m[1] || m[2] || m[3])) return;
     if (BAND && c.zb && zquad_slab(g, oz)) {     // z memory variable at the quad's slab nodes
         float mem[4];
-        ld4(mem, cur.psiv[0] + o);
+        put(mem, lds4(slot + Lay::ZA + txi * 48 + 4 * tzi + 8));
 #pragma unroll
         for (int r = 0; r < 4; r++) {
-            const int t = oz - c.z0 + 8 + r;
+            const int t = 4 * tzi + 8 + r;
             if (!(m[r] && slab_at(g, 0, oz + r))) continue;
             if (MODE == FWD) {
                 mem[r] = tb.z[1][t] * mem[r] + tb.z[0][t] * dz[r];
@@ -372,8 +357,8 @@ __device__ __forceinline__ void p_update(const Grid &g, const FCtx &c, const FTa
     }
     if (BAND && c.xb && slab_at(g, 1, ox)) {
         float mem[4];
-        ld4(mem, cur.psiv[1] + o);
-        const int t = ox - c.x0 + 8;
+        put(mem, lds4(slot + Lay::XB + (txi + 2 * N - 1) * 32 + 4 * tzi));
+        const int t = txi + 8;
 #pragma unroll
         for (int r = 0; r < 4; r++) {
             if (!m[r]) continue;
@@ -538,10 +523,12 @@ k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUte
          const __grid_constant__ CUtensorMap tm_vzA, const __grid_constant__ CUtensorMap tm_vxB,
          const __grid_constant__ CUtensorMap tm_vy, const __grid_constant__ CUtensorMap tm_pc,
          const __grid_constant__ CUtensorMap tm_rA, const __grid_constant__ CUtensorMap tm_rB,
-         const __grid_constant__ CUtensorMap tm_rc, const __grid_constant__ CUtensorMap tm_Kc, Grid g, Batch b,
+         const __grid_constant__ CUtensorMap tm_rc, const __grid_constant__ CUtensorMap tm_Kc,
+         const __grid_constant__ CUtensorMap tm_mzA, const __grid_constant__ CUtensorMap tm_mxB,
+         const __grid_constant__ CUtensorMap tm_mzV, const __grid_constant__ CUtensorMap tm_mxV, Grid g, Batch b,
          Fields cur, Fields nxt, int step, unsigned *err)
 {
-    using Lay = FLay<N>;
+    using Lay = FLay<N, BAND>;
     constexpr int Q = 2 * N;
     extern __shared__ __align__(128) float sm[];
     float *vzn = sm + FD1 * Lay::SLOT;
@@ -573,6 +560,26 @@ k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUte
         const int oz = c.z0 + 4 * tzi, ox = c.x0 + txi;
         const bool memq = oz < g.ne[0] && ox < g.ne[1];
         const int own = txi * TZ + 4 * tzi;        // own quad in the core tiles
+        const long long plane = (long long)g.px * g.ne[1];
+        // box masks of the quads this thread updates (z, x parts; y per plane)
+        bool mzo[4], mzh[4], mzv[4];
+        const bool mxo = in_range(ox, c.lo[1], c.hi[1]);
+        const bool hvz = tid >= NTHR - 32;         // warp 3: the z halo of v_z
+        const bool hvx = tid < 8 * (2 * N - 1);    // warps 0, 1: the x halo of v_x
+        const int hzt = tid - (NTHR - 32);
+        const int hz_x = hzt & (TX - 1), hz_z = (hzt >= TX) ? c.z0 + TZ : c.z0 - 4;
+        const int hx_zq = tid & 7, hx_col = tid >> 3;
+        const int hx_x = hx_col < N ? c.x0 - N + hx_col : c.x0 + TX + hx_col - N;
+        const bool mxh = in_range(c.x0 + hz_x, c.lo[1], c.hi[1]);
+        const bool mxv = in_range(hx_x, c.lo[1], c.hi[1]);
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            mzo[r] = in_range(oz + r, c.lo[0], c.hi[0]);
+            mzh[r] = in_range(hz_z + r, c.lo[0], c.hi[0]);
+            mzv[r] = in_range(c.z0 + 4 * hx_zq + r, c.lo[0], c.hi[0]);
+        }
+        // own-node offset at plane 0 (v_z, v_x, p and the full-size memory variables share it)
+        const long long o0 = c.sh + foff(g, oz, ox, 0);
 
         // CPML coefficient tables of a band tile (published by the barrier below)
         if (BAND) {
@@ -591,7 +598,7 @@ k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUte
         auto issue = [&](int y) {
             const int k = (y - ya) % FD1;
             float *sl = sm + k * Lay::SLOT;
-            mbar_expect(&bar[k], Lay::BYTES);
+            mbar_expect(&bar[k], Lay::BYTES + (BAND && c.zb ? Lay::ZBYTES : 0u) + (BAND && c.xb ? Lay::XBYTES : 0u));
             tma4(sl + Lay::PA, &tm_pA, c.z0 - 8, c.x0, y, c.s, &bar[k]);
             tma4(sl + Lay::PB, &tm_pB, c.z0, c.x0 - 2 * N + 1, y, c.s, &bar[k]);
             tma4(sl + Lay::VZ, &tm_vzA, c.z0 - 4, c.x0, y, c.s, &bar[k]);
@@ -603,6 +610,16 @@ k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUte
             tma4(sl + Lay::VY, &tm_vy, c.z0, c.x0, y + N - 1, c.s, &bar[k]);
             tma4(sl + Lay::RY, &tm_rc, c.z0, c.x0, y + N, 0, &bar[k]);
             tma4(sl + Lay::PQ, &tm_pc, c.z0, c.x0, y + 2 * N - 1, c.s, &bar[k]);
+            if (BAND) {
+                if (c.zb) {
+                    tma4(sl + Lay::ZA, &tm_mzA, c.z0 - 8, c.x0, y, c.s, &bar[k]);
+                    tma4(sl + Lay::ZV, &tm_mzV, c.z0 - 4, c.x0, y, c.s, &bar[k]);
+                }
+                if (c.xb) {
+                    tma4(sl + Lay::XB, &tm_mxB, c.z0, c.x0 - 2 * N + 1, y, c.s, &bar[k]);
+                    tma4(sl + Lay::XV, &tm_mxV, c.z0, c.x0 - N, y, c.s, &bar[k]);
+                }
+            }
         };
         Ring rr{ya, min(yb, ya + FD1 - 1)};
         if (tid == 0)
@@ -685,22 +702,30 @@ k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUte
                 for (int r = 0; r < 4; r++) pq[(Q - 1 + kq) % Q][r] = e[r];
             }
             float t4[4];
+            const bool my = in_range(y, c.lo[2], c.hi[2]);
+            const long long oy = o0 + (long long)y * plane;
+            bool m[4];
             // ---- v_z at plane y: own quad, then the z halo (warp 3) ----
-            vz_quad<N, MODE, BAND>(g, c, tb, slot, oz, ox, y, true, cur, nxt, t4);
+#pragma unroll
+            for (int r = 0; r < 4; r++) m[r] = mzo[r] && mxo && my;
+            vz_quad<N, MODE, BAND>(g, c, tb, slot, oz, txi, m, memq && mxo && my, oy, nxt, t4);
             sts4(vzn + txi * 40 + 4 * tzi + 4, t4);
-            if (tid >= NTHR - 32) {
-                const int t = tid - (NTHR - 32), hx = t & (TX - 1), hz = (t >= TX) ? c.z0 + TZ : c.z0 - 4;
-                vz_quad<N, MODE, BAND>(g, c, tb, slot, hz, c.x0 + hx, y, false, cur, nxt, t4);
-                sts4(vzn + hx * 40 + (hz - c.z0 + 4), t4);
+            if (hvz) {
+                bool mh[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) mh[r] = mzh[r] && mxh && my;
+                vz_quad<N, MODE, BAND>(g, c, tb, slot, hz_z, hz_x, mh, false, 0, nxt, t4);
+                sts4(vzn + hz_x * 40 + (hz_z - c.z0 + 4), t4);
             }
             // ---- v_x at plane y: own quad, then the x halo (warps 0, 1) ----
-            vx_quad<N, MODE, BAND>(g, c, tb, slot, oz, ox, y, true, cur, nxt, t4);
+            vx_quad<N, MODE, BAND>(g, c, tb, slot, 4 * tzi, ox, m, memq && mxo && my, oy, nxt, t4);
             sts4(vxn + (txi + N) * 32 + 4 * tzi, t4);
-            if (tid < 8 * (2 * N - 1)) {
-                const int zq = tid & 7, col = tid >> 3;
-                const int hx = col < N ? c.x0 - N + col : c.x0 + TX + col - N;
-                vx_quad<N, MODE, BAND>(g, c, tb, slot, c.z0 + 4 * zq, hx, y, false, cur, nxt, t4);
-                sts4(vxn + (hx - c.x0 + N) * 32 + 4 * zq, t4);
+            if (hvx) {
+                bool mh[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) mh[r] = mzv[r] && mxv && my;
+                vx_quad<N, MODE, BAND>(g, c, tb, slot, 4 * hx_zq, hx_x, mh, false, 0, nxt, t4);
+                sts4(vxn + (hx_x - c.x0 + N) * 32 + 4 * hx_zq, t4);
             }
             // ---- v_y at plane y+N-1 (own quad) ----
             {
@@ -768,7 +793,10 @@ k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUte
                 }
                 put(K, lds4(slot + Lay::KC + own));
                 put(p0, lds4(slot + Lay::P0 + own));
-                p_update<MODE, BAND>(g, c, tb, oz, ox, y, memq, dz, dx, dy, p0, K, cur, nxt);
+                bool mp[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) mp[r] = memq && m[r];
+                p_update<N, MODE, BAND>(g, c, tb, slot, oz, ox, y, txi, tzi, mp, oy, dz, dx, dy, p0, K, cur, nxt);
             }
             // all reads of plane y's slot and of the new v tiles are done
             if (__syncthreads_or(!ok)) {
@@ -804,7 +832,7 @@ template <int N, int MODE, bool BAND>
 void run_class(const LaunchCtx &lc, const MapsF &mc, const MapsM &mm, const Grid &g, const Batch &b, Fields cur,
                Fields nxt, int step, unsigned *err)
 {
-    constexpr int smem = s3::FLay<N>::SMEM;
+    constexpr int smem = s3::FLay<N, BAND>::SMEM;
     static const int grid = [] {
         cudaFuncSetAttribute(s3::k3_fused<N, MODE, BAND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(s3::k3_fused<N, MODE, BAND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -815,7 +843,8 @@ void run_class(const LaunchCtx &lc, const MapsF &mc, const MapsM &mm, const Grid
         return std::max(1, per) * std::max(1, sms);
     }();
     s3::k3_fused<N, MODE, BAND><<<grid, s3::NTHR, smem, static_cast<cudaStream_t>(lc.stream)>>>(
-        mc.pA, mc.pB, mc.vzA, mc.vxB, mc.vy, mc.pc, mm.rA, mm.rB, mm.rc, mm.Kc, g, b, cur, nxt, step, err);
+        mc.pA, mc.pB, mc.vzA, mc.vxB, mc.vy, mc.pc, mm.rA, mm.rB, mm.rc, mm.Kc, mc.mzA, mc.mxB, mc.mzV, mc.mxV, g, b,
+        cur, nxt, step, err);
     ++*lc.launches;
 }
 
@@ -839,7 +868,11 @@ bool make_maps_fused(MapsF &m, const Grid &g, const Fields &f, int nshot)
     return make_tile_map(&m.pA, g, f.p, nshot, 48, TX) && make_tile_map(&m.pB, g, f.p, nshot, 32, TX + 4 * N - 2) &&
            make_tile_map(&m.vzA, g, f.v[0], nshot, 40, TX) &&
            make_tile_map(&m.vxB, g, f.v[1], nshot, 32, TX + 2 * N - 1) &&
-           make_tile_map(&m.vy, g, f.v[2], nshot, 32, TX) && make_tile_map(&m.pc, g, f.p, nshot, 32, TX);
+           make_tile_map(&m.vy, g, f.v[2], nshot, 32, TX) && make_tile_map(&m.pc, g, f.p, nshot, 32, TX) &&
+           make_tile_map(&m.mzA, g, f.psiv[0], nshot, 48, TX) &&
+           make_tile_map(&m.mxB, g, f.psiv[1], nshot, 32, TX + 4 * N - 2) &&
+           make_tile_map(&m.mzV, g, f.psip[0], nshot, 40, TX) &&
+           make_tile_map(&m.mxV, g, f.psip[1], nshot, 32, TX + 2 * N - 1);
 }
 
 bool make_maps_model(MapsM &m, const Grid &g)

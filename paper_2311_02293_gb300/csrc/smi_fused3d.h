@@ -10,9 +10,10 @@
 namespace smi {
 
 // Tensor maps of one state buffer (p with its z- and x-widened tiles, the
-// velocity components with theirs, the core tiles) ...
+// velocity components with theirs, the core tiles, and the full-size z / x
+// CPML memory variables in the same geometries) ...
 struct MapsF {
-    CUtensorMap pA, pB, vzA, vxB, vy, pc;
+    CUtensorMap pA, pB, vzA, vxB, vy, pc, mzA, mxB, mzV, mxV;
 };
 // ... and of the model (rho widened along z and x, rho and kappa core tiles).
 struct MapsM {
