@@ -71,8 +71,8 @@ def parse():
     ap.add_argument("--n", type=int, default=300, help="physical grid size of the profiling case (n^3)")
     ap.add_argument("--no-box", action="store_true", help="profiling case without the computing box")
     ap.add_argument("--freesurf", action="store_true", help="profiling case with the free surface (Sec. 2.1)")
-    ap.add_argument("--kernels", default="auto", choices=["auto", "twopass", "generic"],
-                    help="3D kernel family (auto: the single-pass step; twopass: velocity and pressure passes)")
+    ap.add_argument("--kernels", default="auto", choices=["auto", "twopass", "fused", "generic"],
+                    help="3D kernel family (auto = twopass: velocity and pressure passes; fused: the single-pass step)")
     return ap.parse_args()
 
 

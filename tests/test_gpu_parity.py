@@ -60,10 +60,10 @@ SMALL = {
 }
 
 
-# 3D runs the single-pass step by default; "twopass" forces the two-pass tile
-# kernels with the CPML band kernels (the free-surface path).
-KERNELS = {"2d_o4_off": ["auto"], "2d_o8_on": ["auto"], "3d_o4_off": ["auto", "twopass"],
-           "3d_o8_on": ["auto", "twopass"]}
+# 3D runs the two-pass tile kernels by default; "fused" runs the single-pass
+# step (velocity and pressure in one kernel, CPML inline).
+KERNELS = {"2d_o4_off": ["auto"], "2d_o8_on": ["auto"], "3d_o4_off": ["auto", "fused"],
+           "3d_o8_on": ["auto", "fused"]}
 CASE_KERNELS = [(c, k) for c in sorted(SMALL) for k in KERNELS[c]]
 
 
@@ -242,7 +242,7 @@ def test_errors_are_reported(smi):
     assert e.value.code == -1
 
 
-@pytest.mark.parametrize("order,kernels", [(4, "auto"), (8, "auto"), (8, "twopass")])
+@pytest.mark.parametrize("order,kernels", [(4, "auto"), (8, "auto"), (4, "fused"), (8, "fused")])
 def test_long_adjoint_through_cpml_corners_3d(smi, order, kernels):
     """Hundreds of steps with most of the energy inside the CPML slabs and
     their edges/corners: the transposed CPML terms of the adjoint must stay
@@ -347,7 +347,7 @@ def test_single_pass_matches_two_pass(smi, order, use_box):
     recs = [w.recs[0], w.recs[0][::2].copy()]
     vp, rho, stf = _dev(w.vp), _dev(w.rho), _dev(w.stf)
     out = {}
-    for k in ("auto", "twopass"):
+    for k in ("fused", "twopass"):
         prob = _gprob(smi, w, use_box=use_box, kernels=k)
         seis = smi.smi_forward(vp, rho, prob, srcs, recs, stf, flat=True)
         dobs = (0.8 * seis).contiguous()
@@ -356,6 +356,6 @@ def test_single_pass_matches_two_pass(smi, order, use_box):
         img = smi.smi_rtm(vp, rho, prob, srcs, recs, stf, dobs)
         out[k] = [t.double().cpu().numpy() for t in (seis, g, img)] + [float(J.item())]
         torch.cuda.synchronize()
-    for a, b in zip(out["auto"][:3], out["twopass"][:3]):
+    for a, b in zip(out["fused"][:3], out["twopass"][:3]):
         assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
-    assert abs(out["auto"][3] - out["twopass"][3]) <= 1e-5 * abs(out["twopass"][3])
+    assert abs(out["fused"][3] - out["twopass"][3]) <= 1e-5 * abs(out["twopass"][3])
