@@ -106,6 +106,8 @@ struct Setup {
     int img_norm = 0;                      // normalised RTM image
     bool rho_grad = false;                 // gradient with the density part (parametrisation families)
     bool fused = false;                    // 3D forward / adjoint steps by the single-pass kernel
+    bool inline3 = false;                  // 3D two-pass tile kernels with the z / x CPML terms inline
+    bool fullmem = false;                  // z / x CPML memory variables as full-size arrays (either of the above)
     long long nrec_total = 0;
     std::vector<int> rec_offset;
     std::vector<Stencil> src_st, rec_st;
@@ -239,6 +241,8 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     for (int a = 0; a < 3; a++)
         for (int l = 0; l < kMaxHalf; l++) g.c[a][l] = (a < m->ndim && l < N) ? (float)(coef[l] / hh[a]) : 0.0f;
     S.fused = o->kernels == SMI_KERNELS_FUSED && fused3d_supported(g);
+    S.inline3 = !S.fused && o->kernels == SMI_KERNELS_AUTO && stencil3d_supported(g);
+    S.fullmem = S.fused || S.inline3;
 
     // inputs on the device
     const size_t nphys = (size_t)g.nphys;
@@ -399,7 +403,7 @@ size_t per_shot_bytes(const Setup &S, int kind)
     const size_t fields = (size_t)(1 + g.ndim) * g.ntot * 4;
     const int nbuf = S.fused ? 2 : 1;          // the single-pass step reads one state buffer, writes the other
     size_t slabs = 0;
-    for (int a = 0; a < g.ndim; a++) slabs += 2 * (size_t)(S.fused && a < 2 ? g.ntot : g.slab_n[a]) * 4;
+    for (int a = 0; a < g.ndim; a++) slabs += 2 * (size_t)(S.fullmem && a < 2 ? g.ntot : g.slab_n[a]) * 4;
     const long long maxrec = S.nrec_total;     // upper bound of one shot's receivers
     size_t b = nbuf * (fields + slabs) + (size_t)S.nt * maxrec * 4;
     if (kind != 0) {
@@ -579,6 +583,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         const bool fast3 = o->kernels != SMI_KERNELS_GENERIC && stencil3d_supported(g);
         const bool fast2 = o->kernels != SMI_KERNELS_GENERIC && stencil2d_supported(g);
         const bool fused = S.fused;
+        const bool inl = S.inline3;            // two-pass 3D kernels with the z / x CPML terms inline
         const bool norm = kind == 1 && S.img_norm;       // normalised RTM image
 
         size_t batch_peak = 0;                   // largest batch arena (fields, bands, accumulators)
@@ -607,7 +612,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             // after every step).  Memory variables of the single-pass step:
             // z and x full-size, y in the y-slab layout.
             Fields F{}, A{}, F2{}, A2{};
-            auto mem_n = [&](int a) { return (size_t)(fused && a < 2 ? g.ntot : g.slab_n[a]) * nb_shot; };
+            auto mem_n = [&](int a) { return (size_t)(S.fullmem && a < 2 ? g.ntot : g.slab_n[a]) * nb_shot; };
             for (Fields *f : {&F, &F2}) {
                 if ((f == &F2 && !fused) || kind == 7) break;
                 f->p = ba.get<float>((size_t)g.ntot * nb_shot);
@@ -666,13 +671,14 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 cudaMemcpyAsync(d_soff, soff.data(), sizeof(long long) * soff.size(), cudaMemcpyHostToDevice, st);
             }
             Maps3 mF{}, mA{}, mF2{}, mA2{};
-            if (fast3 && (!make_maps3(mF, g, F, nb_shot) || (kind != 0 && !make_maps3(mA, g, A, nb_shot))))
+            if (fast3 && (!make_maps3(mF, g, F, nb_shot, S.fullmem) ||
+                          (kind != 0 && !make_maps3(mA, g, A, nb_shot, S.fullmem))))
                 return fail(SMI_ERR_CUDA, "tensor map encoding failed");
             MapsF fF{}, fF2{}, fA{}, fA2{};
             MapsM fM{};
-            if (fused && (!make_maps3(mF2, g, F2, nb_shot) || !make_maps_fused(fF, g, F, nb_shot) ||
+            if (fused && (!make_maps3(mF2, g, F2, nb_shot, true) || !make_maps_fused(fF, g, F, nb_shot) ||
                           !make_maps_fused(fF2, g, F2, nb_shot) || !make_maps_model(fM, g) ||
-                          (kind != 0 && (!make_maps3(mA2, g, A2, nb_shot) || !make_maps_fused(fA, g, A, nb_shot) ||
+                          (kind != 0 && (!make_maps3(mA2, g, A2, nb_shot, true) || !make_maps_fused(fA, g, A, nb_shot) ||
                                          !make_maps_fused(fA2, g, A2, nb_shot)))))
                 return fail(SMI_ERR_CUDA, "tensor map encoding failed");
             // after a single-pass step the written buffers become the current ones
@@ -739,11 +745,11 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     launch3_fused(lc, fF, fM, g, b, F, F2, it, 0, d_wait);
                     swap_F();
                 } else if (fast3) {
-                    launch3_v(lc, mF, g, b, F, it, 0, d_wait);
-                    launch_fwd_corrections(lc, g, b, F, it, true, blo, bhi);
+                    launch3_v(lc, mF, g, b, F, it, 0, d_wait, inl);
+                    if (!inl) launch_fwd_corrections(lc, g, b, F, it, true, blo, bhi);
                     launch_free_surface(lc, g, F.v[0], nb_shot, kFsMirrorV);
-                    launch3_p(lc, mF, nullptr, g, b, F, it, 0, d_wait, nullptr, 0, nullptr, 0.0f);
-                    launch_fwd_corrections(lc, g, b, F, it, false, blo, bhi);
+                    launch3_p(lc, mF, nullptr, g, b, F, it, 0, d_wait, nullptr, 0, nullptr, 0.0f, inl);
+                    if (!inl) launch_fwd_corrections(lc, g, b, F, it, false, blo, bhi);
                 } else if (fast2) {                    // CPML and (it < nt) the source inline
                     launch2_v(lc, g, b, F, it, 0, blo, bhi);
                     launch_free_surface(lc, g, F.v[0], nb_shot, kFsMirrorV);
@@ -826,9 +832,9 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             auto reconstruct = [&](int it) {
                 tm.begin(2);
                 if (fast3) {
-                    launch3_p(lc, mF, &mA, g, b, F, it, 2, d_wait, acc, mode, S.stf, (float)S.src_scale);
+                    launch3_p(lc, mF, &mA, g, b, F, it, 2, d_wait, acc, mode, S.stf, (float)S.src_scale, false);
                     launch_free_surface(lc, g, F.p, nb_shot, kFsMirrorP);
-                    launch3_v(lc, mF, g, b, F, it, 2, d_wait);
+                    launch3_v(lc, mF, g, b, F, it, 2, d_wait, false);
                 } else {
                     int blo[3], bhi[3];
                     batch_box(S.box_src, it, blo, bhi);
@@ -868,11 +874,11 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                     launch3_fused(lc, fA, fM, g, b, A, A2, mrev, 1, d_wait);
                     swap_A();
                 } else if (fast3) {
-                    launch_adj_corrections(lc, g, b, A, mrev, true, blo, bhi);
-                    launch3_v(lc, mA, g, b, A, mrev, 1, d_wait);
+                    if (!inl) launch_adj_corrections(lc, g, b, A, mrev, true, blo, bhi);
+                    launch3_v(lc, mA, g, b, A, mrev, 1, d_wait, inl);
                     launch_free_surface(lc, g, A.v[0], nb_shot, kFsFoldV);
-                    launch_adj_corrections(lc, g, b, A, mrev, false, blo, bhi);
-                    launch3_p(lc, mA, nullptr, g, b, A, mrev, 1, d_wait, nullptr, 0, nullptr, 0.0f);
+                    if (!inl) launch_adj_corrections(lc, g, b, A, mrev, false, blo, bhi);
+                    launch3_p(lc, mA, nullptr, g, b, A, mrev, 1, d_wait, nullptr, 0, nullptr, 0.0f, inl);
                 } else if (fast2) {                    // transposed CPML inline in the 2D kernels
                     launch2_v(lc, g, b, A, mrev, 1, blo, bhi);
                     launch_free_surface(lc, g, A.v[0], nb_shot, kFsFoldV);

@@ -99,24 +99,6 @@ template <int N, bool BAND = false> struct FLay {
                   "slot pieces must stay 128-byte aligned for TMA");
 };
 
-// CPML coefficient tables of one tile (band tiles only): [0] Ap, [1] Bp,
-// [2] Av, [3] Bv along z for z0-8 .. z0+39 and along x for x0-8 .. x0+TX+7,
-// zero outside the grid.
-struct FTabs {
-    float z[4][48];
-    float x[4][TX + 16];
-};
-
-__device__ __forceinline__ bool slab_at(const Grid &g, int a, int j)
-{
-    return j < g.nb || j >= g.ne[a] - g.nb - 1;
-}
-// Quad of z nodes z..z+3 touches the z slab.
-__device__ __forceinline__ bool zquad_slab(const Grid &g, int z)
-{
-    return z < g.nb || z + 3 >= g.ne[0] - g.nb - 1;
-}
-
 // Own-node offsets: field arrays and full-size z / x memory variables share
 // the padded layout; 32-bit within one shot.
 __device__ __forceinline__ int foff(const Grid &g, int z, int x, int y) { return z + g.px * (x + g.ne[1] * y); }
@@ -394,125 +376,6 @@ __device__ __forceinline__ void p_update(const Grid &g, const FCtx &c, const FTa
     st4(nxt.p + o, np);
 }
 
-// ---------------------------------------------------------------------------
-// Work of one launch: the tile columns of one class (interior: no stencil of
-// the tile reaches a z or x slab; band: the others) times y-chunks of the
-// box.  A column is a band column when its z window [z0-8, z0+39] or x
-// window [x0-8, x0+TX+7] meets a slab; interior z tiles (and x tiles) form
-// one contiguous range, so the interior columns are a rectangle.
-__device__ __forceinline__ bool band_z(const Grid &g, int z0) { return z0 - 8 < g.nb || z0 + 39 >= g.ne[0] - g.nb - 1; }
-__device__ __forceinline__ bool band_x(const Grid &g, int x0)
-{
-    return x0 - 8 < g.nb || x0 + TX + 7 >= g.ne[1] - g.nb - 1;
-}
-
-struct CDecomp {
-    int zbase, nzt, nxt, iz0, iz1, ix0, ix1, ncol, nyc, cy;
-};
-
-__device__ __forceinline__ CDecomp cdecomp(const Grid &g, const int lo[3], const int hi[3], int grid, bool band)
-{
-    CDecomp d;
-    d.zbase = lo[0] & ~31;
-    const int ylen = hi[2] - lo[2] + 1;
-    d.nzt = hi[0] >= lo[0] ? (hi[0] - d.zbase) / TZ + 1 : 0;
-    d.nxt = hi[1] >= lo[1] ? (hi[1] - lo[1]) / TX + 1 : 0;
-    d.iz0 = d.iz1 = d.ix0 = d.ix1 = 0;
-    d.ncol = 0;
-    d.nyc = 0;
-    d.cy = 1;
-    if (d.nzt == 0 || d.nxt == 0 || ylen <= 0) return d;
-    d.iz0 = d.nzt;
-    for (int i = 0; i < d.nzt; i++)
-        if (!band_z(g, d.zbase + TZ * i)) {
-            if (d.iz0 == d.nzt) d.iz0 = i;
-            d.iz1 = i + 1;
-        }
-    if (d.iz0 == d.nzt) d.iz0 = d.iz1 = 0;
-    d.ix0 = d.nxt;
-    for (int i = 0; i < d.nxt; i++)
-        if (!band_x(g, lo[1] + TX * i)) {
-            if (d.ix0 == d.nxt) d.ix0 = i;
-            d.ix1 = i + 1;
-        }
-    if (d.ix0 == d.nxt) d.ix0 = d.ix1 = 0;
-    const int nint = (d.iz1 - d.iz0) * (d.ix1 - d.ix0);
-    d.ncol = band ? d.nzt * d.nxt - nint : nint;
-    if (d.ncol == 0) return d;
-    // chunks along y: as many as fill the persistent grid's waves to 90 %
-    const long long cols = d.ncol;
-    const int cmax = max(1, ylen / 16);
-    auto fill = [&](int c) {
-        const long long items = cols * c;
-        return (float)items / (float)(((items + grid - 1) / grid) * grid);
-    };
-    int chunks = max(1, min(cmax, (int)(grid / cols)));
-    if (fill(chunks) < 0.9f) {
-        for (int c = chunks + 1; c <= min(cmax, 4 * chunks + 4); c++) {
-            if (fill(c) >= 0.9f) {
-                chunks = c;
-                break;
-            }
-        }
-    }
-    d.cy = (ylen + chunks - 1) / chunks;
-    d.nyc = (ylen + d.cy - 1) / d.cy;
-    return d;
-}
-
-// Column k (0 .. ncol-1) of the class -> tile indices (zi, xi).
-__device__ __forceinline__ void class_column(const CDecomp &d, bool band, int k, int &zi, int &xi)
-{
-    const int nix = d.ix1 - d.ix0;
-    if (!band) {
-        zi = d.iz0 + k / nix;
-        xi = d.ix0 + k % nix;
-        return;
-    }
-    for (zi = 0; zi < d.nzt; zi++) {
-        const bool zint = zi >= d.iz0 && zi < d.iz1;
-        const int cnt = zint ? d.nxt - nix : d.nxt;
-        if (k < cnt) {
-            xi = (zint && k >= d.ix0) ? k - d.ix0 + d.ix1 : k;
-            return;
-        }
-        k -= cnt;
-    }
-    xi = 0;
-}
-
-// Item w of a class's launch (shots in order), false past the end.
-__device__ __forceinline__ bool get_citem(const Grid &g, const Batch &b, int mode, int step, bool band, long long w,
-                                          Item &it)
-{
-    const int target = (int)gridDim.x;
-    for (int s = 0; s < b.nshot; s++) {
-        int lo[3], hi[3], plo[3] = {0, 0, 0}, phi[3] = {-1, -1, -1};
-        item_box(g, b, mode, s, step, lo, hi, plo, phi);
-        const CDecomp d = cdecomp(g, lo, hi, target, band);
-        const long long n = (long long)d.ncol * d.nyc;
-        if (w < n) {
-            const int k = (int)(w % d.ncol), ci = (int)(w / d.ncol);
-            int zi, xi;
-            class_column(d, band, k, zi, xi);
-            it.s = s;
-            it.z0 = d.zbase + TZ * zi;
-            it.x0 = lo[1] + TX * xi;
-            it.ya = lo[2] + ci * d.cy;
-            it.yb = min(hi[2], it.ya + d.cy - 1);
-            for (int a = 0; a < 3; a++) {
-                it.lo[a] = lo[a];
-                it.hi[a] = hi[a];
-                it.plo[a] = plo[a];
-                it.phi[a] = phi[a];
-            }
-            return true;
-        }
-        w -= n;
-    }
-    return false;
-}
-
 // ===========================================================================
 // The fused step.  MODE FWD: the forward scheme with the forward CPML (box
 // of the source); MODE ADJ: the adjoint in lambda form with the transposed
@@ -582,18 +445,7 @@ k3_fused(const __grid_constant__ CUtensorMap tm_pA, const __grid_constant__ CUte
         const long long o0 = c.sh + foff(g, oz, ox, 0);
 
         // CPML coefficient tables of a band tile (published by the barrier below)
-        if (BAND) {
-            for (int i = tid; i < 4 * 48; i += NTHR) {
-                const int k = i / 48, j = i % 48, zz = c.z0 - 8 + j;
-                const float *src = k == 0 ? g.cpa[0] : k == 1 ? g.cpb[0] : k == 2 ? g.cva[0] : g.cvb[0];
-                tb.z[k][j] = (zz >= 0 && zz < g.ne[0]) ? src[zz] : 0.f;
-            }
-            for (int i = tid; i < 4 * (TX + 16); i += NTHR) {
-                const int k = i / (TX + 16), j = i % (TX + 16), xx = c.x0 - 8 + j;
-                const float *src = k == 0 ? g.cpa[1] : k == 1 ? g.cpb[1] : k == 2 ? g.cva[1] : g.cvb[1];
-                tb.x[k][j] = (xx >= 0 && xx < g.ne[1]) ? src[xx] : 0.f;
-            }
-        }
+        if (BAND) load_tabs(g, c.z0, c.x0, tb);
 
         auto issue = [&](int y) {
             const int k = (y - ya) % FD1;

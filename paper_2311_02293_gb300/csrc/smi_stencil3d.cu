@@ -44,18 +44,34 @@ namespace s3 {
 // of lead.  Core ring: the pointwise 32 x 16 tiles of one plane, SC slots.
 constexpr int PFP = SMI_PFP, SC = 3, CORE = TZ * TX;
 
-template <int N> struct VLay {
+// Tile classes of a launch (template CLS): ALLT every tile column of the box
+// (z / x CPML terms then come from the band kernels), INT the interior
+// columns only, BND the CPML-band columns only, with the z / x CPML terms
+// applied inline from memory-variable tiles that arrive in the core ring
+// (BND core slots: two deep).
+enum { ALLT = 0, INT = 1, BND = 2 };
+
+// Band extras of the velocity kernel's core slot: the p-grid memory
+// variables (adjoint phi_z, phi_x) over the p tile's geometry, and the
+// v-grid ones (forward psi / adjoint chi, z and x) over the core tile.
+template <int N, int CLS = ALLT> struct VLay {
     static constexpr int PR = TX + 2 * N - 1;            // p tile rows: x0-N+1 .. x0+TX-1+N
     static constexpr int P_OFF = 0, P_SZ = rup32(ZW * PR);
     static constexpr int R_OFF = P_SZ, R_SZ = rup32(36 * (TX + 1));   // rho: z0..z0+35, x0..x0+TX
     static constexpr int SLOT = P_SZ + R_SZ;
     static constexpr int S = N + 1 + PFP;
     static constexpr unsigned BYTES = (unsigned)(ZW * PR + 36 * (TX + 1)) * 4u;
-    static constexpr int CSLOT = 3 * CORE;                              // vz, vx, vy
+    static constexpr int E_PZ = 3 * CORE, E_PX = E_PZ + P_SZ, E_CZ = E_PX + P_SZ, E_CX = E_CZ + CORE;
+    static constexpr int CSLOT = CLS == BND ? E_CX + CORE : 3 * CORE;   // vz, vx, vy (+ band extras)
     static constexpr unsigned CBYTES = 3u * CORE * 4u;
-    static constexpr int SMEM = (S * SLOT + SC * CSLOT) * 4;
+    static constexpr unsigned PBYTES = (unsigned)(ZW * PR) * 4u;        // one p-geometry memory tile
+    static constexpr int NC = CLS == BND ? 2 : SC;
+    static constexpr int SMEM = (S * SLOT + NC * CSLOT) * 4;
 };
-template <int N> struct PLay {
+// Band extras of the pressure kernel's core slot: the v-grid memory
+// variables (adjoint chi_z, chi_x) over the v_z / v_x tile geometries, and
+// the p-grid ones (forward psi / adjoint phi, z and x) over the core tile.
+template <int N, int CLS = ALLT> struct PLay {
     static constexpr int XR = TX + 2 * N - 1;            // vx tile rows: x0-N .. x0+TX-2+N
     static constexpr int Z_OFF = 0, Z_SZ = rup32(ZW * TX);            // vz: z0-4.., x core
     static constexpr int X_OFF = Z_SZ, X_SZ = rup32(TZ * XR);         // vx: z core
@@ -63,25 +79,31 @@ template <int N> struct PLay {
     static constexpr int SLOT = Z_SZ + X_SZ + Y_SZ;
     static constexpr int S = N + PFP;
     static constexpr unsigned BYTES = (unsigned)(ZW * TX + TZ * XR + CORE) * 4u;
-    static constexpr int CSLOT = 3 * CORE;                              // p, kappa, lambda_p
-    static constexpr int SMEM = (S * SLOT + SC * CSLOT) * 4;
+    static constexpr int E_HZ = 3 * CORE, E_HX = E_HZ + Z_SZ, E_CZ = E_HX + X_SZ, E_CX = E_CZ + CORE;
+    static constexpr int CSLOT = CLS == BND ? E_CX + CORE : 3 * CORE;   // p, kappa, lambda_p (+ band extras)
+    static constexpr int NC = CLS == BND ? 2 : SC;
+    static constexpr int SMEM = (S * SLOT + NC * CSLOT) * 4;
 };
 
 
 // ===========================================================================
 // Velocity kernel.  FWD/ADJ: v_a -= dt b_a D_a p (+ CPML terms); REC:
 // v_a += dt b_a D_a p on L_a+N-1..H_a-N, zero outside the previous box.
-template <int N, int MODE>
-__global__ void __launch_bounds__(NTHR, SMI_MINB)
+template <int N, int MODE, int CLS>
+__global__ void __launch_bounds__(NTHR, CLS == BND ? 3 : SMI_MINB)
 k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_rho,
      const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensorMap tm_vx,
-     const __grid_constant__ CUtensorMap tm_vy, Grid g, Batch b, Fields f, int step, unsigned *err)
+     const __grid_constant__ CUtensorMap tm_vy, const __grid_constant__ CUtensorMap tm_pzh,
+     const __grid_constant__ CUtensorMap tm_pxh, const __grid_constant__ CUtensorMap tm_cz,
+     const __grid_constant__ CUtensorMap tm_cx, Grid g, Batch b, Fields f, int step, unsigned *err)
 {
-    using Lay = VLay<N>;
+    using Lay = VLay<N, CLS>;
     constexpr int S = Lay::S;
+    constexpr int SC = Lay::NC;
     extern __shared__ __align__(128) float sm[];
     float *cbase = sm + S * Lay::SLOT;
     __shared__ __align__(8) uint64_t bar[S], cbar[SC];
+    __shared__ FTabs tb;
     const int tid = threadIdx.x, tzi = tid & 7, txi = tid >> 3;
     if (tid == 0) {
         for (int k = 0; k < S; k++) mbar_init(&bar[k], 1);
@@ -96,9 +118,34 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
 #endif
 
     Item it;
-    for (long long w = blockIdx.x; get_item(g, b, MODE, step, w, it); w += gridDim.x) {
+    for (long long w = blockIdx.x;
+         CLS == ALLT ? get_item(g, b, MODE, step, w, it) : get_citem(g, b, MODE, step, CLS == BND, w, it);
+         w += gridDim.x) {
         const int s = it.s, z0 = it.z0, x0 = it.x0, ya = it.ya, yb = it.yb;
         const int ylast = yb + N;                 // last haloed plane needed
+        const bool zb = CLS == BND && band_z(g, z0), xb = CLS == BND && band_x(g, x0);
+        if (CLS == BND) load_tabs(g, z0, x0, tb);   // published by the barrier after the first waits
+        // band extras of a core slot: bytes and copies (adjoint: p-geometry phi tiles too)
+        const unsigned cbytes = Lay::CBYTES + (zb ? CORE * 4u + (MODE == ADJ ? Lay::PBYTES : 0u) : 0u) +
+                                (xb ? CORE * 4u + (MODE == ADJ ? Lay::PBYTES : 0u) : 0u);
+        auto issue_core = [&](int yy) {
+            const int k = (yy - ya) % SC;
+            float *cs = cbase + k * Lay::CSLOT;
+            mbar_expect(&cbar[k], cbytes);
+            tma4(cs, &tm_vz, z0, x0, yy, s, &cbar[k]);
+            tma4(cs + CORE, &tm_vx, z0, x0, yy, s, &cbar[k]);
+            tma4(cs + 2 * CORE, &tm_vy, z0, x0, yy, s, &cbar[k]);
+            if (CLS == BND) {
+                if (zb) {
+                    if (MODE == ADJ) tma4(cs + Lay::E_PZ, &tm_pzh, z0 - 4, x0 - N + 1, yy, s, &cbar[k]);
+                    tma4(cs + Lay::E_CZ, &tm_cz, z0, x0, yy, s, &cbar[k]);
+                }
+                if (xb) {
+                    if (MODE == ADJ) tma4(cs + Lay::E_PX, &tm_pxh, z0 - 4, x0 - N + 1, yy, s, &cbar[k]);
+                    tma4(cs + Lay::E_CX, &tm_cx, z0, x0, yy, s, &cbar[k]);
+                }
+            }
+        };
         const int oz = z0 + 4 * tzi, ox = x0 + txi;
         const bool mem = oz < g.ne[0] && ox < g.ne[1];
         const long long sh = (long long)s * g.ntot;
@@ -126,14 +173,7 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
                 tma4(slot + Lay::P_OFF, &tm_p, z0 - 4, x0 - N + 1, y, s, &bar[k]);
                 tma4(slot + Lay::R_OFF, &tm_rho, z0, x0, y, 0, &bar[k]);
             }
-            for (int y = ya; y <= cr.issued; y++) {
-                const int k = (y - ya) % SC;
-                float *cs = cbase + k * Lay::CSLOT;
-                mbar_expect(&cbar[k], Lay::CBYTES);
-                tma4(cs, &tm_vz, z0, x0, y, s, &cbar[k]);
-                tma4(cs + CORE, &tm_vx, z0, x0, y, s, &cbar[k]);
-                tma4(cs + 2 * CORE, &tm_vy, z0, x0, y, s, &cbar[k]);
-            }
+            for (int y = ya; y <= cr.issued; y++) issue_core(y);
         }
         bool ok = true;
 #pragma unroll
@@ -182,7 +222,8 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
             const float *rt = pt + Lay::R_OFF;
             const float *rt1 = sm + ((y + 1 - ya) % S) * Lay::SLOT + Lay::R_OFF;
             put(q[((2 * N - 1) + kq) % (2 * N)], lds4(sm + ((y + N - ya) % S) * Lay::SLOT + Lay::P_OFF + own));
-            const float *cs = cbase + ((y - ya) % SC) * Lay::CSLOT + txi * TZ + 4 * tzi;
+            const float *cslot = cbase + ((y - ya) % SC) * Lay::CSLOT;   // this plane's core slot
+            const float *cs = cslot + txi * TZ + 4 * tzi;
             bool keep[4];
             if (MODE == REC) {
                 const bool kxy = in_range(ox, it.plo[1], it.phi[1]) && in_range(y, it.plo[2], it.phi[2]);
@@ -204,6 +245,12 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
                     W[4] = a1.x; W[5] = a1.y; W[6] = a1.z; W[7] = a1.w;
                     W[8] = a2.x; W[9] = a2.y; W[10] = a2.z; W[11] = a2.w;
                 }
+                if (MODE == ADJ && CLS == BND && zb && (oz - 4 < g.nb || oz + 7 >= g.ne[0] - g.nb - 1)) {
+                    // transposed CPML operand over the window: lp + Ap (lp + phi) (Ap = 0 off the slab)
+                    const float *ph = cslot + Lay::E_PZ + (txi + N - 1) * ZW + 4 * tzi;
+#pragma unroll
+                    for (int i = 0; i < 12; i++) W[i] += tb.z[0][oz - z0 + 4 + i] * (W[i] + ph[i]);
+                }
                 const float r4 = rt[txi * 36 + 4 * tzi + 4];
                 const float rz[5] = {rho0[0], rho0[1], rho0[2], rho0[3], r4};
                 float v[4];
@@ -215,6 +262,24 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
 #pragma unroll
                     for (int l = 1; l <= N; l++) d += g.c[0][l - 1] * (W[4 + r + l] - W[4 + r - l + 1]);
                     D[r] = d;
+                }
+                if (CLS == BND && zb && zquad_slab(g, oz) && act) {
+                    // z memory variable at the quad's slab nodes: forward psi <- Bv psi + Av D (added to D);
+                    // adjoint chi <- Bv (chi + lv before this step)
+                    float mz4[4];
+                    put(mz4, lds4(cs + Lay::E_CZ));
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        const int t = oz - z0 + 8 + r;
+                        if (!(mz[r] && slab_at(g, 0, oz + r))) continue;
+                        if (MODE == FWD) {
+                            mz4[r] = tb.z[3][t] * mz4[r] + tb.z[2][t] * D[r];
+                            D[r] += mz4[r];
+                        } else {
+                            mz4[r] = tb.z[3][t] * (mz4[r] + v[r]);
+                        }
+                    }
+                    stg4(f.psip[0] + sh + gidx(g, oz, ox, y), mz4);
                 }
                 float nv[4];
 #pragma unroll
@@ -237,6 +302,19 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
                     put(Xr[N - 1 + l], lds4(pt + Lay::P_OFF + (txi + N - 1 + l) * ZW + 4 * tzi + 4));
                     put(Xr[N - l], lds4(pt + Lay::P_OFF + (txi + N - l) * ZW + 4 * tzi + 4));
                 }
+                if (MODE == ADJ && CLS == BND && xb) {
+                    // transposed CPML operand at the taps x - N + 1 + t (Ap = 0 off the slab)
+#pragma unroll
+                    for (int t = 0; t < 2 * N; t++) {
+                        const float A = tb.x[0][txi + t - N + 1 + 8];
+                        if (A != 0.f) {
+                            float ph[4];
+                            put(ph, lds4(cslot + Lay::E_PX + (txi + t) * ZW + 4 * tzi + 4));
+#pragma unroll
+                            for (int r = 0; r < 4; r++) Xr[t][r] += A * (Xr[t][r] + ph[r]);
+                        }
+                    }
+                }
                 float rx[4], v[4];
                 put(rx, lds4(rt + (txi + 1) * 36 + 4 * tzi));
                 put(v, lds4(cs + CORE));
@@ -247,6 +325,22 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
 #pragma unroll
                     for (int l = 1; l <= N; l++) d += g.c[1][l - 1] * (Xr[N - 1 + l][r] - Xr[N - l][r]);
                     D[r] = d;
+                }
+                if (CLS == BND && xb && ox < g.ne[1] && slab_at(g, 1, ox) && act) {
+                    float mx4[4];
+                    put(mx4, lds4(cs + Lay::E_CX));
+                    const int t = txi + 8;
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        if (!mz[r]) continue;
+                        if (MODE == FWD) {
+                            mx4[r] = tb.x[3][t] * mx4[r] + tb.x[2][t] * D[r];
+                            D[r] += mx4[r];
+                        } else {
+                            mx4[r] = tb.x[3][t] * (mx4[r] + v[r]);
+                        }
+                    }
+                    stg4(f.psip[1] + sh + gidx(g, oz, ox, y), mx4);
                 }
                 const bool lastx = ox + 1 >= g.ne[1];
                 const bool rxm = MODE == REC && in_range(ox, g.L[1] + N - 1, g.H[1] - N);
@@ -338,15 +432,7 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
                     tma4(slot + Lay::P_OFF, &tm_p, z0 - 4, x0 - N + 1, yn, s, &bar[k]);
                     tma4(slot + Lay::R_OFF, &tm_rho, z0, x0, yn, 0, &bar[k]);
                 }
-                if (cr.issued < yb) {
-                    const int yn = cr.issued + 1;
-                    const int k = (yn - ya) % SC;
-                    float *c2 = cbase + k * Lay::CSLOT;
-                    mbar_expect(&cbar[k], Lay::CBYTES);
-                    tma4(c2, &tm_vz, z0, x0, yn, s, &cbar[k]);
-                    tma4(c2 + CORE, &tm_vx, z0, x0, yn, s, &cbar[k]);
-                    tma4(c2 + 2 * CORE, &tm_vy, z0, x0, yn, s, &cbar[k]);
-                }
+                if (cr.issued < yb) issue_core(cr.issued + 1);
             }
             if (hr.issued < ylast) hr.issued++;
             if (cr.issued < yb) cr.issued++;
@@ -376,19 +462,23 @@ k3_v(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorM
 // Pressure kernel.  FWD/ADJ: p -= dt kappa sum_a D_a v_a (+ CPML terms);
 // REC: acc += lp * (div v | p), p += dt kappa div v - source, zero outside the
 // previous box, on the physical domain.
-template <int N, int MODE>
-__global__ void __launch_bounds__(NTHR, SMI_MINB)
+template <int N, int MODE, int CLS>
+__global__ void __launch_bounds__(NTHR, CLS == BND ? 3 : SMI_MINB)
 k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensorMap tm_vx,
      const __grid_constant__ CUtensorMap tm_vy, const __grid_constant__ CUtensorMap tm_pc,
-     const __grid_constant__ CUtensorMap tm_K, const __grid_constant__ CUtensorMap tm_lp, Grid g, Batch b,
+     const __grid_constant__ CUtensorMap tm_K, const __grid_constant__ CUtensorMap tm_lp,
+     const __grid_constant__ CUtensorMap tm_czh, const __grid_constant__ CUtensorMap tm_cxh,
+     const __grid_constant__ CUtensorMap tm_pzc, const __grid_constant__ CUtensorMap tm_pxc, Grid g, Batch b,
      Fields f, int step, unsigned *err, float *acc, int img_mode, const float *stf, float src_scale)
 {
-    using Lay = PLay<N>;
+    using Lay = PLay<N, CLS>;
     constexpr int S = Lay::S;
+    constexpr int SC = Lay::NC;
     constexpr unsigned CBYTES = (MODE == REC ? 3u : 2u) * CORE * 4u;
     extern __shared__ __align__(128) float sm[];
     float *cbase = sm + S * Lay::SLOT;
     __shared__ __align__(8) uint64_t bar[S], cbar[SC];
+    __shared__ FTabs tb;
     const int tid = threadIdx.x, tzi = tid & 7, txi = tid >> 3;
     if (tid == 0) {
         for (int k = 0; k < S; k++) mbar_init(&bar[k], 1);
@@ -403,9 +493,34 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
 #endif
 
     Item it;
-    for (long long w = blockIdx.x; get_item(g, b, MODE, step, w, it); w += gridDim.x) {
+    for (long long w = blockIdx.x;
+         CLS == ALLT ? get_item(g, b, MODE, step, w, it) : get_citem(g, b, MODE, step, CLS == BND, w, it);
+         w += gridDim.x) {
         const int s = it.s, z0 = it.z0, x0 = it.x0, ya = it.ya, yb = it.yb;
         const int ylast = yb + N - 1;
+        const bool zb = CLS == BND && band_z(g, z0), xb = CLS == BND && band_x(g, x0);
+        if (CLS == BND) load_tabs(g, z0, x0, tb);   // published by the barrier after the first waits
+        // band extras of a core slot (adjoint: the chi tiles in the v_z / v_x geometries too)
+        const unsigned cbytes = CBYTES + (zb ? CORE * 4u + (MODE == ADJ ? ZW * TX * 4u : 0u) : 0u) +
+                                (xb ? CORE * 4u + (MODE == ADJ ? TZ * Lay::XR * 4u : 0u) : 0u);
+        auto issue_core = [&](int yy) {
+            const int k = (yy - ya) % SC;
+            float *cs = cbase + k * Lay::CSLOT;
+            mbar_expect(&cbar[k], cbytes);
+            tma4(cs, &tm_pc, z0, x0, yy, s, &cbar[k]);
+            tma4(cs + CORE, &tm_K, z0, x0, yy, 0, &cbar[k]);
+            if (MODE == REC) tma4(cs + 2 * CORE, &tm_lp, z0, x0, yy, s, &cbar[k]);
+            if (CLS == BND) {
+                if (zb) {
+                    if (MODE == ADJ) tma4(cs + Lay::E_HZ, &tm_czh, z0 - 4, x0, yy, s, &cbar[k]);
+                    tma4(cs + Lay::E_CZ, &tm_pzc, z0, x0, yy, s, &cbar[k]);
+                }
+                if (xb) {
+                    if (MODE == ADJ) tma4(cs + Lay::E_HX, &tm_cxh, z0, x0 - N, yy, s, &cbar[k]);
+                    tma4(cs + Lay::E_CX, &tm_pxc, z0, x0, yy, s, &cbar[k]);
+                }
+            }
+        };
         const int oz = z0 + 4 * tzi, ox = x0 + txi;
         const bool mem = oz < g.ne[0] && ox < g.ne[1];
         const long long sh = (long long)s * g.ntot;
@@ -434,14 +549,7 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
                 tma4(slot + Lay::X_OFF, &tm_vx, z0, x0 - N, y, s, &bar[k]);
                 tma4(slot + Lay::Y_OFF, &tm_vy, z0, x0, y, s, &bar[k]);
             }
-            for (int y = ya; y <= cr.issued; y++) {
-                const int k = (y - ya) % SC;
-                float *cs = cbase + k * Lay::CSLOT;
-                mbar_expect(&cbar[k], CBYTES);
-                tma4(cs, &tm_pc, z0, x0, y, s, &cbar[k]);
-                tma4(cs + CORE, &tm_K, z0, x0, y, 0, &cbar[k]);
-                if (MODE == REC) tma4(cs + 2 * CORE, &tm_lp, z0, x0, y, s, &cbar[k]);
-            }
+            for (int y = ya; y <= cr.issued; y++) issue_core(y);
         }
         bool ok = true;
 #pragma unroll
@@ -467,7 +575,8 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
         bool zxb[4];
 #pragma unroll
         for (int r = 0; r < 4; r++)
-            zxb[r] = oz + r < g.nb + N || oz + r >= g.ne[0] - g.nb - N - 1 || ox < g.nb + N || ox >= g.ne[1] - g.nb - N - 1;
+            zxb[r] = CLS == ALLT && (oz + r < g.nb + N || oz + r >= g.ne[0] - g.nb - N - 1 || ox < g.nb + N ||
+                                     ox >= g.ne[1] - g.nb - N - 1);
         if (__syncthreads_or(!ok)) goto timeout;
 
         {
@@ -505,12 +614,14 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
 #endif
             put(q[((2 * N - 1) + kq) % (2 * N)], lds4(sm + ((y + N - 1 - ya) % S) * Lay::SLOT + Lay::Y_OFF + own));
             const float *slot = sm + ((y - ya) % S) * Lay::SLOT;
-            const float *cs = cbase + ((y - ya) % SC) * Lay::CSLOT + own;
+            const float *cslot = cbase + ((y - ya) % SC) * Lay::CSLOT;   // this plane's core slot
+            const float *cs = cslot + own;
             const bool act = mem && mx && my;
             float pv[4], Kv[4];
             put(pv, lds4(cs));
             put(Kv, lds4(cs + CORE));
             float div[4];
+            const bool bact = CLS == BND && act;     // band tile, quad column inside the box
             // ---- z ----
             {
                 float W[12];
@@ -521,12 +632,36 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
                     W[4] = a1.x; W[5] = a1.y; W[6] = a1.z; W[7] = a1.w;
                     W[8] = a2.x; W[9] = a2.y; W[10] = a2.z; W[11] = a2.w;
                 }
+                if (MODE == ADJ && CLS == BND && zb && (oz - 4 < g.nb || oz + 7 >= g.ne[0] - g.nb - 1)) {
+                    // transposed CPML operand over the v_z window: lv + Av (lv + chi) (Av = 0 off the slab)
+                    const float *ch = cslot + Lay::E_HZ + txi * ZW + 4 * tzi;
+#pragma unroll
+                    for (int i = 0; i < 12; i++) W[i] += tb.z[2][oz - z0 + 4 + i] * (W[i] + ch[i]);
+                }
 #pragma unroll
                 for (int r = 0; r < 4; r++) {
                     float d = 0.f;
 #pragma unroll
                     for (int l = 1; l <= N; l++) d += g.c[0][l - 1] * (W[4 + r + l - 1] - W[4 + r - l]);
                     div[r] = d;
+                }
+                if (bact && zb && zquad_slab(g, oz)) {
+                    // z memory variable at the quad's slab nodes: forward psi <- Bp psi + Ap D (added);
+                    // adjoint phi <- Bp (phi + lp before this step)
+                    float mz4[4];
+                    put(mz4, lds4(cslot + Lay::E_CZ + own));
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        const int t = oz - z0 + 8 + r;
+                        if (!(mz[r] && slab_at(g, 0, oz + r))) continue;
+                        if (MODE == FWD) {
+                            mz4[r] = tb.z[1][t] * mz4[r] + tb.z[0][t] * div[r];
+                            div[r] += mz4[r];
+                        } else {
+                            mz4[r] = tb.z[1][t] * (mz4[r] + pv[r]);
+                        }
+                    }
+                    stg4(f.psiv[0] + sh + gidx(g, oz, ox, y), mz4);
                 }
             }
             // ---- x ----
@@ -537,6 +672,19 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
                     put(Xr[N + l - 1], lds4(slot + Lay::X_OFF + (txi + N + l - 1) * TZ + 4 * tzi));
                     put(Xr[N - l], lds4(slot + Lay::X_OFF + (txi + N - l) * TZ + 4 * tzi));
                 }
+                if (MODE == ADJ && CLS == BND && xb) {
+                    // transposed CPML operand at the taps x - N + t (Av = 0 off the slab)
+#pragma unroll
+                    for (int t = 0; t < 2 * N; t++) {
+                        const float A = tb.x[2][txi + t - N + 8];
+                        if (A != 0.f) {
+                            float ch[4];
+                            put(ch, lds4(cslot + Lay::E_HX + (txi + t) * TZ + 4 * tzi));
+#pragma unroll
+                            for (int r = 0; r < 4; r++) Xr[t][r] += A * (Xr[t][r] + ch[r]);
+                        }
+                    }
+                }
                 float D[4];
 #pragma unroll
                 for (int r = 0; r < 4; r++) {
@@ -544,6 +692,22 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
 #pragma unroll
                     for (int l = 1; l <= N; l++) d += g.c[1][l - 1] * (Xr[N + l - 1][r] - Xr[N - l][r]);
                     D[r] = d;
+                }
+                if (bact && xb && ox < g.ne[1] && slab_at(g, 1, ox)) {
+                    float mx4[4];
+                    put(mx4, lds4(cslot + Lay::E_CX + own));
+                    const int t = txi + 8;
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        if (!mz[r]) continue;
+                        if (MODE == FWD) {
+                            mx4[r] = tb.x[1][t] * mx4[r] + tb.x[0][t] * D[r];
+                            D[r] += mx4[r];
+                        } else {
+                            mx4[r] = tb.x[1][t] * (mx4[r] + pv[r]);
+                        }
+                    }
+                    stg4(f.psiv[1] + sh + gidx(g, oz, ox, y), mx4);
                 }
 #pragma unroll
                 for (int r = 0; r < 4; r++) div[r] += D[r];
@@ -636,15 +800,7 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
                     tma4(sl + Lay::X_OFF, &tm_vx, z0, x0 - N, yn, s, &bar[k]);
                     tma4(sl + Lay::Y_OFF, &tm_vy, z0, x0, yn, s, &bar[k]);
                 }
-                if (cr.issued < yb) {
-                    const int yn = cr.issued + 1;
-                    const int k = (yn - ya) % SC;
-                    float *c2 = cbase + k * Lay::CSLOT;
-                    mbar_expect(&cbar[k], CBYTES);
-                    tma4(c2, &tm_pc, z0, x0, yn, s, &cbar[k]);
-                    tma4(c2 + CORE, &tm_K, z0, x0, yn, 0, &cbar[k]);
-                    if (MODE == REC) tma4(c2 + 2 * CORE, &tm_lp, z0, x0, yn, s, &cbar[k]);
-                }
+                if (cr.issued < yb) issue_core(cr.issued + 1);
             }
             if (hr.issued < ylast) hr.issued++;
             if (cr.issued < yb) cr.issued++;
@@ -742,26 +898,56 @@ template <class K> int grid_for(K kernel, int smem)
     return std::max(1, per) * std::max(1, sms);
 }
 
-template <int N, int MODE>
+template <int N, int MODE, int CLS>
 void run_v(const LaunchCtx &lc, const Maps3 &m, const Grid &g, const Batch &b, Fields f, int step, unsigned *err)
 {
-    constexpr int smem = s3::VLay<N>::SMEM;
-    static const int grid = grid_for(s3::k3_v<N, MODE>, smem);
-    s3::k3_v<N, MODE><<<grid, s3::NTHR, smem, static_cast<cudaStream_t>(lc.stream)>>>(
-        m.p_halo, m.rho_v, m.vz_core, m.vx_core, m.vy_core, g, b, f, step, err);
+    constexpr int smem = s3::VLay<N, CLS>::SMEM;
+    static const int grid = grid_for(s3::k3_v<N, MODE, CLS>, smem);
+    s3::k3_v<N, MODE, CLS><<<grid, s3::NTHR, smem, static_cast<cudaStream_t>(lc.stream)>>>(
+        m.p_halo, m.rho_v, m.vz_core, m.vx_core, m.vy_core, m.pz_halo, m.px_halo, m.cz_core, m.cx_core, g, b, f,
+        step, err);
     ++*lc.launches;
 }
 
-template <int N, int MODE>
+template <int N, int MODE, int CLS>
 void run_p(const LaunchCtx &lc, const Maps3 &m, const Maps3 *lpm, const Grid &g, const Batch &b, Fields f, int step,
            unsigned *err, float *acc, int img_mode, const float *stf, float src_scale)
 {
-    constexpr int smem = s3::PLay<N>::SMEM;
-    static const int grid = grid_for(s3::k3_p<N, MODE>, smem);
-    s3::k3_p<N, MODE><<<grid, s3::NTHR, smem, static_cast<cudaStream_t>(lc.stream)>>>(
-        m.vz_halo, m.vx_halo, m.vy_core, m.p_core, m.K_core, lpm ? lpm->p_core : m.p_core, g, b, f, step, err, acc,
-        img_mode, stf, src_scale);
+    constexpr int smem = s3::PLay<N, CLS>::SMEM;
+    static const int grid = grid_for(s3::k3_p<N, MODE, CLS>, smem);
+    s3::k3_p<N, MODE, CLS><<<grid, s3::NTHR, smem, static_cast<cudaStream_t>(lc.stream)>>>(
+        m.vz_halo, m.vx_halo, m.vy_core, m.p_core, m.K_core, lpm ? lpm->p_core : m.p_core, m.cz_vhalo, m.cx_vhalo,
+        m.pz_core, m.px_core, g, b, f, step, err, acc, img_mode, stf, src_scale);
     ++*lc.launches;
+}
+
+// One forward / adjoint stencil half-step: every tile column in one launch
+// (inl = false: the z / x CPML terms come from the band kernels), or the
+// interior columns and then the CPML-band columns with the terms inline.
+// The two classes update disjoint nodes and, within a half-step, read only
+// what the other does not write.
+template <int N, int MODE>
+void run_v_cls(const LaunchCtx &lc, const Maps3 &m, const Grid &g, const Batch &b, Fields f, int step,
+               unsigned *err, bool inl)
+{
+    if (!inl) {
+        run_v<N, MODE, s3::ALLT>(lc, m, g, b, f, step, err);
+        return;
+    }
+    run_v<N, MODE, s3::BND>(lc, m, g, b, f, step, err);
+    run_v<N, MODE, s3::INT>(lc, m, g, b, f, step, err);
+}
+
+template <int N, int MODE>
+void run_p_cls(const LaunchCtx &lc, const Maps3 &m, const Maps3 *lpm, const Grid &g, const Batch &b, Fields f,
+               int step, unsigned *err, float *acc, int img_mode, const float *stf, float src_scale, bool inl)
+{
+    if (!inl) {
+        run_p<N, MODE, s3::ALLT>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
+        return;
+    }
+    run_p<N, MODE, s3::BND>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
+    run_p<N, MODE, s3::INT>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
 }
 
 }  // namespace
@@ -785,44 +971,60 @@ bool stencil3d_supported(const Grid &g)
     return g.ndim == 3 && (g.N == 2 || g.N == 4) && g.ntot < (1LL << 31) && encoder() != nullptr;
 }
 
-bool make_maps3(Maps3 &m, const Grid &g, const Fields &f, int nshot)
+bool make_maps3(Maps3 &m, const Grid &g, const Fields &f, int nshot, bool fullmem)
 {
     const int R = s3::TX + 2 * g.N - 1;
-    return make_map(&m.p_halo, g, f.p, nshot, s3::ZW, R) && make_map(&m.p_core, g, f.p, nshot, s3::TZ, s3::TX) &&
-           make_map(&m.vz_core, g, f.v[0], nshot, s3::TZ, s3::TX) &&
-           make_map(&m.vx_core, g, f.v[1], nshot, s3::TZ, s3::TX) &&
-           make_map(&m.vy_core, g, f.v[2], nshot, s3::TZ, s3::TX) &&
-           make_map(&m.vz_halo, g, f.v[0], nshot, s3::ZW, s3::TX) &&
-           make_map(&m.vx_halo, g, f.v[1], nshot, s3::TZ, R) &&
-           make_map(&m.rho_v, g, g.rho, 1, 36, s3::TX + 1) && make_map(&m.K_core, g, g.K, 1, s3::TZ, s3::TX);
+    bool ok = make_map(&m.p_halo, g, f.p, nshot, s3::ZW, R) && make_map(&m.p_core, g, f.p, nshot, s3::TZ, s3::TX) &&
+              make_map(&m.vz_core, g, f.v[0], nshot, s3::TZ, s3::TX) &&
+              make_map(&m.vx_core, g, f.v[1], nshot, s3::TZ, s3::TX) &&
+              make_map(&m.vy_core, g, f.v[2], nshot, s3::TZ, s3::TX) &&
+              make_map(&m.vz_halo, g, f.v[0], nshot, s3::ZW, s3::TX) &&
+              make_map(&m.vx_halo, g, f.v[1], nshot, s3::TZ, R) &&
+              make_map(&m.rho_v, g, g.rho, 1, 36, s3::TX + 1) && make_map(&m.K_core, g, g.K, 1, s3::TZ, s3::TX);
+    if (!ok) return false;
+    if (!fullmem) {
+        // compressed CPML slabs: the band maps are never read (the band kernels apply the terms)
+        m.pz_halo = m.px_halo = m.p_halo;
+        m.cz_core = m.cx_core = m.pz_core = m.px_core = m.p_core;
+        m.cz_vhalo = m.vz_halo;
+        m.cx_vhalo = m.vx_halo;
+        return true;
+    }
+    return make_map(&m.pz_halo, g, f.psiv[0], nshot, s3::ZW, R) && make_map(&m.px_halo, g, f.psiv[1], nshot, s3::ZW, R) &&
+           make_map(&m.cz_core, g, f.psip[0], nshot, s3::TZ, s3::TX) &&
+           make_map(&m.cx_core, g, f.psip[1], nshot, s3::TZ, s3::TX) &&
+           make_map(&m.cz_vhalo, g, f.psip[0], nshot, s3::ZW, s3::TX) &&
+           make_map(&m.cx_vhalo, g, f.psip[1], nshot, s3::TZ, R) &&
+           make_map(&m.pz_core, g, f.psiv[0], nshot, s3::TZ, s3::TX) &&
+           make_map(&m.px_core, g, f.psiv[1], nshot, s3::TZ, s3::TX);
 }
 
 void launch3_v(const LaunchCtx &lc, const Maps3 &m, const Grid &g, const Batch &b, Fields f, int step, int mode,
-               unsigned *err)
+               unsigned *err, bool inl)
 {
     // the adjoint's interior update is the forward scheme; only its box differs
     if (g.N == 2) {
-        if (mode == 0) run_v<2, 0>(lc, m, g, b, f, step, err);
-        else if (mode == 1) run_v<2, 1>(lc, m, g, b, f, step, err);
-        else run_v<2, 2>(lc, m, g, b, f, step, err);
+        if (mode == 0) run_v_cls<2, 0>(lc, m, g, b, f, step, err, inl);
+        else if (mode == 1) run_v_cls<2, 1>(lc, m, g, b, f, step, err, inl);
+        else run_v<2, 2, s3::ALLT>(lc, m, g, b, f, step, err);
     } else {
-        if (mode == 0) run_v<4, 0>(lc, m, g, b, f, step, err);
-        else if (mode == 1) run_v<4, 1>(lc, m, g, b, f, step, err);
-        else run_v<4, 2>(lc, m, g, b, f, step, err);
+        if (mode == 0) run_v_cls<4, 0>(lc, m, g, b, f, step, err, inl);
+        else if (mode == 1) run_v_cls<4, 1>(lc, m, g, b, f, step, err, inl);
+        else run_v<4, 2, s3::ALLT>(lc, m, g, b, f, step, err);
     }
 }
 
 void launch3_p(const LaunchCtx &lc, const Maps3 &m, const Maps3 *lpm, const Grid &g, const Batch &b, Fields f,
-               int step, int mode, unsigned *err, float *acc, int img_mode, const float *stf, float src_scale)
+               int step, int mode, unsigned *err, float *acc, int img_mode, const float *stf, float src_scale, bool inl)
 {
     if (g.N == 2) {
-        if (mode == 0) run_p<2, 0>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
-        else if (mode == 1) run_p<2, 1>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
-        else run_p<2, 2>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
+        if (mode == 0) run_p_cls<2, 0>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale, inl);
+        else if (mode == 1) run_p_cls<2, 1>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale, inl);
+        else run_p<2, 2, s3::ALLT>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
     } else {
-        if (mode == 0) run_p<4, 0>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
-        else if (mode == 1) run_p<4, 1>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
-        else run_p<4, 2>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
+        if (mode == 0) run_p_cls<4, 0>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale, inl);
+        else if (mode == 1) run_p_cls<4, 1>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale, inl);
+        else run_p<4, 2, s3::ALLT>(lc, m, lpm, g, b, f, step, err, acc, img_mode, stf, src_scale);
     }
 }
 
