@@ -65,18 +65,21 @@ extern "C" {
 #define SMI_ERR_CUDA (-7)         /* a CUDA runtime call failed */
 #define SMI_ERR_UNSUPPORTED (-8)  /* a size outside this build (boundary bands of a step >= 2^31 values) */
 
-/* Kernel family (smi_opts.kernels). */
+/* Kernel family (smi_opts.kernels).  Every family computes the same scheme;
+ * results agree to FP32 rounding. */
 #define SMI_KERNELS_AUTO 0        /* the fastest measured kernels that support the problem: in 3D the two-pass
-                                     tile kernels (a velocity pass, then a pressure pass, z / x CPML terms in
-                                     band kernels), in 2D the 2D tile kernels */
+                                     tile kernels (a velocity pass, then a pressure pass) with the z / x CPML
+                                     terms in band kernels over the slabs, in 2D the 2D tile kernels */
 #define SMI_KERNELS_GENERIC 1     /* the generic grid-stride kernels (CPML inline, 64-bit indexing) that
                                      serve 3D fields of 2^31 points or more and smi_forward_noalloc; for
                                      tests that check them against the oracle on small problems */
-#define SMI_KERNELS_TWOPASS 2     /* 3D: the two-pass tile kernels (what AUTO runs) */
+#define SMI_KERNELS_TWOPASS 2     /* 3D: the two-pass tile kernels with the CPML band kernels (what AUTO runs) */
 #define SMI_KERNELS_FUSED 3       /* 3D forward and adjoint steps: the single-pass kernel (velocity and pressure
                                      in one pass, CPML of all axes inline, state double buffered); no free
-                                     surface (falls back to two-pass).  Same results to FP32 rounding;
-                                     measured slower than two-pass on GB300 (instruction issue bound) */
+                                     surface (falls back to two-pass).  Measured slower than AUTO on GB300 */
+#define SMI_KERNELS_INLINE 4      /* 3D forward and adjoint steps: the two-pass tile kernels launched as an
+                                     interior and a CPML-band tile class, the z / x CPML terms inline in the
+                                     band class (no band kernels).  Measured slower than AUTO on GB300 */
 
 /* Storage precision of the saved boundaries (Sec. 4.2). */
 #define SMI_PREC_F32 0
@@ -134,7 +137,8 @@ typedef struct {
     int img_norm;             /* smi_rtm only: 0 the zero-lag cross-correlation (Eq. rtmimage); 1 each
                                  shot's image divided by its source illumination sum_t p_s^2 + eps,
                                  eps = 1e-3 of the shot's largest illumination (Sec. 2.3) */
-    int kernels;              /* SMI_KERNELS_AUTO (default), _GENERIC, _TWOPASS or _FUSED; else SMI_ERR_ARG */
+    int kernels;              /* SMI_KERNELS_AUTO (default), _GENERIC, _TWOPASS, _FUSED or _INLINE; else
+                                 SMI_ERR_ARG */
 } smi_opts;
 
 /* Per-call measurements, filled for the calling thread's last call.  Index

@@ -182,8 +182,8 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     if (o->dr < 1) return fail(SMI_ERR_ARG, "dr must be >= 1");
     if (o->shell_prec < SMI_PREC_F32 || o->shell_prec > SMI_PREC_BF16)
         return fail(SMI_ERR_ARG, "shell_prec must be SMI_PREC_F32, F16 or BF16");
-    if (o->kernels < SMI_KERNELS_AUTO || o->kernels > SMI_KERNELS_FUSED)
-        return fail(SMI_ERR_ARG, "kernels must be SMI_KERNELS_AUTO, _GENERIC, _TWOPASS or _FUSED");
+    if (o->kernels < SMI_KERNELS_AUTO || o->kernels > SMI_KERNELS_INLINE)
+        return fail(SMI_ERR_ARG, "kernels must be SMI_KERNELS_AUTO, _GENERIC, _TWOPASS, _FUSED or _INLINE");
     const int N = o->order / 2;
     if (o->nb < N) return fail(SMI_ERR_ARG, "nb must be >= order/2");
     if (!m->vp || !m->rho) return fail(SMI_ERR_ARG, "model arrays are null");
@@ -241,7 +241,7 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     for (int a = 0; a < 3; a++)
         for (int l = 0; l < kMaxHalf; l++) g.c[a][l] = (a < m->ndim && l < N) ? (float)(coef[l] / hh[a]) : 0.0f;
     S.fused = o->kernels == SMI_KERNELS_FUSED && fused3d_supported(g);
-    S.inline3 = !S.fused && o->kernels == SMI_KERNELS_AUTO && stencil3d_supported(g);
+    S.inline3 = o->kernels == SMI_KERNELS_INLINE && stencil3d_supported(g);
     S.fullmem = S.fused || S.inline3;
 
     // inputs on the device

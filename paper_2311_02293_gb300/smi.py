@@ -83,7 +83,7 @@ EXPORTS = ["smi_opts_default", "smi_forward", "smi_rtm", "smi_fwi_gradient", "sm
            "smi_forward_vjp", "smi_server_create", "smi_submit", "smi_wait", "smi_poll", "smi_cancel",
            "smi_server_info", "smi_server_destroy", "smi_fwi_gradient_family", "smi_wait_check",
            "smi_forward_adjoint", "smi_dot", "smi_forward_tape", "smi_tape_vjp", "smi_tape_free"]
-KERNELS = {"auto": 0, "generic": 1, "twopass": 2, "fused": 3}
+KERNELS = {"auto": 0, "generic": 1, "twopass": 2, "fused": 3, "inline": 4}
 
 
 def _load():
@@ -184,7 +184,7 @@ class Problem:
     dr: int = 1             # boundary decimation ratio (Sec. 4.2)
     img_norm: bool = False  # smi_rtm: normalise each shot's image by its source illumination
     freesurf: bool = False  # free surface on the top face (image method, Sec. 2.1)
-    kernels: str = "auto"   # "generic" / "twopass" / "fused": force a kernel family (tests, comparisons)
+    kernels: str = "auto"   # "generic" / "twopass" / "fused" / "inline": force a kernel family (tests)
 
 
 def _geometry(srcs, recs):

@@ -13,8 +13,8 @@ carpet), with nt shortened so that the oracle finishes in a minute or two.
   reconstruction's box shrinks (Sec. 4.1, Algorithm 2 reverse loop).
 - Computing box off: every step covers the whole 340^3 grid, i.e. every tile
   column and y-chunk of the persistent kernels and every piece of the CPML
-  bands (the two-pass kernels), and every interior and CPML-band tile of the
-  single-pass step.
+  bands (the default two-pass kernels), and every interior and CPML-band
+  tile of the single-pass step and of the inline-CPML two-pass kernels.
 
 The wavelet is the workload's Ricker advanced so that its main lobe falls
 inside the shortened time axis (the workloads delay it by 1.2 / fm, longer
@@ -107,7 +107,7 @@ def test_salt_full_grid_gradient_box_off(smi):
     dobs = _observed(w, use_box=False)
     Jr, gr, ur = O.gradient(_oprob(w, use_box=False), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
     assert np.linalg.norm(gr) > 0
-    for kernels in ("auto", "fused"):          # the two-pass kernels and the single-pass step
+    for kernels in ("auto", "fused", "inline"):   # the three 3D kernel families
         J, g = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), _gprob(smi, w, use_box=False, kernels=kernels),
                                     w.srcs, w.recs, _dev(w.stf), _dev(dobs))
         e_g = _rel(g.cpu().numpy(), gr)

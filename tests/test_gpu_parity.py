@@ -60,10 +60,12 @@ SMALL = {
 }
 
 
-# 3D runs the two-pass tile kernels by default; "fused" runs the single-pass
-# step (velocity and pressure in one kernel, CPML inline).
-KERNELS = {"2d_o4_off": ["auto"], "2d_o8_on": ["auto"], "3d_o4_off": ["auto", "fused"],
-           "3d_o8_on": ["auto", "fused"]}
+# 3D runs the two-pass tile kernels with the CPML band kernels by default;
+# "fused" runs the single-pass step (velocity and pressure in one kernel, CPML
+# inline), "inline" the two-pass kernels with the CPML terms in a band-tile
+# class.
+KERNELS = {"2d_o4_off": ["auto"], "2d_o8_on": ["auto"], "3d_o4_off": ["auto", "fused", "inline"],
+           "3d_o8_on": ["auto", "fused", "inline"]}
 CASE_KERNELS = [(c, k) for c in sorted(SMALL) for k in KERNELS[c]]
 
 
@@ -242,7 +244,8 @@ def test_errors_are_reported(smi):
     assert e.value.code == -1
 
 
-@pytest.mark.parametrize("order,kernels", [(4, "auto"), (8, "auto"), (4, "fused"), (8, "fused")])
+@pytest.mark.parametrize("order,kernels", [(4, "auto"), (8, "auto"), (4, "fused"), (8, "fused"), (4, "inline"),
+                                           (8, "inline")])
 def test_long_adjoint_through_cpml_corners_3d(smi, order, kernels):
     """Hundreds of steps with most of the energy inside the CPML slabs and
     their edges/corners: the transposed CPML terms of the adjoint must stay
@@ -334,11 +337,13 @@ def test_16bit_boundaries_3d_against_the_oracle(smi):
 
 @pytest.mark.parametrize("order", [4, 8])
 @pytest.mark.parametrize("use_box", [True, False])
-def test_single_pass_matches_two_pass(smi, order, use_box):
-    """The single-pass 3D step against the two-pass tile kernels on a grid of
-    several tiles in every direction (tile columns in and out of the CPML
-    bands, several y-chunks, two shots in one batch): seismograms, gradient
-    and image agree to FP32 rounding."""
+@pytest.mark.parametrize("other", ["fused", "inline"])
+def test_single_pass_matches_two_pass(smi, order, use_box, other):
+    """The single-pass 3D step and the inline-CPML two-pass kernels against
+    the default two-pass kernels on a grid of several tiles in every
+    direction (tile columns in and out of the CPML bands, several y-chunks,
+    two shots in one batch): seismograms, gradient and image agree to FP32
+    rounding."""
     import torch
     w = S.tiny_3d(nz=70, nx=50, ny=44, nt=160, nb=10, order=order, off_grid=True)
     moved = w.srcs.copy()
@@ -347,7 +352,7 @@ def test_single_pass_matches_two_pass(smi, order, use_box):
     recs = [w.recs[0], w.recs[0][::2].copy()]
     vp, rho, stf = _dev(w.vp), _dev(w.rho), _dev(w.stf)
     out = {}
-    for k in ("fused", "twopass"):
+    for k in (other, "twopass"):
         prob = _gprob(smi, w, use_box=use_box, kernels=k)
         seis = smi.smi_forward(vp, rho, prob, srcs, recs, stf, flat=True)
         dobs = (0.8 * seis).contiguous()
@@ -356,6 +361,6 @@ def test_single_pass_matches_two_pass(smi, order, use_box):
         img = smi.smi_rtm(vp, rho, prob, srcs, recs, stf, dobs)
         out[k] = [t.double().cpu().numpy() for t in (seis, g, img)] + [float(J.item())]
         torch.cuda.synchronize()
-    for a, b in zip(out["fused"][:3], out["twopass"][:3]):
+    for a, b in zip(out[other][:3], out["twopass"][:3]):
         assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
-    assert abs(out["fused"][3] - out["twopass"][3]) <= 1e-5 * abs(out["twopass"][3])
+    assert abs(out[other][3] - out["twopass"][3]) <= 1e-5 * abs(out["twopass"][3])
