@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--other-nt2", type=int, default=3000, help="time steps of the 2D gradient workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nt", type=int, default=2500, help="time steps (full workload: 2500)")
+    ap.add_argument("--table", action="store_true",
+                    help="results table instead: GPU and oracle rates of each workload (several minutes)")
     ap.add_argument("--serve", action="store_true",
                     help="serving mix instead: throughput and p50/p99 latency of the request server")
     ap.add_argument("--serve-requests", type=int, default=48)
@@ -512,6 +514,83 @@ def run_profile_grad2d(args, torch, synth, smi, dev):
                       "kernel_launches": st["kernel_launches"]}), flush=True)
 
 
+def run_table(args):
+    """One JSON line per workload for the results table: the GPU rate of the
+    workload's call (CUDA events after a warm-up call; grid-point updates
+    inside the computing box, and over the full grid) with the dominant
+    stencil class's roofline fraction, and the FP64 oracle's per-step rate on
+    all of this host's cores and on one core (a few time steps of one shot
+    with the box off, set-up and each loop's first step excluded)."""
+    import torch
+    from oracle import oracle as O
+    from paper_2311_02293_gb300 import build, synth
+    if not os.path.exists(os.path.join(ROOT, "paper_2311_02293_gb300", "libsmi.so")):
+        build.build()
+    from paper_2311_02293_gb300 import smi
+    dev = torch.device("cuda:0")
+    peak = measured_peaks()[0]
+
+    def oracle_rate(w, nsteps, nthreads):
+        prob = O.Problem(w.n, w.d, nsteps, w.dt, order=w.order, nb=w.nb, fm=w.fm, use_box=False, nthreads=nthreads)
+        phase = np.zeros(4)
+        O.gradient(prob, w.vp, w.rho, w.stf[:nsteps], w.srcs[0], w.recs[0], np.zeros((nsteps, len(w.recs[0]))),
+                   mode="rtm", phase_s=phase)
+        ext, phys = float(np.prod([n + 2 * w.nb for n in w.n])), float(np.prod(w.n))
+        k = nsteps - 1
+        return {"gpts": k * (2 * ext + phys) / (phase[0] + phase[1]) / 1e9, "threads": nthreads or O.max_threads(),
+                "steps_timed": k}
+
+    def gpu(call, st_scale=1.0):
+        call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = smi.smi_last_stats()
+        cms, cby = np.array(st["ms"]), np.array(st["bytes"])
+        dom = int(np.argmax(cms))
+        return ms, st, {"class": ["forward", "adjoint", "reconstruction"][dom],
+                        "frac": float(cby[dom] / (cms[dom] / 1e3) / 1e9 / peak)}
+
+    rows = []
+    cases = [("C1 2D forward 201x201 nt1000", synth.two_layer_2d(), "forward", 60, 20),
+             ("C2 2D gradient 301x1001 40 shots nt3000", synth.layered_fault_2d(nt=3000, nshot=40), "gradient", 12, 4),
+             ("C3 3D forward 400x400x200 nt3000", synth.random_smooth_3d(nt=3000), "forward", 3, 2),
+             ("C4 3D RTM 300^3 one shot nt2500", synth.salt_3d(nt=2500).subset([0]), "rtm", 3, 2)]
+    for name, w, kind, ns_all, ns_one in cases:
+        vp, rho, stf = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (w.vp, w.rho, w.stf))
+        line = {"table": name}
+        for shell in (["f32", "f16"] if kind == "rtm" else ["f32"]):
+            prob = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, profile=True, shell_prec=shell)
+            if kind == "forward":
+                call = lambda: smi.smi_forward(vp, rho, prob, w.srcs, w.recs, stf, flat=True)
+                props = 1
+            else:
+                vpt = torch.from_numpy(np.ascontiguousarray(w.vp_true if w.vp_true is not None else w.vp)).to(dev)
+                dobs = smi.smi_forward(vpt, rho, smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb),
+                                       w.srcs, w.recs, stf, flat=True)
+                if kind == "rtm":
+                    call = lambda: smi.smi_rtm(vp, rho, prob, w.srcs, w.recs, stf, dobs)
+                else:
+                    call = lambda: smi.smi_fwi_gradient(vp, rho, prob, w.srcs, w.recs, stf, dobs)
+                props = 3
+            ms, st, roof = gpu(call)
+            ext = float(np.prod([n + 2 * w.nb for n in w.n]))
+            phys = float(np.prod(w.n))
+            full = (ext if props == 1 else 2 * ext + phys) * w.nt * len(w.srcs)
+            line["gpu_" + shell] = {"ms": ms, "gpts": st["point_updates"] / (ms * 1e6), "effective_gpts": full / (ms * 1e6),
+                                    "roofline": roof}
+        line["oracle_all_cores"] = oracle_rate(w, ns_all, 0)
+        line["oracle_one_core"] = oracle_rate(w, ns_one, 1)
+        rows.append(line)
+        print(json.dumps(line), flush=True)
+        del vp, rho, stf
+        torch.cuda.empty_cache()
+
+
 def run_serve(args):
     """Serving mix: one-at-a-time plain FP32 calls vs the request server (FP16
     boundaries, --serve-slots slots) under Poisson arrivals at 1.2x and 0.5x
@@ -559,6 +638,8 @@ if __name__ == "__main__":
     a = parse()
     if a.profile:
         run_profile(a)
+    elif a.table:
+        run_table(a)
     elif a.serve:
         run_serve(a)
     elif a.impl == "reference":

@@ -133,6 +133,7 @@ def test_salt_3d_full_grid_seismograms(smi):
     seis = smi.smi_forward(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs, _dev(w.stf))[0]
     ref = O.forward(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0])
     assert np.linalg.norm(ref) > 0
+    print(f"3D salt 340^3 forward: seismograms {_rel(seis.cpu().numpy(), ref):.2e}")
     assert _rel(seis.cpu().numpy(), ref) <= SEIS_TOL
 
 
@@ -158,4 +159,5 @@ def test_random_3d_full_grid_seismograms(smi):
     seis = smi.smi_forward(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs, _dev(w.stf))[0]
     ref = O.forward(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0])
     assert np.linalg.norm(ref) > 0
+    print(f"3D random 400x400x200 forward: seismograms {_rel(seis.cpu().numpy(), ref):.2e}")
     assert _rel(seis.cpu().numpy(), ref) <= SEIS_TOL

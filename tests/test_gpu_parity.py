@@ -86,6 +86,7 @@ def test_forward_parity_two_layer_2d_full_size(smi):
     seis = smi.smi_forward(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs,
                            _dev(w.stf))[0].cpu().numpy()
     ref = O.forward(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0])
+    print(f"2D two-layer 201x201 forward: seismograms {_rel(seis, ref):.2e}")
     assert _rel(seis, ref) <= SEIS_TOL
 
 
@@ -218,6 +219,8 @@ def test_gradient_parity_layered_fault_2d_full_grid(smi):
     J, g = smi.smi_fwi_gradient(_dev(w.vp), _dev(w.rho), _gprob(smi, w), w.srcs, w.recs,
                                 _dev(w.stf), _dev(dobs))
     Jr, gr, ur = O.gradient(_oprob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
+    print(f"2D layered-fault 301x1001 gradient: {_rel(g.cpu().numpy(), gr):.2e}, "
+          f"misfit {abs(float(J.item()) - Jr) / Jr:.2e}")
     assert _misfit_ok(float(J.item()), Jr, ur)
     assert _rel(g.cpu().numpy(), gr) <= IMG_TOL
 
