@@ -63,7 +63,7 @@ extern "C" {
 #define SMI_ERR_UNSTABLE (-5)     /* a non-finite value appeared */
 #define SMI_ERR_TIMEOUT (-6)      /* a bounded device wait gave up */
 #define SMI_ERR_CUDA (-7)         /* a CUDA runtime call failed */
-#define SMI_ERR_UNSUPPORTED (-8)  /* a size outside this build (boundary bands of a step >= 2^31 values) */
+#define SMI_ERR_UNSUPPORTED (-8)  /* a size the library does not support (boundary bands of a step >= 2^31 values) */
 
 /* Kernel family (smi_opts.kernels).  Every family computes the same scheme;
  * results agree to FP32 rounding. */

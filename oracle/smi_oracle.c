@@ -227,6 +227,18 @@ static void grid_free(grid_t *g)
     memset(g, 0, sizeof *g);
 }
 
+#ifdef _OPENMP
+/* The OpenMP thread count the process started with (OMP_NUM_THREADS or the
+ * core count), taken before any call sets one: nthreads = 0 restores it, so
+ * a one-thread call does not leave later calls on one thread. */
+static int default_threads(void)
+{
+    static int n = 0;
+    if (n == 0) n = omp_get_max_threads();
+    return n;
+}
+#endif
+
 /* check_cfl + cpml_init + extend_model (Algorithm 2).  Reading: the model is
  * extended into the layers by copying the nearest physical value. */
 static int grid_init(grid_t *g, const orc_par *par, const double *vp, const double *rho)
@@ -238,7 +250,7 @@ static int grid_init(grid_t *g, const orc_par *par, const double *vp, const doub
     if (par->periodic && par->nb != 0) return ORC_ERR_ARG;
     if (par->freesurf && (par->periodic || par->nb < par->order / 2)) return ORC_ERR_ARG;
 #ifdef _OPENMP
-    if (par->nthreads > 0) omp_set_num_threads(par->nthreads);
+    omp_set_num_threads(par->nthreads > 0 ? par->nthreads : default_threads());
 #endif
     g->ndim = par->ndim;
     g->N = par->order / 2;
@@ -1412,7 +1424,7 @@ long orc_band_count(const orc_par *par, const double *vp, const double *rho)
 int orc_max_threads(void)
 {
 #ifdef _OPENMP
-    return omp_get_max_threads();
+    return default_threads();
 #else
     return 1;
 #endif

@@ -5,8 +5,16 @@
 // "same solver" form, Sec. 2.2 / Eq. adj).
 //
 // Why one pass: a two-pass step writes v and reads it back (56 B a point);
-// here v^{n+1/2} is produced and consumed on chip and every array is read
-// and written once (40 B a point: p, v_z, v_x, v_y, kappa, rho in; p, v out).
+// here v^{n+1/2} is produced and consumed on chip, so the algorithmic traffic
+// is 40 B a point (p, v_z, v_x, v_y, kappa, rho in; p, v out).  In practice
+// p is loaded twice (its halo tiles at its own plane, and 2N-1 planes earlier
+// for the v_y queue) and rho in three geometries, and those re-reads do not
+// all hit in L2: about 50 B a point reach DRAM in interior tiles.
+//
+// Status: an opt-in kernel family (SMI_KERNELS_FUSED).  On GB300 it runs
+// slower than the two-pass kernels with the CPML band kernels: it issues at
+// 35-40 % with 7-10 warps resident (both register queues, the halo
+// recomputation and the CPML work sit on each thread).
 //
 // How: persistent CTAs walk 32 (z) x 16 (x) tile columns times y-chunks of
 // the computing box (Sec. 4.1).  For the p-plane y a CTA computes

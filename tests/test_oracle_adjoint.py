@@ -218,3 +218,18 @@ def test_normalised_image_is_the_image_over_the_forward_illumination():
     ill = np.sum(snaps ** 2, axis=0)
     ref = img / (ill + 1e-3 * ill.max())
     assert np.linalg.norm(nimg - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_gradient_does_not_depend_on_the_thread_count():
+    """The parallel adjoint sweep (chunks of the outermost axis in two
+    colours) gives the one-thread result up to FP64 rounding order, and a
+    one-thread call does not leave later default calls on one thread."""
+    w = S.tiny_3d(order=8, nb=5, nt=25)
+    seis = O.forward(_prob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0])
+    dobs = 0.9 * seis
+    default = O.max_threads()
+    J1, g1, _ = O.gradient(_prob(w, nthreads=1), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
+    assert O.max_threads() == default
+    Jn, gn, _ = O.gradient(_prob(w), w.vp, w.rho, w.stf, w.srcs[0], w.recs[0], dobs)
+    assert abs(Jn - J1) <= 1e-12 * J1
+    assert np.linalg.norm(gn - g1) <= 1e-12 * np.linalg.norm(g1)
