@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-scale", type=float, default=0.5,
                     help="grid sizes and nt of the serving mix relative to the full mix")
-    ap.add_argument("--serve-slots", type=int, default=4, help="concurrent request slots of the server")
+    ap.add_argument("--serve-slots", type=int, default=8, help="concurrent request slots of the server")
     ap.add_argument("--profile", choices=["fwd", "rtm", "family", "grad2d"],
                     help="profiling case instead: one untimed forward call (observed data), then one forward "
                          "or RTM call of a one-shot salt model, printing per-class times")

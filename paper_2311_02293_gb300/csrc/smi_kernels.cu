@@ -30,6 +30,21 @@ constexpr int kThreads = 256;
 constexpr int kCpmlChunk = SMI_CPML_U;     // nodes per thread along x, CPML kernel of the x piece
 constexpr int kCpmlChunkZ = SMI_CPML_UZ;   // nodes per lane along x, CPML kernel of the z piece (adjoint)
 constexpr int kMaxBlocksX = 152 * 16;
+#ifndef SMI_CPML_ZP
+#define SMI_CPML_ZP 1        // z piece: persistent k_cpml_zp (1) or one unit a warp, k_cpml_z (0)
+#endif
+#ifndef SMI_CPML_ZP_MINB
+#define SMI_CPML_ZP_MINB 4   // resident 256-thread blocks of k_cpml_zp (its warps loop: fewer are needed)
+#endif
+#ifndef SMI_CPML_XW
+#define SMI_CPML_XW 1        // x piece: walking k_cpml_xw (1) or one chunk a thread, k_cpml_x (0)
+#endif
+#ifndef SMI_CPML_XW_U
+#define SMI_CPML_XW_U 4      // nodes a chunk of the walk
+#endif
+#ifndef SMI_CPML_XW_MINB
+#define SMI_CPML_XW_MINB 4   // resident 256-thread blocks of k_cpml_xw
+#endif
 #ifndef SMI_CPML_MINB_F
 #define SMI_CPML_MINB_F 4
 #endif
@@ -541,6 +556,71 @@ __device__ __forceinline__ void cpml_chunk(const Grid &g, const Fields &f, const
     }
 }
 
+// x piece, walking: a thread takes one line along x (fixed z index i0 and y
+// index i2) and walks one band of it (blockIdx.y: the low band, then the
+// high band) in chunks of U nodes.  The window of h along x rolls from chunk
+// to chunk: the last 2N - 1 values of one chunk's window open the next, so
+// each h value is loaded once per line (cpml_chunk loads U + 2N - 1 values
+// for every U nodes).  Same arithmetic as cpml_chunk.
+template <int N, int KIND, int U>
+__device__ __forceinline__ void cpml_xwalk(const Grid &g, const Fields &f, const Piece &p, int s, int c0, int cr,
+                                           int seg, const int lo[3], const int hi[3])
+{
+    constexpr int W = 1;
+    constexpr bool VK = KIND == kFV || KIND == kAV;
+    constexpr int O = VK ? 0 : -1;
+    constexpr int NW = U + 2 * N - 1;
+    int i[3];
+    i[0] = iv_map(p.iv[0], c0);
+    i[2] = iv_map(p.iv[2], cr);
+    if (i[0] < lo[0] || i[0] > hi[0] || i[2] < lo[2] || i[2] > hi[2]) return;
+    const int js = max(p.iv[W][2 * seg], lo[W]);
+    const int jend = min(p.iv[W][2 * seg] + p.iv[W][2 * seg + 1] - 1, hi[W]);
+    if (js > jend) return;
+    i[W] = js;
+    const int k0 = gidx32(g, i[0], i[1], i[2]);
+    const CpmlAxis<KIND, W> x(g, f, s, i);
+    float *ps = f.p + (long long)s * g.ntot;
+    const CpmlPhiY py(g, f, s, i, g.px);
+
+    float win[NW];
+#pragma unroll
+    for (int q = 0; q < 2 * N - 1; q++) win[q] = x.h(g, k0, js, js + O - N + 1 + q);
+    for (int j0 = js; j0 <= jend; j0 += U) {
+        // ---- loads: the window's U new values and the chunk's own values ----
+#pragma unroll
+        for (int q = 2 * N - 1; q < NW; q++) win[q] = x.h(g, k0, js, j0 + O - N + 1 + q);
+        CpmlOwn oW[U];
+        float rho0[U], own_p[U], kap[U], phy[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int j = j0 + u, k = k0 + (j - js) * x.st;
+            const bool ok = j <= jend;
+            rho0[u] = (VK && ok) ? g.rho[k] : 1.0f;
+            own_p[u] = (!VK && ok) ? ps[k] : 0.0f;
+            kap[u] = (!VK && ok) ? g.K[k] : 0.0f;
+            phy[u] = (KIND == kAP && ok && py.ph) ? py.ph[(j - js) * py.step] : 0.0f;
+            oW[u] = CpmlOwn{0.0f, 0.0f, 0.0f};
+            if (ok) oW[u] = cpml_own(g, x, j, k, x.slab(g, j));
+        }
+        // ---- compute and store ----
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int j = j0 + u, k = k0 + (j - js) * x.st;
+            if (j > jend) continue;
+            float acc = 0.0f;
+            cpml_apply(g, x, j, k, x.slab(g, j), oW[u], rho0[u], own_p[u], cpml_d<N>(g, W, win + u), acc);
+            if (KIND == kFP) ps[k] = own_p[u] - g.dt * kap[u] * acc;
+            if (KIND == kAP) {
+                if (py.ph) py.ph[(j - js) * py.step] = py.B * (phy[u] + own_p[u]);
+                if (acc != 0.0f) ps[k] = own_p[u] - g.dt * kap[u] * acc;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 2 * N - 1; q++) win[q] = win[q + U];
+    }
+}
+
 // z piece: a warp takes one line segment along z (32 lanes = BW owned nodes
 // plus the 2N - 1 halo nodes of their stencils) times up to U consecutive
 // nodes along x.  Each lane loads h along z at its own position and the z
@@ -587,7 +667,7 @@ __device__ __forceinline__ void cpml_zwarp(const Grid &g, const Fields &f, const
     for (int u = 0; u < U; u++) {
         CpmlAxis<KIND, 0> xu = xz;
         xu.sb += u * g.S;
-        hz[u] = xu.h(g, k0 + u * xw.st, zc, z);
+        hz[u] = j0 + u <= jend ? xu.h(g, k0 + u * xw.st, zc, z) : 0.0f;   // no line past the chunk's end
     }
 #pragma unroll
     for (int q = 0; q < U + 2 * N - 1; q++) win[q] = (zown && wband) ? xw.h(g, k0, j0, j0 + O - N + 1 + q) : 0.0f;
@@ -659,6 +739,23 @@ __global__ void __launch_bounds__(256, cpml_min_blocks(KIND)) k_cpml_x(Grid g, B
     cpml_chunk<N, KIND, kCpmlChunk>(g, f, p, s, c0, cr, blockIdx.y, lo, hi);
 }
 
+// x piece, walking (cpml_xwalk): block = ZB z indices x 256/ZB y indices
+// as in k_cpml_x; blockIdx.y = band (low, high), blockIdx.z = shot.
+template <int N, int KIND>
+__global__ void __launch_bounds__(256, SMI_CPML_XW_MINB) k_cpml_xw(Grid g, Batch b, Fields f, Pieces P, int m)
+{
+    const Piece &p = P.q[1];
+    const int zb = g.ndim == 3 ? 64 : 256;
+    const int nbz = (p.cnt[0] + zb - 1) / zb;
+    const int bz = blockIdx.x % nbz, br = blockIdx.x / nbz;
+    const int c0 = bz * zb + (int)threadIdx.x % zb, cr = br * (256 / zb) + (int)threadIdx.x / zb;
+    if (c0 >= p.cnt[0] || cr >= p.cnt[2] || p.iv[1][2 * blockIdx.y + 1] == 0) return;
+    const int s = blockIdx.z;
+    int lo[3], hi[3];
+    box_at((KIND == kFV || KIND == kFP) ? b.tab_src : b.tab_rec, b.nt1, s, m, lo, hi);
+    cpml_xwalk<N, KIND, SMI_CPML_XW_U>(g, f, p, s, c0, cr, blockIdx.y, lo, hi);
+}
+
 // z piece: 8 warps a block, warp -> (z segment, y index); blockIdx.y =
 // chunk along x, blockIdx.z = shot.
 template <int N, int KIND>
@@ -675,6 +772,123 @@ __global__ void __launch_bounds__(256, cpml_min_blocks(KIND)) k_cpml_z(Grid g, B
     box_at((KIND == kFV || KIND == kFP) ? b.tab_src : b.tab_rec, b.nt1, s, m, lo, hi);
     constexpr int UZ = (KIND == kFV || KIND == kFP) ? 2 * kCpmlChunkZ : kCpmlChunkZ;
     cpml_zwarp<N, KIND, UZ>(g, f, P, p, s, threadIdx.x & 31, zw, cr, blockIdx.y, lo, hi);
+}
+
+// z piece, persistent: blockIdx.y = z warp segment (those of the low band,
+// then those of the high band), blockIdx.z = shot; the warps of a segment
+// walk its units (UZ consecutive x lines at one y, the chunks cpml_zwarp
+// takes) in a strided loop.  What depends on z alone -- the lane's node, its
+// CPML coefficients, slab offsets and box test -- is computed once per warp
+// instead of once per unit.  Units whose x range reaches the x band take
+// cpml_zwarp, which adds the x terms there; the others run the z terms
+// below, the same arithmetic as cpml_apply.
+template <int N, int KIND>
+__global__ void __launch_bounds__(256, SMI_CPML_ZP_MINB) k_cpml_zp(Grid g, Batch b, Fields f, Pieces P, int m)
+{
+    constexpr bool VK = KIND == kFV || KIND == kAV;
+    constexpr bool ADJ = KIND == kAV || KIND == kAP;
+    constexpr int O = VK ? 0 : -1;
+    constexpr int HL = N - 1 - O, HR = N + O, BW = 32 - HL - HR;
+    constexpr int U = ADJ ? kCpmlChunkZ : 2 * kCpmlChunkZ;
+    const Piece &p = P.q[0];
+    const int s = blockIdx.z, lane = threadIdx.x & 31;
+    int lo[3], hi[3];
+    box_at(ADJ ? b.tab_rec : b.tab_src, b.nt1, s, m, lo, hi);
+
+    // ---- per warp: the segment and the lane's node along z ----
+    const int zw = blockIdx.y;
+    const int nz0 = (p.iv[0][1] + BW - 1) / BW;
+    const int zseg = zw < nz0 ? 0 : 1;
+    const int zs = p.iv[0][2 * zseg], ze = min(zs + p.iv[0][2 * zseg + 1] - 1, hi[0]);
+    const int ne = g.ne[0], hib = ne - 2 * g.nb - 1;           // slab index = j, or j - hib in the high slab
+    const int z = zs + (zw - (zseg ? nz0 : 0)) * BW + lane - HL;
+    const bool zown = lane >= HL && lane < 32 - HR && z <= ze && z >= lo[0];
+    const int zc = min(max(z, 0), ne - 1);
+    bool hv = (unsigned)z < (unsigned)ne;                          // h exists at z
+    if (ADJ) hv = hv && (z < g.nb || z >= ne - g.nb - 1);
+    const int hms = z < g.nb ? z : z - hib;
+    const float hca = (ADJ && hv) ? __ldg((KIND == kAV ? g.cpa[0] : g.cva[0]) + z) : 0.0f;
+    const bool sl = zc < g.nb || zc >= ne - g.nb - 1;              // own node in the slab
+    const int oms = zc < g.nb ? zc : zc - hib;
+    const bool up = zc + 1 < ne;
+    const float cb = sl ? (VK ? g.cvb[0][zc] : g.cpb[0][zc]) : 0.0f;
+    const float ca = (!ADJ && sl) ? (VK ? g.cva[0][zc] : g.cpa[0][zc]) : 0.0f;
+
+    const long long so = (long long)s * g.ntot, ms = (long long)s * g.slab_n[0];
+    const float *src = (VK ? f.p : f.v[0]) + so;
+    const float *hmem = (KIND == kAV ? f.psiv[0] : f.psip[0]) + ms;
+    float *mem = (VK ? f.psip[0] : f.psiv[0]) + ms;
+    float *fld = f.v[0] + so;
+    float *ps = f.p + so;
+
+    const int nch = (p.iv[1][1] + U - 1) / U;
+    const int nunit = p.cnt[2] * nch;
+    const int xend = min(p.iv[1][0] + p.iv[1][1] - 1, hi[1]);
+    for (int t = blockIdx.x * 8 + (int)(threadIdx.x >> 5); t < nunit; t += gridDim.x * 8) {   // warp-uniform
+        const int cr = t / nch, ch = t - cr * nch;
+        const int y = iv_map(p.iv[2], cr);
+        if (y < lo[2] || y > hi[2]) continue;
+        const int x0 = p.iv[1][0] + ch * U;
+        if (cpml_in<KIND>(g, P, 1, x0) || cpml_in<KIND>(g, P, 1, x0 + U - 1)) {
+            cpml_zwarp<N, KIND, U>(g, f, P, p, s, lane, zw, cr, ch, lo, hi);
+            continue;
+        }
+        const int kl = gidx32(g, 0, x0, y), sL = g.S * (x0 + g.ne[1] * y);
+        int iz[3] = {zc, x0, y};
+        const CpmlPhiY py(g, f, s, iz, g.px);
+
+        // ---- loads ----
+        float hz[U], rho0[U], rho1[U], fo[U], mo[U], pk[U], kp[U], phy[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int k = kl + u * g.px + zc, mi = sL + u * g.S;
+            const bool ok = zown && x0 + u <= xend && x0 + u >= lo[1];
+            hz[u] = 0.0f;
+            if (hv && x0 + u <= xend) {
+                const int kk = kl + u * g.px + z;
+                hz[u] = ADJ ? hca * (src[kk] + hmem[mi + hms]) : src[kk];
+            }
+            rho0[u] = (VK && ok) ? g.rho[k] : 1.0f;
+            rho1[u] = (VK && ok && up) ? g.rho[k + 1] : 0.0f;
+            fo[u] = (VK && ok) ? fld[k] : 0.0f;
+            mo[u] = (ok && sl) ? mem[mi + oms] : 0.0f;
+            pk[u] = (!VK && ok) ? ps[k] : 0.0f;
+            kp[u] = (!VK && ok) ? g.K[k] : 0.0f;
+            phy[u] = (KIND == kAP && ok && py.ph) ? py.ph[u * py.step] : 0.0f;
+        }
+
+        // ---- compute and store ----
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (!(x0 + u <= xend && x0 + u >= lo[1])) continue;    // warp-uniform
+            float Dz = 0.0f;
+#pragma unroll
+            for (int l = 1; l <= N; l++)
+                Dz += g.c[0][l - 1] * (__shfl_sync(0xffffffffu, hz[u], lane + O + l) -
+                                       __shfl_sync(0xffffffffu, hz[u], lane + O + 1 - l));
+            if (!zown) continue;
+            const int k = kl + u * g.px + zc, mi = sL + u * g.S + oms;
+            if (VK) {
+                const float bb = up ? __fdividef(2.0f, rho0[u] + rho1[u]) : __fdividef(1.0f, rho0[u]);
+                if (KIND == kFV) {
+                    const float psi = cb * mo[u] + ca * Dz;
+                    mem[mi] = psi;
+                    fld[k] = fo[u] - g.dt * bb * psi;
+                } else {
+                    if (sl) mem[mi] = cb * (mo[u] + fo[u]);                // deferred chi update
+                    if (Dz != 0.0f) fld[k] = fo[u] - g.dt * bb * Dz;
+                }
+            } else if (KIND == kFP) {
+                const float psi = cb * mo[u] + ca * Dz;
+                mem[mi] = psi;
+                ps[k] = pk[u] - g.dt * kp[u] * psi;
+            } else {
+                if (sl) mem[mi] = cb * (mo[u] + pk[u]);                    // phi update, lp before this step
+                if (py.ph) py.ph[u * py.step] = py.B * (phy[u] + pk[u]);
+                if (Dz != 0.0f) ps[k] = pk[u] - g.dt * kp[u] * Dz;
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1446,6 +1660,30 @@ Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, in
 
 namespace {
 
+// Persistent z-piece launch: one block column per z warp segment and shot,
+// as many blocks along x as fill the GPU once (at least one unit a warp).
+template <int N, int KIND>
+void zp_launch(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, const Pieces &P, int m)
+{
+    static const int fill = [] {
+        int per = 0, dev = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cpml_zp<N, KIND>, 256, 0);
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        return std::max(1, per) * std::max(1, sms);
+    }();
+    constexpr int BW = 32 - (2 * N - 1);
+    constexpr int U = KIND >= kAV ? kCpmlChunkZ : 2 * kCpmlChunkZ;
+    const Piece &p = P.q[0];
+    const int nseg = (p.iv[0][1] + BW - 1) / BW + (p.iv[0][3] + BW - 1) / BW;
+    const long long nunit = (long long)p.cnt[2] * ((p.iv[1][1] + U - 1) / U);
+    if (nseg == 0 || nunit == 0) return;
+    const long long per_col = (long long)nseg * b.nshot;
+    const long long nblk = std::max(1LL, std::min((fill + per_col - 1) / per_col, (nunit + 7) / 8));
+    k_cpml_zp<N, KIND><<<dim3((unsigned)nblk, nseg, b.nshot), 256, 0, S(lc)>>>(g, b, f, P, m);
+    ++*lc.launches;
+}
+
 template <int N>
 void corr_launch(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, int m, int kind,
                  const int lo[3], const int hi[3])
@@ -1458,11 +1696,23 @@ void corr_launch(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, i
         const Piece &p = P.q[a];
         if (p.blocks == 0 || p.chunks == 0) continue;
         const dim3 grid(p.blocks, p.chunks, b.nshot);
-        if (a == 0) {
+        if (a == 0 && SMI_CPML_ZP) {
+            if (kind == kFV) zp_launch<N, kFV>(lc, g, b, f, P, m);
+            else if (kind == kFP) zp_launch<N, kFP>(lc, g, b, f, P, m);
+            else if (kind == kAV) zp_launch<N, kAV>(lc, g, b, f, P, m);
+            else zp_launch<N, kAP>(lc, g, b, f, P, m);
+            continue;                                     // counts its own launch
+        } else if (a == 0) {
             if (kind == kFV) k_cpml_z<N, kFV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
             else if (kind == kFP) k_cpml_z<N, kFP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
             else if (kind == kAV) k_cpml_z<N, kAV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
             else k_cpml_z<N, kAP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+        } else if (SMI_CPML_XW) {
+            const dim3 gw(p.blocks, 2, b.nshot);
+            if (kind == kFV) k_cpml_xw<N, kFV><<<gw, 256, 0, S(lc)>>>(g, b, f, P, m);
+            else if (kind == kFP) k_cpml_xw<N, kFP><<<gw, 256, 0, S(lc)>>>(g, b, f, P, m);
+            else if (kind == kAV) k_cpml_xw<N, kAV><<<gw, 256, 0, S(lc)>>>(g, b, f, P, m);
+            else k_cpml_xw<N, kAP><<<gw, 256, 0, S(lc)>>>(g, b, f, P, m);
         } else {
             if (kind == kFV) k_cpml_x<N, kFV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
             else if (kind == kFP) k_cpml_x<N, kFP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);

@@ -66,7 +66,7 @@ class Request:
 
 
 class Server:
-    def __init__(self, budget_bytes: int = 0, slots: int = 4):
+    def __init__(self, budget_bytes: int = 0, slots: int = 8):
         self._s = _L.smi_server_create(budget_bytes, slots)
         self._keep = {}
         self._lock = threading.Lock()
@@ -221,7 +221,7 @@ def run_alone(reqs, dev) -> tuple:
     return outs, time.perf_counter() - t0
 
 
-def run_mix(reqs, dev, slots: int = 4, budget: int = 0, rate: float | None = None, seed: int = 7) -> dict:
+def run_mix(reqs, dev, slots: int = 8, budget: int = 0, rate: float | None = None, seed: int = 7) -> dict:
     """Replays reqs through a Server with Poisson arrivals at `rate` requests/s
     (None: all at once).  Returns outputs, latencies and throughput."""
     import torch
