@@ -37,7 +37,7 @@ constexpr int kMaxBlocksX = 152 * 16;
 #define SMI_CPML_ZP_MINB 4   // resident 256-thread blocks of k_cpml_zp (its warps loop: fewer are needed)
 #endif
 #ifndef SMI_CPML_XW
-#define SMI_CPML_XW 1        // x piece: walking k_cpml_xw (1) or one chunk a thread, k_cpml_x (0)
+#define SMI_CPML_XW 1        // adjoint x piece: walking k_cpml_xw (1) or one chunk a thread, k_cpml_x (0)
 #endif
 #ifndef SMI_CPML_XW_U
 #define SMI_CPML_XW_U 4      // nodes a chunk of the walk
@@ -1707,11 +1707,9 @@ void corr_launch(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, i
             else if (kind == kFP) k_cpml_z<N, kFP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
             else if (kind == kAV) k_cpml_z<N, kAV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
             else k_cpml_z<N, kAP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-        } else if (SMI_CPML_XW) {
+        } else if (SMI_CPML_XW && kind >= kAV) {   // measured: the walk pays in the adjoint kinds only
             const dim3 gw(p.blocks, 2, b.nshot);
-            if (kind == kFV) k_cpml_xw<N, kFV><<<gw, 256, 0, S(lc)>>>(g, b, f, P, m);
-            else if (kind == kFP) k_cpml_xw<N, kFP><<<gw, 256, 0, S(lc)>>>(g, b, f, P, m);
-            else if (kind == kAV) k_cpml_xw<N, kAV><<<gw, 256, 0, S(lc)>>>(g, b, f, P, m);
+            if (kind == kAV) k_cpml_xw<N, kAV><<<gw, 256, 0, S(lc)>>>(g, b, f, P, m);
             else k_cpml_xw<N, kAP><<<gw, 256, 0, S(lc)>>>(g, b, f, P, m);
         } else {
             if (kind == kFV) k_cpml_x<N, kFV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
