@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--serve-scale", type=float, default=0.5,
                     help="grid sizes and nt of the serving mix relative to the full mix")
     ap.add_argument("--serve-slots", type=int, default=8, help="concurrent request slots of the server")
+    ap.add_argument("--serve-mix", default="surveys", choices=["surveys", "independent"],
+                    help="requests as shots of seeded surveys (shareable calls) or independent draws")
     ap.add_argument("--profile", choices=["fwd", "rtm", "family", "grad2d"],
                     help="profiling case instead: one untimed forward call (observed data), then one forward "
                          "or RTM call of a one-shot salt model, printing per-class times")
@@ -595,7 +597,10 @@ def run_serve(args):
     """Serving mix: one-at-a-time plain FP32 calls vs the request server (FP16
     boundaries, --serve-slots slots) under Poisson arrivals at 1.2x and 0.5x
     the measured one-at-a-time service rate, and with every request queued at
-    once; `value` is the served gradient shots/s of the saturated run."""
+    once; `value` is the served gradient shots/s of the saturated run.
+    --serve-mix surveys draws the requests as shots of seeded surveys, which
+    the server may merge into shot-batched calls; independent draws every
+    request's own nt, so none can share a call."""
     import torch
     from paper_2311_02293_gb300 import build
     if not os.path.exists(os.path.join(ROOT, "paper_2311_02293_gb300", "libsmi.so")):
@@ -603,8 +608,9 @@ def run_serve(args):
     from paper_2311_02293_gb300 import serve, smi
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
-    reqs = serve.make_mix(args.serve_requests, scale=args.serve_scale, shell="f16")
-    plain = serve.make_mix(args.serve_requests, scale=args.serve_scale, shell="f32")
+    surveys = args.serve_mix == "surveys"
+    reqs = serve.make_mix(args.serve_requests, scale=args.serve_scale, shell="f16", surveys=surveys)
+    plain = serve.make_mix(args.serve_requests, scale=args.serve_scale, shell="f32", surveys=surveys)
     serve._prepare(reqs, dev)
     serve._prepare(plain, dev)
     serve.run_alone(plain[:4], dev)                        # warm-up
@@ -618,14 +624,16 @@ def run_serve(args):
     for name, factor in (("rate_1.2x", 1.2), ("rate_0.5x", 0.5), ("saturated", None)):
         m = serve.run_mix(reqs, dev, slots=args.serve_slots, rate=factor * rate1 if factor else None)
         out[name] = {"requests_per_s": m["requests_per_s"], "gradient_shots_per_s": m["gradient_shots_per_s"],
-                     "p50_s": m["p50_s"], "p99_s": m["p99_s"], "failed": m["failed"], "seconds": m["seconds"]}
+                     "p50_s": m["p50_s"], "p99_s": m["p99_s"], "failed": m["failed"], "seconds": m["seconds"],
+                     "merged_calls": m["merged_calls"], "merged_requests": m["merged_requests"]}
     clk = clocks.stop()
     ngrad = sum(1 for r in plain if r.kind == "gradient")
     kinds = {k: sum(1 for r in reqs if r.kind == k) for k in ("gradient", "forward", "rtm")}
     line = {"metric": "served gradient shots/s (request server, FP16 boundaries)",
             "value": out["saturated"]["gradient_shots_per_s"], "unit": "gradient shots/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"serving_mix_{len(reqs)}req_scale{args.serve_scale}", "kinds": kinds,
+            "config": {"workload": f"serving_mix_{len(reqs)}req_scale{args.serve_scale}", "mix": args.serve_mix,
+                       "kinds": kinds,
                        "slots": args.serve_slots, "arrivals": "poisson", "boundaries": "f16 served, f32 one at a time"},
             "clocks": clk,
             "one_at_a_time_fp32": {"requests_per_s": rate1, "gradient_shots_per_s": ngrad / t_alone,

@@ -139,6 +139,11 @@ typedef struct {
                                  eps = 1e-3 of the shot's largest illumination (Sec. 2.3) */
     int kernels;              /* SMI_KERNELS_AUTO (default), _GENERIC, _TWOPASS, _FUSED or _INLINE; else
                                  SMI_ERR_ARG */
+    int per_shot;             /* 1: smi_rtm and smi_fwi_gradient return each shot's result instead of the sum
+                                 over shots: image / gradient [nshot][n3][n2][n1] and misfit [nshot],
+                                 shot s equal to a call with shot s alone (the shots of a batch share
+                                 launches).  Not with img_norm, the family gradients or the tape calls
+                                 (SMI_ERR_ARG); no effect on smi_forward.  0: sums (default) */
 } smi_opts;
 
 /* Per-call measurements, filled for the calling thread's last call.  Index
@@ -267,6 +272,14 @@ int smi_query(const smi_model *model, const smi_geometry *geom, const smi_wavele
               const smi_opts *opts, int kind, size_t *seis_elems, size_t *image_elems,
               size_t *device_bytes);
 
+/* The device bytes of a call (smi_query's device_bytes, estimated the same
+ * way) from the sizes alone: no device work and no wait on the GPU, for
+ * admission decisions while other work runs.  Checks the arguments
+ * (SMI_ERR_ARG) but not CFL, dispersion or positions: a call that fails
+ * those fails when it runs. */
+int smi_footprint(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                  const smi_opts *opts, int kind, size_t *device_bytes);
+
 /* Computing-box bounds (Sec. 4.1) as the kernels compute them on the
  * device: for shot `shot`, the box around its source (which = 0) or its
  * receivers (which = 1) after n = n0 .. n0+count-1 steps.  lo, hi: host
@@ -304,8 +317,16 @@ int smi_forward_noalloc(const smi_model *model, const smi_geometry *geom,
  * slots (each with its own CUDA stream and host thread) as soon as a slot is
  * free and the request's device footprint (smi_query) fits in the remaining
  * memory budget; admitted requests run concurrently.  Among queued requests
- * the oldest one that fits is admitted first.  A request whose footprint
- * exceeds the whole budget fails at submission with SMI_ERR_NOMEM. */
+ * the oldest one that fits is admitted first.  A request's footprint comes
+ * from smi_footprint (no device work at submission); a request whose
+ * footprint exceeds the whole budget fails at submission with SMI_ERR_NOMEM.
+ * Single-shot requests of one survey -- same kind (forward, RTM without
+ * img_norm, gradient), the same model arrays (vp, rho pointers), wavelet
+ * (stf pointer, nt, dt, fm) and options -- that are queued when a slot admits
+ * the first of them join its call, up to 64 shots while they fit the budget:
+ * one shot-batched call whose shots share every launch, with per-shot results
+ * (opts.per_shot) copied back to each request's own outputs.  Each request's
+ * result equals the same request run alone. */
 typedef struct smi_server smi_server;
 
 typedef struct {
@@ -346,6 +367,9 @@ int smi_cancel(smi_server *s, long long ticket);
 int smi_server_info(smi_server *s, size_t *budget, size_t *in_use, long long *queued,
                     long long *completed, long long *failed);
 /* Finishes running requests, drops queued ones, joins the workers. */
+/* Merged calls the server has made and the requests they carried (each
+ * merged call carries two or more). */
+int smi_server_merges(smi_server *s, long long *calls, long long *requests);
 void smi_server_destroy(smi_server *s);
 
 /* Failure detection (no paper counterpart): exercises the give-up path of

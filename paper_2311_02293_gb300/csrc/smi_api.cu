@@ -109,6 +109,7 @@ struct Setup {
     bool inline3 = false;                  // 3D two-pass tile kernels with the z / x CPML terms inline
     bool fullmem = false;                  // z / x CPML memory variables as full-size arrays (either of the above)
     long long nrec_total = 0;
+    size_t setup_bytes = 0;                // sizes-only set-up: estimated bytes of the set-up arena
     std::vector<int> rec_offset;
     std::vector<Stencil> src_st, rec_st;
     std::vector<int> box_src, box_rec;      // [nshot][6]
@@ -173,7 +174,8 @@ void stencil_extent(const Grid &g, const Stencil &s, int lo[3], int hi[3])
 }
 
 int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wavelet *w,
-                       const smi_opts *o, Arena &ar, cudaStream_t st, long long *launches, Setup &S)
+                       const smi_opts *o, Arena &ar, cudaStream_t st, long long *launches, Setup &S,
+                       bool sizes_only = false)
 {
     if (!m || !geo || !w || !o) return fail(SMI_ERR_ARG, "null argument");
     if (m->ndim != 2 && m->ndim != 3) return fail(SMI_ERR_ARG, "ndim must be 2 or 3");
@@ -243,6 +245,50 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     S.fused = o->kernels == SMI_KERNELS_FUSED && fused3d_supported(g);
     S.inline3 = o->kernels == SMI_KERNELS_INLINE && stencil3d_supported(g);
     S.fullmem = S.fused || S.inline3;
+
+    // boundary bands: v_a on the 2N-1 half nodes straddling each face of the
+    // physical domain, over the physical cross-section, stored every dr-th
+    // step (Sec. 4.2)
+    Bands &bd = S.bands;
+    bd.count = 0;
+    bd.prec = o->shell_prec;
+    bd.nt = S.nsamp;
+    for (int a = 0; a < 3; a++)
+        for (int sd = 0; sd < 2; sd++) {
+            bd.off[a][sd] = bd.count;
+            for (int b = 0; b < 3; b++) {
+                bd.lo[a][sd][b] = g.L[b];
+                bd.hi[a][sd][b] = g.H[b];
+            }
+            if (a >= m->ndim) {
+                bd.hi[a][sd][0] = bd.lo[a][sd][0] - 1;   // empty
+                continue;
+            }
+            if (sd == 0) {
+                bd.lo[a][sd][a] = g.L[a] - N;
+                bd.hi[a][sd][a] = g.L[a] + N - 2;
+            } else {
+                bd.lo[a][sd][a] = g.H[a] - N + 1;
+                bd.hi[a][sd][a] = g.H[a] + N - 1;
+            }
+            long long c = 1;
+            for (int b = 0; b < 3; b++) c *= bd.hi[a][sd][b] - bd.lo[a][sd][b] + 1;
+            bd.count += c;
+        }
+    if (bd.count >= (1LL << 31)) return fail(SMI_ERR_UNSUPPORTED, "boundary bands of one step exceed 2^31 values");
+    if (sizes_only) {
+        // the set-up arena of a call: host inputs copied to the device, the
+        // extended model, CPML tables, stencils and the box tables
+        size_t b = 2 * (size_t)g.ntot * 4 + 64;
+        b += (is_device_ptr(m->vp) ? 0 : (size_t)g.nphys * 4) + (is_device_ptr(m->rho) ? 0 : (size_t)g.nphys * 4);
+        b += is_device_ptr(w->stf) ? 0 : (size_t)w->nt * 4;
+        for (int a = 0; a < m->ndim; a++) b += 16 * (size_t)g.ne[a];
+        b += sizeof(Stencil) * (size_t)(S.nshot + std::max<long long>(1, S.nrec_total));
+        b += 2 * 6 * 4 * (size_t)S.nshot * (S.nt_fwd + 2);
+        S.setup_bytes = b;
+        return SMI_OK;
+    }
+
 
     // inputs on the device
     const size_t nphys = (size_t)g.nphys;
@@ -361,36 +407,6 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
     for (int a = 0; a < m->ndim; a++) dV *= hh[a];
     S.src_scale = w->dt / dV;
 
-    // boundary bands: v_a on the 2N-1 half nodes straddling each face of the
-    // physical domain, over the physical cross-section, stored every dr-th
-    // step (Sec. 4.2)
-    Bands &bd = S.bands;
-    bd.count = 0;
-    bd.prec = o->shell_prec;
-    bd.nt = S.nsamp;
-    for (int a = 0; a < 3; a++)
-        for (int sd = 0; sd < 2; sd++) {
-            bd.off[a][sd] = bd.count;
-            for (int b = 0; b < 3; b++) {
-                bd.lo[a][sd][b] = g.L[b];
-                bd.hi[a][sd][b] = g.H[b];
-            }
-            if (a >= m->ndim) {
-                bd.hi[a][sd][0] = bd.lo[a][sd][0] - 1;   // empty
-                continue;
-            }
-            if (sd == 0) {
-                bd.lo[a][sd][a] = g.L[a] - N;
-                bd.hi[a][sd][a] = g.L[a] + N - 2;
-            } else {
-                bd.lo[a][sd][a] = g.H[a] - N + 1;
-                bd.hi[a][sd][a] = g.H[a] + N - 1;
-            }
-            long long c = 1;
-            for (int b = 0; b < 3; b++) c *= bd.hi[a][sd][b] - bd.lo[a][sd][b] + 1;
-            bd.count += c;
-        }
-    if (bd.count >= (1LL << 31)) return fail(SMI_ERR_UNSUPPORTED, "boundary bands of one step exceed 2^31 values");
     return SMI_OK;
 }
 
@@ -404,7 +420,8 @@ size_t per_shot_bytes(const Setup &S, int kind)
     const int nbuf = S.fused ? 2 : 1;          // the single-pass step reads one state buffer, writes the other
     size_t slabs = 0;
     for (int a = 0; a < g.ndim; a++) slabs += 2 * (size_t)(S.fullmem && a < 2 ? g.ntot : g.slab_n[a]) * 4;
-    const long long maxrec = S.nrec_total;     // upper bound of one shot's receivers
+    long long maxrec = 0;                      // receivers of the largest shot
+    for (int k = 0; k < S.nshot; k++) maxrec = std::max<long long>(maxrec, S.rec_offset[k + 1] - S.rec_offset[k]);
     size_t b = nbuf * (fields + slabs) + (size_t)S.nt * maxrec * 4;
     if (kind != 0) {
         b += nbuf * fields;                                            // adjoint fields
@@ -524,8 +541,13 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         LaunchCtx lc{st, &launches};
         const bool out_seis = kind == 0 || kind == 6;   // the call writes seismograms
         const size_t nseis = (size_t)S.nt * S.nrec_total;
-        const size_t nimg = kind == 5 ? (size_t)S.nt : (size_t)g.nphys;   // floats of img_out
         S.rho_grad = kind == 2 && family > 0;
+        // per-shot results: images / gradients [nshot][nphys], misfits [nshot]
+        const bool per_shot = o->per_shot != 0 && (kind == 1 || kind == 2);
+        if (o->per_shot && kind != 0 && (!per_shot || S.rho_grad || (kind == 1 && S.img_norm)))
+            return fail(SMI_ERR_ARG, "per_shot: smi_rtm without img_norm and smi_fwi_gradient only");
+        const size_t nimg = kind == 5 ? (size_t)S.nt : (size_t)g.nphys * (per_shot ? S.nshot : 1);   // floats of img_out
+        const int nmis = per_shot ? S.nshot : 1;       // misfit values
         if (out_seis && !seis_out) return fail(SMI_ERR_ARG, "seis is null");
         if (!out_seis && !dobs)
             return fail(SMI_ERR_ARG, kind == 3 || kind == 5 || kind == 7 ? "adj_src is null" : "dobs is null");
@@ -537,9 +559,9 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         // outputs and observed data on the device
         float *d_seis_out = nullptr, *d_img = nullptr;
         const float *d_dobs = nullptr;
-        double *d_misfit = ar.get<double>(1);
+        double *d_misfit = ar.get<double>((size_t)nmis);
         if (!d_misfit) return fail(SMI_ERR_NOMEM, "device allocation failed");
-        launch_zero(lc, d_misfit, sizeof(double));
+        launch_zero(lc, d_misfit, sizeof(double) * nmis);
         if (out_seis) {
             d_seis_out = is_device_ptr(seis_out) ? seis_out : ar.get<float>(nseis);
         } else {
@@ -805,7 +827,16 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
             }
 
             // ---- residual, misfit ----
-            if (batch_seis > 0) {
+            if (batch_seis > 0 && per_shot && kind == 2) {
+                // one residual and FP64 sum per shot: the same launches as the shot alone
+                const float *dob = d_dobs + (size_t)S.nt * S.rec_offset[s0];
+                for (int s = 0; s < nb_shot; s++) {
+                    const long long ns = (long long)S.nt * (roff[s + 1] - roff[s]);
+                    if (ns <= 0) continue;
+                    launch_residual(lc, seis + soff[s], dob + soff[s], ns, 0, res + soff[s], partials, npart);
+                    launch_sum_partials(lc, partials, npart, d_misfit + s0 + s);
+                }
+            } else if (batch_seis > 0) {
                 const float *dob = d_dobs + (size_t)S.nt * S.rec_offset[s0];
                 launch_residual(lc, kind == 5 || kind == 7 ? dob : seis, dob, batch_seis, kind == 2 ? 0 : 1, res,
                                 partials, npart);
@@ -917,12 +948,17 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
                 continue;
             }
             launch_nonfinite(lc, acc, g.nphys * nb_shot, d_flag);
-            if (norm) launch_reduce_norm(lc, g, acc, nb_shot, norm_mx, d_img, s0 > 0);
+            if (per_shot)
+                cudaMemcpyAsync(d_img + (size_t)s0 * g.nphys, acc, sizeof(float) * g.nphys * nb_shot,
+                                cudaMemcpyDeviceToDevice, st);
+            else if (norm) launch_reduce_norm(lc, g, acc, nb_shot, norm_mx, d_img, s0 > 0);
             else launch_reduce_shots(lc, g, acc, nb_shot, d_img, s0 > 0);
             // batch buffers are released (stream-ordered) when `ba` goes out of scope
         }
         if (S.rho_grad) launch_finalize_family(lc, g, S.vp, S.rho, d_img, R, family, logp, d_img, d_img2);
-        else if (kind == 2 || kind == 3 || kind == 7) launch_finalize_grad(lc, g.nphys, S.vp, g.dt, d_img);
+        else if (kind == 2 || kind == 3 || kind == 7)
+            for (int s = 0; s < (per_shot ? S.nshot : 1); s++)
+                launch_finalize_grad(lc, g.nphys, S.vp, g.dt, d_img + (size_t)s * g.nphys);
         else if (kind == 5) {
             launch_to_float(lc, d_series, S.nt, d_img);
             launch_nonfinite(lc, d_img, S.nt, d_flag);
@@ -936,7 +972,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
         if (d_img2 && d_img2 != img2_out)
             cudaMemcpyAsync(img2_out, d_img2, (size_t)g.nphys * sizeof(float), cudaMemcpyDeviceToHost, st);
         if (kind == 2 && misfit_out) {
-            cudaMemcpyAsync(misfit_out, d_misfit, sizeof(double),
+            cudaMemcpyAsync(misfit_out, d_misfit, sizeof(double) * nmis,
                             is_device_ptr(misfit_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
         }
         unsigned flag = 0, waitflag = 0;
@@ -1124,7 +1160,8 @@ int smi_query(const smi_model *model, const smi_geometry *geom, const smi_wavele
         rc = validate_and_setup(model, geom, wav, opts, ar, st, &launches, S);
         if (!rc) {
             if (seis_elems) *seis_elems = (size_t)S.nt * S.nrec_total;
-            if (image_elems) *image_elems = (size_t)S.g.nphys;
+            if (image_elems)
+                *image_elems = (size_t)S.g.nphys * (opts->per_shot && (kind == 1 || kind == 2) ? S.nshot : 1);
             if (device_bytes) {
                 int B = S.nshot;
                 if (opts->max_batch > 0) B = std::min(B, opts->max_batch);
@@ -1136,6 +1173,25 @@ int smi_query(const smi_model *model, const smi_geometry *geom, const smi_wavele
     }
     int rc2 = finish_stream(st);
     return rc ? rc : rc2;
+}
+
+int smi_footprint(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,
+                  const smi_opts *opts, int kind, size_t *device_bytes)
+{
+    t_err.clear();
+    if (!opts || !device_bytes) return fail(SMI_ERR_ARG, "null argument");
+    if (kind < 0 || kind > 4) return fail(SMI_ERR_ARG, "kind must be 0 .. 4");
+    Setup S;
+    Arena ar(nullptr);                     // not used: the sizes-only set-up allocates nothing
+    long long launches = 0;
+    const int rc = validate_and_setup(model, geom, wav, opts, ar, nullptr, &launches, S, true);
+    if (rc) return rc;
+    int B = S.nshot;
+    if (opts->max_batch > 0) B = std::min(B, opts->max_batch);
+    S.rho_grad = kind == 4;
+    const size_t extra = kind == 4 ? (size_t)S.g.ndim * S.g.ntot * 4 + (size_t)S.g.nphys * 4 : 0;
+    *device_bytes = S.setup_bytes + extra + (size_t)B * per_shot_bytes(S, kind == 4 ? 2 : kind);
+    return SMI_OK;
 }
 
 int smi_box_table(const smi_model *model, const smi_geometry *geom, const smi_wavelet *wav,

@@ -7,8 +7,13 @@
 // CUDA stream and a host thread, so admitted requests run concurrently on the
 // GPU while later ones wait.  A request that can never fit (footprint above
 // the whole budget) fails with SMI_ERR_NOMEM instead of blocking the queue.
-// This is the GPU counterpart of the paper's batchwise job scheduling
-// (Sec. 4.3) and of its one-process-per-shot parallelism (Sec. 3.2).
+// Single-shot requests that can share one call -- same kind, model arrays,
+// wavelet and options, i.e. shots of one survey -- are taken together when a
+// slot admits the first of them: their shots are concatenated into one
+// shot-batched call (the shots share every launch, blockIdx.z = shot) with
+// per-shot results (opts.per_shot), which are then copied to each request's
+// own outputs.  This is the GPU counterpart of the paper's batchwise job
+// scheduling (Sec. 4.3) and of its one-process-per-shot parallelism (Sec. 3.2).
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -26,6 +31,98 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+constexpr int kMaxMerge = 64;     // shots of one merged call
+
+// A request that may join a merged call: one shot, and a kind with per-shot results.
+bool mergeable(const smi_request &r)
+{
+    return r.geom.nshot == 1 && (r.kind == 0 || r.kind == 2 || (r.kind == 1 && !r.opts.img_norm)) &&
+           !r.opts.per_shot;
+}
+
+// Two requests that one call can run: same kind, model arrays, wavelet and
+// options (the stream aside).
+bool same_call(const smi_request &a, const smi_request &b)
+{
+    const smi_model &p = a.model, &q = b.model;
+    const smi_opts &u = a.opts, &v = b.opts;
+    return a.kind == b.kind && p.ndim == q.ndim && p.n1 == q.n1 && p.n2 == q.n2 && p.n3 == q.n3 && p.d1 == q.d1 &&
+           p.d2 == q.d2 && p.d3 == q.d3 && p.vp == q.vp && p.rho == q.rho && a.wav.nt == b.wav.nt &&
+           a.wav.dt == b.wav.dt && a.wav.fm == b.wav.fm && a.wav.stf == b.wav.stf && u.order == v.order &&
+           u.nb == v.nb && u.freesurf == v.freesurf && u.dr == v.dr && u.use_box == v.use_box &&
+           u.shell_prec == v.shell_prec && u.kaiser_b == v.kaiser_b && u.cpml_R == v.cpml_R &&
+           u.max_batch == v.max_batch && u.profile == v.profile && u.img_norm == v.img_norm &&
+           u.kernels == v.kernels && u.per_shot == v.per_shot;
+}
+
+int run_one(smi_request r, cudaStream_t st)
+{
+    r.opts.stream = st;
+    if (r.kind == 0) return smi_forward(&r.model, &r.geom, &r.wav, &r.opts, r.out);
+    if (r.kind == 1) return smi_rtm(&r.model, &r.geom, &r.wav, &r.opts, r.dobs, r.out);
+    return smi_fwi_gradient(&r.model, &r.geom, &r.wav, &r.opts, r.dobs, r.misfit, r.out);
+}
+
+// Requests of one survey as one shot-batched call: shots concatenated in the
+// requests' order, observed data gathered, per-shot results scattered back.
+int run_merged(const std::vector<smi_request> &rs, cudaStream_t st, std::string &err)
+{
+    const smi_request &r0 = rs[0];
+    const int K = (int)rs.size();
+    std::vector<double> src(3 * (size_t)K), rec;
+    std::vector<int> roff(K + 1, 0);
+    for (int k = 0; k < K; k++) {
+        const smi_geometry &g = rs[k].geom;
+        for (int c = 0; c < 3; c++) src[3 * (size_t)k + c] = g.src[c];
+        const int n = g.rec_offset[1] - g.rec_offset[0];
+        roff[k + 1] = roff[k] + n;
+        rec.insert(rec.end(), g.rec + 3 * (size_t)g.rec_offset[0], g.rec + 3 * (size_t)g.rec_offset[1]);
+    }
+    const smi_geometry geo{K, src.data(), roff.data(), rec.data()};
+    const size_t nt = (size_t)r0.wav.nt;
+    const size_t nphys = (size_t)r0.model.n1 * r0.model.n2 * (r0.model.ndim == 3 ? r0.model.n3 : 1);
+    const size_t nout = r0.kind == 0 ? nt * roff[K] : nphys * K;
+    float *d_dobs = nullptr, *d_out = nullptr;
+    double *d_mis = nullptr;
+    bool ok = cudaMallocAsync(&d_out, nout * sizeof(float), st) == cudaSuccess;
+    if (ok && r0.kind != 0) ok = cudaMallocAsync(&d_dobs, nt * roff[K] * sizeof(float), st) == cudaSuccess;
+    if (ok && r0.kind == 2) ok = cudaMallocAsync(&d_mis, K * sizeof(double), st) == cudaSuccess;
+    int rc = SMI_OK;
+    if (!ok) {
+        rc = SMI_ERR_NOMEM;
+        err = "device allocation of a merged call's buffers failed";
+    }
+    for (int k = 0; !rc && r0.kind != 0 && k < K; k++)
+        cudaMemcpyAsync(d_dobs + nt * roff[k], rs[k].dobs, nt * (roff[k + 1] - roff[k]) * sizeof(float),
+                        cudaMemcpyDefault, st);
+    if (!rc) {
+        smi_opts o = r0.opts;
+        o.stream = st;
+        o.per_shot = 1;
+        if (r0.kind == 0) rc = smi_forward(&r0.model, &geo, &r0.wav, &o, d_out);
+        else if (r0.kind == 1) rc = smi_rtm(&r0.model, &geo, &r0.wav, &o, d_dobs, d_out);
+        else rc = smi_fwi_gradient(&r0.model, &geo, &r0.wav, &o, d_dobs, d_mis, d_out);
+        if (rc) err = smi_last_error();
+    }
+    for (int k = 0; !rc && k < K; k++) {
+        if (r0.kind == 0)
+            cudaMemcpyAsync(rs[k].out, d_out + nt * roff[k], nt * (roff[k + 1] - roff[k]) * sizeof(float),
+                            cudaMemcpyDefault, st);
+        else
+            cudaMemcpyAsync(rs[k].out, d_out + nphys * k, nphys * sizeof(float), cudaMemcpyDefault, st);
+        if (r0.kind == 2 && rs[k].misfit) cudaMemcpyAsync(rs[k].misfit, d_mis + k, sizeof(double), cudaMemcpyDefault, st);
+    }
+    if (d_out) cudaFreeAsync(d_out, st);
+    if (d_dobs) cudaFreeAsync(d_dobs, st);
+    if (d_mis) cudaFreeAsync(d_mis, st);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (!rc && e != cudaSuccess) {
+        rc = SMI_ERR_CUDA;
+        err = cudaGetErrorString(e);
+    }
+    return rc;
+}
 
 struct Job {
     long long ticket;
@@ -51,7 +148,7 @@ struct smi_server {
     long long next_ticket = 1;
     std::vector<std::thread> workers;
     Clock::time_point t0 = Clock::now();
-    long long completed = 0, failed = 0;
+    long long completed = 0, failed = 0, merged_calls = 0, merged_requests = 0;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 
@@ -76,34 +173,59 @@ struct smi_server {
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         for (;;) {
             long long t = -1;
-            Job job;
+            std::vector<long long> group;
+            std::vector<smi_request> reqs;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 cv_work.wait(lk, [&] { return stop || (t = pick()) >= 0; });
                 if (t < 0) break;                      // stopping with nothing runnable
-                Job &j = jobs[t];
-                j.state = 1;
-                j.t_start = now();
-                in_use += j.bytes;
-                job = j;
+                const double t_now = now();
+                auto take = [&](long long u) {
+                    Job &j = jobs[u];
+                    j.state = 1;
+                    j.t_start = t_now;
+                    in_use += j.bytes;
+                    group.push_back(u);
+                    reqs.push_back(j.req);
+                };
+                take(t);
+                // queued shots of the same survey join the call while they fit
+                if (mergeable(reqs[0]))
+                    for (auto it = queue.begin(); it != queue.end() && (int)group.size() < kMaxMerge;) {
+                        const Job &u = jobs[*it];
+                        if (mergeable(u.req) && same_call(reqs[0], u.req) && u.bytes <= budget - in_use) {
+                            take(*it);
+                            it = queue.erase(it);
+                        } else {
+                            ++it;
+                        }
+                    }
+                if (group.size() > 1) {
+                    merged_calls++;
+                    merged_requests += (long long)group.size();
+                }
             }
-            smi_request r = job.req;
-            r.opts.stream = st;
             int rc;
-            if (r.kind == 0) rc = smi_forward(&r.model, &r.geom, &r.wav, &r.opts, r.out);
-            else if (r.kind == 1) rc = smi_rtm(&r.model, &r.geom, &r.wav, &r.opts, r.dobs, r.out);
-            else rc = smi_fwi_gradient(&r.model, &r.geom, &r.wav, &r.opts, r.dobs, r.misfit, r.out);
-            const std::string err = rc ? smi_last_error() : "";
+            std::string err;
+            if (group.size() == 1) {
+                rc = run_one(reqs[0], st);
+                if (rc) err = smi_last_error();
+            } else {
+                rc = run_merged(reqs, st, err);
+            }
             {
                 std::lock_guard<std::mutex> lk(mu);
-                Job &j = jobs[t];
-                j.state = 2;
-                j.status = rc;
-                j.error = err;
-                j.t_end = now();
-                in_use -= j.bytes;
-                if (rc) failed++;
-                else completed++;
+                const double t_now = now();
+                for (long long u : group) {
+                    Job &j = jobs[u];
+                    j.state = 2;
+                    j.status = rc;
+                    j.error = err;
+                    j.t_end = t_now;
+                    in_use -= j.bytes;
+                    if (rc) failed++;
+                    else completed++;
+                }
             }
             cv_done.notify_all();
             cv_work.notify_all();                      // memory freed: others may fit now
@@ -135,7 +257,9 @@ int smi_submit(smi_server *s, const smi_request *req, long long *ticket)
     if (!s || !req || !ticket) return SMI_ERR_ARG;
     if (req->kind < 0 || req->kind > 2) return SMI_ERR_ARG;
     size_t bytes = 0;
-    const int rc = smi_query(&req->model, &req->geom, &req->wav, &req->opts, req->kind, nullptr, nullptr, &bytes);
+    // sizes only: a submission never waits for the GPU (a query's set-up
+    // kernels would queue behind the running requests' kernels)
+    const int rc = smi_footprint(&req->model, &req->geom, &req->wav, &req->opts, req->kind, &bytes);
     std::lock_guard<std::mutex> lk(s->mu);
     const long long t = s->next_ticket++;
     Job &j = s->jobs[t];
@@ -225,6 +349,15 @@ int smi_server_info(smi_server *s, size_t *budget, size_t *in_use, long long *qu
     if (queued) *queued = (long long)s->queue.size();
     if (completed) *completed = s->completed;
     if (failed) *failed = s->failed;
+    return SMI_OK;
+}
+
+int smi_server_merges(smi_server *s, long long *calls, long long *requests)
+{
+    if (!s) return SMI_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (calls) *calls = s->merged_calls;
+    if (requests) *requests = s->merged_requests;
     return SMI_OK;
 }
 

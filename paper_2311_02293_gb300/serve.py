@@ -3,11 +3,13 @@ one GPU through the library's request server (include/smi.h, smi_server_*).
 
 ``Server`` queues requests of any size, dimension and nt; the library admits
 them into worker slots (one CUDA stream each) as slots and device memory
-free up, so their work overlaps on the GPU.  ``make_mix`` draws a seeded
-request mix shaped like the serving workload (70 % 2D single-shot gradient
-jobs, 30 % 3D forward / RTM shots, orders 4 and 8, FP16 boundaries), and
-``run_mix`` replays it with Poisson arrivals and reports throughput and
-p50/p99 latency.
+free up, so their work overlaps on the GPU, and merges queued single-shot
+requests of one survey into one shot-batched call.  ``make_mix`` draws a
+seeded request mix shaped like the serving workload (70 % 2D single-shot
+gradient jobs, 30 % 3D forward / RTM shots, orders 4 and 8, FP16
+boundaries), as shots of seeded surveys or as independent requests, and
+``run_mix`` replays it with Poisson arrivals and reports throughput,
+p50/p99 latency and the merges the server made.
 """
 from __future__ import annotations
 
@@ -47,6 +49,8 @@ _L.smi_cancel.restype = ctypes.c_int
 _L.smi_server_info.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_size_t)] * 2 + \
     [ctypes.POINTER(ctypes.c_longlong)] * 3
 _L.smi_server_info.restype = ctypes.c_int
+_L.smi_server_merges.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_longlong)] * 2
+_L.smi_server_merges.restype = ctypes.c_int
 _L.smi_server_destroy.argtypes = [ctypes.c_void_p]
 _L.smi_server_destroy.restype = None
 
@@ -106,7 +110,10 @@ class Server:
         q, c, f = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
         smi._check(_L.smi_server_info(self._s, ctypes.byref(b), ctypes.byref(u), ctypes.byref(q), ctypes.byref(c),
                                       ctypes.byref(f)))
-        return {"budget": b.value, "in_use": u.value, "queued": q.value, "completed": c.value, "failed": f.value}
+        mc, mr = ctypes.c_longlong(), ctypes.c_longlong()
+        smi._check(_L.smi_server_merges(self._s, ctypes.byref(mc), ctypes.byref(mr)))
+        return {"budget": b.value, "in_use": u.value, "queued": q.value, "completed": c.value, "failed": f.value,
+                "merged_calls": mc.value, "merged_requests": mr.value}
 
     def cancel(self, ticket: int) -> bool:
         return _L.smi_cancel(self._s, ticket) == 0
@@ -133,13 +140,24 @@ def _valid(w, prob) -> bool:
         return False
 
 
-def make_mix(n: int, seed: int = synth.SEED_BASE + 5, scale: float = 1.0, shell: str = "f16") -> list:
+def make_mix(n: int, seed: int = synth.SEED_BASE + 5, scale: float = 1.0, shell: str = "f16",
+             surveys: bool = True, n2d: int = 12, n3d: int = 6) -> list:
     """Seeded request mix: 70 % 2D single-shot gradient jobs (nz 201-401,
     nx 601-1601, nt 1500-4000, 12.5 m, 1 ms, 8 Hz), 30 % 3D forward / RTM
     shots (160^3-320^3, nt 1500-3000, 10 m, 0.8 ms, 10 Hz at order 4 or
     12 Hz at order 8), orders 4/8 equally likely.  Grid sizes and nt are
-    multiplied by `scale`; draws failing CFL or dispersion are redrawn."""
+    multiplied by `scale`; draws failing CFL or dispersion are redrawn.
+
+    surveys=True: each request is one shot of a seeded survey -- n2d 2D
+    surveys (model, nt, order and 40 shot positions) and n3d 3D surveys
+    (model, nt, order and 8 shots) drawn from the ranges above -- so the
+    requests of one survey share model, wavelet and options, as the shots of
+    an FWI or RTM job do, and the server may run them in one call.
+    surveys=False: every request draws its own nt (models from a size-bucket
+    cache), so no two requests can share a call."""
     rng = np.random.default_rng(seed)
+    if surveys:
+        return _survey_mix(n, rng, scale, shell, n2d, n3d)
     cache = {}
     reqs = []
     while len(reqs) < n:
@@ -178,17 +196,62 @@ def make_mix(n: int, seed: int = synth.SEED_BASE + 5, scale: float = 1.0, shell:
     return reqs
 
 
+def _survey_mix(n, rng, scale, shell, n2d, n3d) -> list:
+    """The survey form of make_mix: surveys first, then requests as shots."""
+    s2, s3 = [], []
+    while len(s2) < n2d:
+        order = int(rng.choice([4, 8]))
+        nz = int(rng.integers(201, 402) * scale)
+        nx = int(rng.integers(601, 1602) * scale)
+        nt = int(rng.integers(1500, 4001) * scale)
+        base = synth.layered_fault_2d(nz=nz, nx=nx, nt=nt, nshot=40, order=order,
+                                      seed=synth.SEED_BASE + 50 + len(s2))
+        h = base.d[1]                     # 40 shots on nodes across 5-95 % of the line
+        base.srcs[:, 1] = np.round(np.linspace(0.05, 0.95, 40) * (nx - 1)) * h
+        prob = smi.Problem(base.d, nt, 1e-3, 8.0, order=order, nb=20, shell_prec=shell)
+        if _valid(base.subset([0]), prob) and _valid(base.subset([39]), prob):
+            s2.append((base, order, synth.ricker(nt, 1e-3, 8.0)))
+    while len(s3) < n3d:
+        order = int(rng.choice([4, 8]))
+        n3 = max(int(rng.integers(160, 321) * scale) // 20 * 20, 40)
+        nt = int(rng.integers(1500, 3001) * scale)
+        fm = 10.0 if order == 4 else 12.0
+        base = synth.salt_3d(n=n3, nt=10, nshot=8, seed=synth.SEED_BASE + 60 + len(s3))
+        w = synth.Workload(base.name, base.n, base.d, nt, 8e-4, fm, order, base.vp, base.rho, base.srcs[:1],
+                           base.recs[:1], vp_true=base.vp_true)
+        if _valid(w, smi.Problem(w.d, nt, 8e-4, fm, order=order, nb=20, shell_prec=shell)):
+            s3.append((base, order, nt, fm, synth.ricker(nt, 8e-4, fm)))
+    reqs = []
+    for _ in range(n):
+        if rng.random() < 0.7:
+            base, order, stf = s2[int(rng.integers(0, n2d))]
+            shot = int(rng.integers(0, base.nshot))
+            w = synth.Workload(base.name, base.n, base.d, base.nt, 1e-3, 8.0, order, base.vp, base.rho,
+                               base.srcs[shot:shot + 1], base.recs[shot:shot + 1], vp_true=base.vp_true, stf=stf)
+            kind = "gradient"
+        else:
+            base, order, nt, fm, stf = s3[int(rng.integers(0, n3d))]
+            shot = int(rng.integers(0, base.nshot))
+            w = synth.Workload(base.name, base.n, base.d, nt, 8e-4, fm, order, base.vp, base.rho,
+                               base.srcs[shot:shot + 1], base.recs[shot:shot + 1], vp_true=base.vp_true, stf=stf)
+            kind = "forward" if rng.random() < 0.5 else "rtm"
+        reqs.append(Request(kind, w, smi.Problem(w.d, w.nt, w.dt, w.fm, order=order, nb=20, shell_prec=shell)))
+    return reqs
+
+
 def _prepare(reqs, dev):
     """Device inputs and observed data (forward modelling in the true model)."""
     import torch
-    models = {}
+    models, stfs = {}, {}
     for r in reqs:
         key = id(r.w.vp)
         if key not in models:
             models[key] = (torch.from_numpy(r.w.vp).to(dev), torch.from_numpy(r.w.rho).to(dev),
                            torch.from_numpy(r.w.vp_true if r.w.vp_true is not None else r.w.vp).to(dev))
         r._dev = models[key]
-        r._stf = torch.from_numpy(r.w.stf).to(dev)
+        if id(r.w.stf) not in stfs:       # one device wavelet per survey: its requests may share a call
+            stfs[id(r.w.stf)] = torch.from_numpy(r.w.stf).to(dev)
+        r._stf = stfs[id(r.w.stf)]
         if r.kind != "forward":
             vp_t = r._dev[2]
             plain = smi.Problem(r.prob.d, r.prob.nt, r.prob.dt, r.prob.fm, order=r.prob.order, nb=r.prob.nb)
@@ -256,10 +319,12 @@ def run_mix(reqs, dev, slots: int = 8, budget: int = 0, rate: float | None = Non
             results.append(res)
         th.join()
         elapsed = time.perf_counter() - t0
+        info = srv.info()
     torch.cuda.synchronize()
     ok = [r["status"] == 0 for r in results]
     ngrad = sum(1 for r, o in zip(reqs, ok) if o and r.kind == "gradient")
     return {"outputs": outs, "results": results, "latency_s": lat, "seconds": elapsed,
             "requests_per_s": sum(ok) / elapsed, "gradient_shots_per_s": ngrad / elapsed,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "failed": len(reqs) - sum(ok)}
+            "failed": len(reqs) - sum(ok), "merged_calls": info["merged_calls"],
+            "merged_requests": info["merged_requests"]}

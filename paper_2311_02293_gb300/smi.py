@@ -67,7 +67,8 @@ class smi_opts(ctypes.Structure):
                 ("dr", ctypes.c_int), ("use_box", ctypes.c_int), ("shell_prec", ctypes.c_int),
                 ("kaiser_b", ctypes.c_double), ("cpml_R", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("max_batch", ctypes.c_int),
-                ("profile", ctypes.c_int), ("img_norm", ctypes.c_int), ("kernels", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("img_norm", ctypes.c_int), ("kernels", ctypes.c_int),
+                ("per_shot", ctypes.c_int)]
 
 
 class smi_stats(ctypes.Structure):
@@ -78,10 +79,10 @@ class smi_stats(ctypes.Structure):
 
 
 # C functions exported by libsmi (the names of include/smi.h)
-EXPORTS = ["smi_opts_default", "smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query",
+EXPORTS = ["smi_opts_default", "smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query", "smi_footprint",
            "smi_box_table", "smi_last_stats", "smi_last_error", "smi_version", "smi_forward_noalloc",
            "smi_forward_vjp", "smi_server_create", "smi_submit", "smi_wait", "smi_poll", "smi_cancel",
-           "smi_server_info", "smi_server_destroy", "smi_fwi_gradient_family", "smi_wait_check",
+           "smi_server_info", "smi_server_merges", "smi_server_destroy", "smi_fwi_gradient_family", "smi_wait_check",
            "smi_forward_adjoint", "smi_dot", "smi_forward_tape", "smi_tape_vjp", "smi_tape_free"]
 KERNELS = {"auto": 0, "generic": 1, "twopass": 2, "fused": 3, "inline": 4}
 
@@ -109,11 +110,12 @@ def _load():
     L.smi_tape_free.restype = None
     L.smi_dot.argtypes = [vp, vp, ctypes.c_size_t, P(ctypes.c_double), vp]
     L.smi_query.argtypes = common + [c_int, P(ctypes.c_size_t), P(ctypes.c_size_t), P(ctypes.c_size_t)]
+    L.smi_footprint.argtypes = common + [c_int, P(ctypes.c_size_t)]
     L.smi_box_table.argtypes = common + [c_int, c_int, c_int, c_int, vp, vp]
     L.smi_last_stats.argtypes = [P(smi_stats)]
     L.smi_last_error.restype = ctypes.c_char_p
     L.smi_version.restype = ctypes.c_char_p
-    for name in ("smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query", "smi_box_table",
+    for name in ("smi_forward", "smi_rtm", "smi_fwi_gradient", "smi_query", "smi_footprint", "smi_box_table",
                  "smi_last_stats", "smi_forward_noalloc", "smi_forward_vjp", "smi_fwi_gradient_family",
                  "smi_wait_check", "smi_forward_adjoint", "smi_dot", "smi_forward_tape", "smi_tape_vjp"):
         getattr(L, name).restype = c_int
@@ -185,6 +187,7 @@ class Problem:
     img_norm: bool = False  # smi_rtm: normalise each shot's image by its source illumination
     freesurf: bool = False  # free surface on the top face (image method, Sec. 2.1)
     kernels: str = "auto"   # "generic" / "twopass" / "fused" / "inline": force a kernel family (tests)
+    per_shot: bool = False  # smi_rtm / smi_fwi_gradient: each shot's image / gradient / misfit, not the sum
 
 
 def _geometry(srcs, recs):
@@ -234,6 +237,7 @@ def _opts(prob: Problem, stream):
     o.img_norm = int(prob.img_norm)
     o.freesurf = int(prob.freesurf)
     o.kernels = KERNELS[prob.kernels]
+    o.per_shot = int(prob.per_shot)
     if stream is not None:
         o.stream = stream
     elif torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
@@ -324,9 +328,10 @@ def smi_rtm(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None, out=None
     kd, pd, _ = _dobs_flat(dobs, cuda, None)
     w = smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
     o = _opts(prob, stream)
-    img, pimg = _out(out, int(np.prod(shape)), cuda, vp.device if cuda else None)
+    ns = len(srcs) if prob.per_shot else 1
+    img, pimg = _out(out, ns * int(np.prod(shape)), cuda, vp.device if cuda else None)
     _check(_lib.smi_rtm(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w), ctypes.byref(o), pd, pimg))
-    return img.reshape(shape)
+    return img.reshape((ns,) + tuple(shape)) if prob.per_shot else img.reshape(shape)
 
 
 @_on_model_device
@@ -338,11 +343,12 @@ def smi_fwi_gradient(vp, rho, prob: Problem, srcs, recs, stf, dobs, stream=None,
     kd, pd, _ = _dobs_flat(dobs, cuda, None)
     w = smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
     o = _opts(prob, stream)
-    g, pg = _out(out, int(np.prod(shape)), cuda, vp.device if cuda else None)
-    J, pJ = _empty(1, cuda, dtype=np.float64, device=vp.device if cuda else None)
+    ns = len(srcs) if prob.per_shot else 1
+    g, pg = _out(out, ns * int(np.prod(shape)), cuda, vp.device if cuda else None)
+    J, pJ = _empty(ns, cuda, dtype=np.float64, device=vp.device if cuda else None)
     _check(_lib.smi_fwi_gradient(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w),
                                  ctypes.byref(o), pd, pJ, pg))
-    return J, g.reshape(shape)
+    return J, (g.reshape((ns,) + tuple(shape)) if prob.per_shot else g.reshape(shape))
 
 
 @_on_model_device
@@ -461,6 +467,21 @@ def smi_dot(a, b, stream=None) -> float:
         st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
         _check(_lib.smi_dot(pa, pb, ka.numel(), ctypes.byref(out), st))
     return out.value
+
+
+def smi_footprint(vp, rho, prob: Problem, srcs, recs, stf, kind: str = "forward") -> int:
+    """Device bytes of a call from the sizes alone (no device work, no CFL /
+    dispersion / position checks)."""
+    m, keep_m, cuda, shape = _model(vp, rho, prob.d)
+    geo, keep_g, off = _geometry(srcs, recs)
+    ks, ps, _ = _as_f32(stf)
+    w = smi_wavelet(prob.nt, prob.dt, prob.fm, ps)
+    o = _opts(prob, None)
+    c = ctypes.c_size_t()
+    k = {"forward": 0, "rtm": 1, "gradient": 2, "vjp": 3, "gradient_family": 4}[kind]
+    _check(_lib.smi_footprint(ctypes.byref(m), ctypes.byref(geo), ctypes.byref(w), ctypes.byref(o), k,
+                              ctypes.byref(c)))
+    return c.value
 
 
 @_on_model_device

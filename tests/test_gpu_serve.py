@@ -15,7 +15,7 @@ def env():
     from paper_2311_02293_gb300 import serve
     torch.cuda.init()
     dev = torch.device("cuda:0")
-    reqs = serve.make_mix(10, scale=0.25)
+    reqs = serve.make_mix(10, scale=0.25, surveys=False)
     serve._prepare(reqs, dev)
     return serve, reqs, dev
 
@@ -42,6 +42,56 @@ def test_results_same_alone_and_in_mix(env):
     # the mix overlapped: some request started before another finished
     res = sorted(mix["results"], key=lambda x: x["t_start"])
     assert any(res[k + 1]["t_start"] < res[k]["t_end"] for k in range(len(res) - 1))
+
+
+def test_shots_of_one_survey_share_a_call(env):
+    """Survey mix (two 2D surveys, one 3D survey): queued single-shot
+    requests of one survey run as one shot-batched call with per-shot
+    results; every request's output equals the same request run alone."""
+    serve, _, dev = env
+    reqs = serve.make_mix(14, seed=123, scale=0.25, surveys=True, n2d=2, n3d=1)
+    serve._prepare(reqs, dev)
+    alone, _ = serve.run_alone(reqs, dev)
+    mix = serve.run_mix(reqs, dev, slots=2)
+    assert mix["failed"] == 0
+    assert mix["merged_calls"] >= 1 and mix["merged_requests"] >= 2 * mix["merged_calls"]
+    worst = 0.0
+    for r, a, b in zip(reqs, alone, mix["outputs"]):
+        e = _rel(b, a)
+        worst = max(worst, e)
+        assert e <= 1e-6, r.kind
+    print(f"survey mix: {mix['merged_calls']} merged calls carried {mix['merged_requests']} of {len(reqs)} "
+          f"requests; largest difference from alone {worst:.1e}")
+
+
+def test_per_shot_results_equal_single_shot_calls(env):
+    """opts.per_shot: a 3-shot gradient call returns each shot's gradient
+    and misfit, equal to the shot alone; the RTM images likewise."""
+    import torch
+    from paper_2311_02293_gb300 import synth as S
+    serve, _, dev = env
+    smi = serve.smi
+    w = S.layered_fault_2d(nz=60, nx=150, nt=300, nshot=3, order=8)
+    w.srcs[:, 1] = np.array([20.0, 70.0, 120.0]) * w.d[1]
+    vp, rho, stf = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (w.vp, w.rho, w.stf))
+    vpt = torch.from_numpy(w.vp_true).to(dev)
+    p = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb)
+    dobs = smi.smi_forward(vpt, rho, p, w.srcs, w.recs, stf, flat=True)
+    ps = smi.Problem(w.d, w.nt, w.dt, w.fm, order=w.order, nb=w.nb, per_shot=True)
+    J, g = smi.smi_fwi_gradient(vp, rho, ps, w.srcs, w.recs, stf, dobs)
+    img = smi.smi_rtm(vp, rho, ps, w.srcs, w.recs, stf, dobs)
+    assert g.shape == (3,) + tuple(w.vp.shape) and J.numel() == 3 and img.shape == g.shape
+    n = w.nt * len(w.recs[0])
+    Jsum, gsum = smi.smi_fwi_gradient(vp, rho, p, w.srcs, w.recs, stf, dobs)
+    assert abs(float(J.sum()) - float(Jsum.item())) <= 1e-9 * float(Jsum.item())
+    assert _rel(g.sum(0), gsum) <= 1e-6
+    for s in range(3):
+        one = w.subset([s])
+        Js, gs = smi.smi_fwi_gradient(vp, rho, p, one.srcs, one.recs, stf, dobs[s * n:(s + 1) * n])
+        assert abs(float(J[s]) - float(Js.item())) <= 1e-12 * float(Js.item())
+        assert _rel(g[s], gs) <= 1e-6
+        i1 = smi.smi_rtm(vp, rho, p, one.srcs, one.recs, stf, dobs[s * n:(s + 1) * n])
+        assert _rel(img[s], i1) <= 1e-6
 
 
 def test_budget_serialises_and_oversized_requests_fail(env):
