@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--serve-scale", type=float, default=0.5,
                     help="grid sizes and nt of the serving mix relative to the full mix")
     ap.add_argument("--serve-slots", type=int, default=8, help="concurrent request slots of the server")
+    ap.add_argument("--serve-rates", default="1.2,0.5",
+                    help="Poisson arrival rates as multiples of the one-at-a-time rate (comma list)")
     ap.add_argument("--serve-mix", default="surveys", choices=["surveys", "independent"],
                     help="requests as shots of seeded surveys (shareable calls) or independent draws")
     ap.add_argument("--profile", choices=["fwd", "rtm", "family", "grad2d"],
@@ -621,7 +623,8 @@ def run_serve(args):
     out = {}
     # Poisson arrivals at 1.2x and 0.5x the one-at-a-time rate (latency under load; the arrival rate
     # bounds the throughput), then every request queued at once (the server's capacity)
-    for name, factor in (("rate_1.2x", 1.2), ("rate_0.5x", 0.5), ("saturated", None)):
+    rates = [float(x) for x in args.serve_rates.split(",") if x.strip()]
+    for name, factor in [(f"rate_{r:g}x", r) for r in rates] + [("saturated", None)]:
         m = serve.run_mix(reqs, dev, slots=args.serve_slots, rate=factor * rate1 if factor else None)
         out[name] = {"requests_per_s": m["requests_per_s"], "gradient_shots_per_s": m["gradient_shots_per_s"],
                      "p50_s": m["p50_s"], "p99_s": m["p99_s"], "failed": m["failed"], "seconds": m["seconds"],

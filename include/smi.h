@@ -323,7 +323,9 @@ int smi_forward_noalloc(const smi_model *model, const smi_geometry *geom,
  * Single-shot requests of one survey -- same kind (forward, RTM without
  * img_norm, gradient), the same model arrays (vp, rho pointers), wavelet
  * (stf pointer, nt, dt, fm) and options -- that are queued when a slot admits
- * the first of them join its call, up to 64 shots while they fit the budget:
+ * the first of them join its call, up to 64 shots while they fit the budget
+ * and their extended grids sum to at most 2^24 points (one launch over them
+ * would not yet fill the GPU; a 300^3 shot joins none):
  * one shot-batched call whose shots share every launch, with per-shot results
  * (opts.per_shot) copied back to each request's own outputs.  Each request's
  * result equals the same request run alone. */

@@ -1113,9 +1113,26 @@ __global__ void k_dot(const float *a, const float *b, long long n, double *parti
 // 2^31 values (checked at set-up), so offsets are 32-bit.
 constexpr int kBandVals = 4;
 
+// Unsigned division of u < 2^31 by a divisor fixed for the launch, by a
+// multiply-high and a shift (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994: m = floor(2^32 (2^l - d) / d) + 1,
+// l = ceil(log2 d), q = (mulhi(m, u) + u) >> l).
+struct DivU {
+    unsigned m;
+    int l;
+    __device__ __forceinline__ void init(unsigned d)
+    {
+        l = 0;
+        while ((1ull << l) < d) l++;
+        m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    }
+    __device__ __forceinline__ unsigned div(unsigned u) const { return (__umulhi(m, u) + u) >> l; }
+};
+
 struct BandRegion {
     int a, sd, w0, w1, n, off;
     const int *lo;
+    DivU d0, d1;
     __device__ __forceinline__ BandRegion(const Bands &bd, int r)
     {
         a = r >> 1;
@@ -1126,12 +1143,16 @@ struct BandRegion {
         w1 = hi[1] - lo[1] + 1;
         n = w0 * w1 * (hi[2] - lo[2] + 1);
         off = (int)bd.off[a][sd];
+        if (n > 0) {
+            d0.init((unsigned)w0);
+            d1.init((unsigned)w1);
+        }
     }
     // flat field index of value u of the region
     __device__ __forceinline__ int node(const Grid &g, int u) const
     {
-        const int q = u / w0;
-        return (lo[0] + u - q * w0) + g.px * ((lo[1] + q % w1) + g.ne[1] * (lo[2] + q / w1));
+        const int q = (int)d0.div((unsigned)u), q1 = (int)d1.div((unsigned)q);
+        return (lo[0] + u - q * w0) + g.px * ((lo[1] + q - q1 * w1) + g.ne[1] * (lo[2] + q1));
     }
 };
 

@@ -9,7 +9,8 @@
 // the whole budget) fails with SMI_ERR_NOMEM instead of blocking the queue.
 // Single-shot requests that can share one call -- same kind, model arrays,
 // wavelet and options, i.e. shots of one survey -- are taken together when a
-// slot admits the first of them: their shots are concatenated into one
+// slot admits the first of them, while one launch over all of them would not
+// yet fill the GPU (2^24 grid points): their shots are concatenated into one
 // shot-batched call (the shots share every launch, blockIdx.z = shot) with
 // per-shot results (opts.per_shot), which are then copied to each request's
 // own outputs.  This is the GPU counterpart of the paper's batchwise job
@@ -32,7 +33,21 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr int kMaxMerge = 64;     // shots of one merged call
+constexpr int kMaxMerge = 64;                 // shots of one merged call
+constexpr long long kMergePoints = 1LL << 24;  // extended grid points of all shots of a merged call
+
+// Extended grid points of one shot of a request (the work of one of its
+// launches): shots are merged only while their sum stays below
+// kMergePoints, i.e. while one launch over all of them does not yet fill the
+// GPU on its own -- a 2D shot (about 0.7 M points) joins up to ~20 others, a
+// 300^3 shot none.
+long long shot_points(const smi_request &r)
+{
+    const long long e = 2LL * r.opts.nb;
+    long long n = (r.model.n1 + e) * (long long)(r.model.n2 + e);
+    if (r.model.ndim == 3) n *= r.model.n3 + e;
+    return n;
+}
 
 // A request that may join a merged call: one shot, and a kind with per-shot results.
 bool mergeable(const smi_request &r)
@@ -190,8 +205,10 @@ struct smi_server {
                 };
                 take(t);
                 // queued shots of the same survey join the call while they fit
+                const long long pts = shot_points(reqs[0]);
                 if (mergeable(reqs[0]))
-                    for (auto it = queue.begin(); it != queue.end() && (int)group.size() < kMaxMerge;) {
+                    for (auto it = queue.begin(); it != queue.end() && (int)group.size() < kMaxMerge &&
+                                                  (long long)(group.size() + 1) * pts <= kMergePoints;) {
                         const Job &u = jobs[*it];
                         if (mergeable(u.req) && same_call(reqs[0], u.req) && u.bytes <= budget - in_use) {
                             take(*it);

@@ -529,6 +529,14 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
         for (int r = 0; r < 4; r++) mz[r] = in_range(oz + r, it.lo[0], it.hi[0]);
         const bool mx = in_range(ox, it.lo[1], it.hi[1]);
         const int own = txi * TZ + 4 * tzi;           // own nodes in a core tile
+        // REC: whether the source stencil reaches this item's tile column and
+        // y range (the per-node test runs only then)
+        bool src_col = false;
+        if (MODE == REC) {
+            const Stencil &st = b.src[s];
+            src_col = st.first[0] <= z0 + TZ - 1 && st.first[0] + st.cnt[0] - 1 >= z0 && st.first[1] <= x0 + TX - 1 &&
+                      st.first[1] + st.cnt[1] - 1 >= x0 && st.first[2] <= yb && st.first[2] + st.cnt[2] - 1 >= ya;
+        }
 
         // y queue of own vy: entry l = plane y-N+l; planes before ya by plain loads
         float q[2 * N][4];
@@ -587,13 +595,19 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
             // accumulator of this plane (REC), loaded before the waits
             float accv[4] = {0.f, 0.f, 0.f, 0.f};
             long long accb = 0;
+            bool acc4 = false;                   // the quad as one aligned 16-byte access
             if (MODE == REC && mem && mx && in_range(y, it.lo[2], it.hi[2])) {
                 const long long n0 = g.H[0] - g.L[0] + 1, n1 = g.H[1] - g.L[1] + 1;
                 accb = (long long)s * g.nphys + (long long)(oz - g.L[0]) +
                        n0 * ((long long)(ox - g.L[1]) + n1 * (long long)(y - g.L[2]));
+                acc4 = mz[0] && mz[1] && mz[2] && mz[3] && (accb & 3) == 0;
+                if (acc4) {
+                    put(accv, *reinterpret_cast<const float4 *>(acc + accb));
+                } else {
 #pragma unroll
-                for (int r = 0; r < 4; r++)
-                    if (mz[r]) accv[r] = acc[accb + r];
+                    for (int r = 0; r < 4; r++)
+                        if (mz[r]) accv[r] = acc[accb + r];
+                }
             }
 #ifdef SMI_TIMING
             const long long tw0 = clock64();
@@ -756,21 +770,26 @@ k3_p(const __grid_constant__ CUtensorMap tm_vz, const __grid_constant__ CUtensor
                 float np[4];
                 if (MODE == REC) {
                     const Stencil &st = b.src[s];
-                    const float amp = src_scale * stf[step];
                     float lpv[4];
                     put(lpv, lds4(cs + 2 * CORE));
                     const bool kxy = in_range(ox, it.plo[1], it.phi[1]) && in_range(y, it.plo[2], it.phi[2]);
+                    float na[4];
+#pragma unroll
+                    for (int r = 0; r < 4; r++) na[r] = accv[r] + lpv[r] * (img_mode == 0 ? div[r] : pv[r]);
+                    if (acc4) *reinterpret_cast<float4 *>(acc + accb) = make_float4(na[0], na[1], na[2], na[3]);
 #pragma unroll
                     for (int r = 0; r < 4; r++) {
                         const int z = oz + r;
                         np[r] = pv[r];
                         if (!mz[r]) continue;
-                        acc[accb + r] = accv[r] + lpv[r] * (img_mode == 0 ? div[r] : pv[r]);
+                        if (!acc4) acc[accb + r] = na[r];
                         if (img_mode == 2) acc[(long long)b.nshot * g.nphys + accb + r] += pv[r] * pv[r];   // illumination
                         float pn = pv[r] + dt * Kv[r] * div[r];
-                        const int t0 = z - st.first[0], t1 = ox - st.first[1], t2 = y - st.first[2];
-                        if (t0 >= 0 && t0 < st.cnt[0] && t1 >= 0 && t1 < st.cnt[1] && t2 >= 0 && t2 < st.cnt[2])
-                            pn -= amp * st.w[0][t0] * st.w[1][t1] * st.w[2][t2];
+                        if (src_col) {           // the source stencil reaches this tile column
+                            const int t0 = z - st.first[0], t1 = ox - st.first[1], t2 = y - st.first[2];
+                            if (t0 >= 0 && t0 < st.cnt[0] && t1 >= 0 && t1 < st.cnt[1] && t2 >= 0 && t2 < st.cnt[2])
+                                pn -= src_scale * stf[step] * st.w[0][t0] * st.w[1][t1] * st.w[2][t2];
+                        }
                         np[r] = (kxy && in_range(z, it.plo[0], it.phi[0])) ? pn : 0.f;
                     }
                 } else {

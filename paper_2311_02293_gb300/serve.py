@@ -310,13 +310,14 @@ def run_mix(reqs, dev, slots: int = 8, budget: int = 0, rate: float | None = Non
 
         th = threading.Thread(target=submitter)
         th.start()
-        lat, results = [], []
+        results = []
         for k in range(len(reqs)):
             while tickets[k] is None:
                 time.sleep(0.001)
-            res = srv.wait(tickets[k][0])
-            lat.append(time.perf_counter() - tickets[k][1])
-            results.append(res)
+            results.append(srv.wait(tickets[k][0]))
+        # latency = the server's own submit-to-end time of each request (waiting
+        # on the tickets in order would charge a request for earlier ones)
+        lat = [r["t_end"] - r["t_submit"] for r in results]
         th.join()
         elapsed = time.perf_counter() - t0
         info = srv.info()
