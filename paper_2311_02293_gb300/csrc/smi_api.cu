@@ -528,7 +528,7 @@ int run(int kind, const smi_model *m, const smi_geometry *geo, const smi_wavelet
     cudaStream_t st = static_cast<cudaStream_t>(o->stream);
     long long launches = 0;
     Setup S;
-    int rc;
+    int rc = SMI_OK;
     {
         Arena ar(st);
         if (kind == 7) S = tape_in->S;        // set-up kept by the tape

@@ -42,7 +42,10 @@ namespace s3 {
 // Haloed ring: slots resident while their plane feeds a derivative (N+1
 // planes for the velocity kernel, N for the pressure kernel) plus PFP planes
 // of lead.  Core ring: the pointwise 32 x 16 tiles of one plane, SC slots.
-constexpr int PFP = SMI_PFP, SC = 3, CORE = TZ * TX;
+#ifndef SMI_SC
+#define SMI_SC 3            // core-tile ring depth of the interior kernels
+#endif
+constexpr int PFP = SMI_PFP, SC = SMI_SC, CORE = TZ * TX;
 
 // Tile classes of a launch (template CLS): ALLT every tile column of the box
 // (z / x CPML terms then come from the band kernels), INT the interior
