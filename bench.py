@@ -40,7 +40,7 @@ METRIC = "3D RTM grid-point updates/s (forward + adjoint + reconstruction, compu
 # over the kernels of one forward and one reverse step of the 340^3 salt
 # case with the box off (`bench.py --profile rtm --nt 30 --no-box`).  A
 # bench launch's traffic is this ratio times its algorithmic bytes.
-TRAFFIC_PER_ALGO_BYTE = (1.523, 1.605, 1.441)
+TRAFFIC_PER_ALGO_BYTE = (1.525, 1.597, 1.441)
 UNIT = "Gpt-updates/s"
 WORKLOAD = "3d_rtm_salt_300^3_order8_nt2500_8shots_150x150rec"
 

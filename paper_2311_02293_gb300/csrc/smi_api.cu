@@ -274,6 +274,8 @@ int validate_and_setup(const smi_model *m, const smi_geometry *geo, const smi_wa
             long long c = 1;
             for (int b = 0; b < 3; b++) c *= bd.hi[a][sd][b] - bd.lo[a][sd][b] + 1;
             bd.count += c;
+            for (int b = 0; b < 2; b++)
+                band_divisor((unsigned)(bd.hi[a][sd][b] - bd.lo[a][sd][b] + 1), bd.dm[a][sd][b], bd.dl[a][sd][b]);
         }
     if (bd.count >= (1LL << 31)) return fail(SMI_ERR_UNSUPPORTED, "boundary bands of one step exceed 2^31 values");
     if (sizes_only) {

@@ -80,7 +80,20 @@ struct Bands {
     void *data;                  // [nshot][nt][count] of float / half / bf16
     float *scale;                // [nshot][nt][3][2] (16-bit storage only)
     int nt;                      // stored samples per shot (steps 0, dr, 2dr, ...)
+    // division of a region's value index by its z extent and by its x extent:
+    // multiplier and shift per (axis, side, divisor), see band_divisor()
+    unsigned dm[3][2][2];
+    int dl[3][2][2];
 };
+// Multiplier m and shift l with u / d = (mulhi(m, u) + u) >> l for every
+// u < 2^31 (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994: l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1).
+inline void band_divisor(unsigned d, unsigned &m, int &l)
+{
+    l = 0;
+    while ((1ull << l) < d) l++;
+    m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+}
 
 // ---------------------------------------------------------------------------
 // Host set-up (smi_setup.cpp): exact FP64 arithmetic, rounded to FP32 tables.

@@ -1113,26 +1113,11 @@ __global__ void k_dot(const float *a, const float *b, long long n, double *parti
 // 2^31 values (checked at set-up), so offsets are 32-bit.
 constexpr int kBandVals = 4;
 
-// Unsigned division of u < 2^31 by a divisor fixed for the launch, by a
-// multiply-high and a shift (Granlund and Montgomery, "Division by invariant
-// integers using multiplication", 1994: m = floor(2^32 (2^l - d) / d) + 1,
-// l = ceil(log2 d), q = (mulhi(m, u) + u) >> l).
-struct DivU {
-    unsigned m;
-    int l;
-    __device__ __forceinline__ void init(unsigned d)
-    {
-        l = 0;
-        while ((1ull << l) < d) l++;
-        m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
-    }
-    __device__ __forceinline__ unsigned div(unsigned u) const { return (__umulhi(m, u) + u) >> l; }
-};
-
 struct BandRegion {
     int a, sd, w0, w1, n, off;
     const int *lo;
-    DivU d0, d1;
+    unsigned m0, m1;                  // u / w0 and q / w1 by multiply-high (band_divisor)
+    int l0, l1;
     __device__ __forceinline__ BandRegion(const Bands &bd, int r)
     {
         a = r >> 1;
@@ -1143,16 +1128,18 @@ struct BandRegion {
         w1 = hi[1] - lo[1] + 1;
         n = w0 * w1 * (hi[2] - lo[2] + 1);
         off = (int)bd.off[a][sd];
-        if (n > 0) {
-            d0.init((unsigned)w0);
-            d1.init((unsigned)w1);
-        }
+        m0 = bd.dm[a][sd][0];
+        l0 = bd.dl[a][sd][0];
+        m1 = bd.dm[a][sd][1];
+        l1 = bd.dl[a][sd][1];
     }
     // flat field index of value u of the region
     __device__ __forceinline__ int node(const Grid &g, int u) const
     {
-        const int q = (int)d0.div((unsigned)u), q1 = (int)d1.div((unsigned)q);
-        return (lo[0] + u - q * w0) + g.px * ((lo[1] + q - q1 * w1) + g.ne[1] * (lo[2] + q1));
+        const unsigned uu = (unsigned)u;
+        const unsigned q = (__umulhi(m0, uu) + uu) >> l0;
+        const unsigned q1 = (__umulhi(m1, q) + q) >> l1;
+        return (lo[0] + u - (int)q * w0) + g.px * ((lo[1] + (int)q - (int)q1 * w1) + g.ne[1] * (lo[2] + (int)q1));
     }
 };
 
