@@ -328,7 +328,9 @@ int smi_forward_noalloc(const smi_model *model, const smi_geometry *geom,
  * would not yet fill the GPU; a 300^3 shot joins none):
  * one shot-batched call whose shots share every launch, with per-shot results
  * (opts.per_shot) copied back to each request's own outputs.  Each request's
- * result equals the same request run alone. */
+ * result equals the same request run alone.  If a merged call fails (a
+ * request invalid on its own: a position outside the model, CFL), its
+ * requests run one by one, so that only the invalid one reports the error. */
 typedef struct smi_server smi_server;
 
 typedef struct {

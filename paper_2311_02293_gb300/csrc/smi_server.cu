@@ -222,25 +222,32 @@ struct smi_server {
                     merged_requests += (long long)group.size();
                 }
             }
-            int rc;
+            std::vector<int> rcs(group.size(), SMI_OK);
+            std::vector<std::string> errs(group.size());
             std::string err;
-            if (group.size() == 1) {
-                rc = run_one(reqs[0], st);
-                if (rc) err = smi_last_error();
-            } else {
-                rc = run_merged(reqs, st, err);
+            if (group.size() > 1 && run_merged(reqs, st, err) != SMI_OK) {
+                // The merged call failed (a request that is invalid on its own --
+                // a position outside the model, CFL -- fails the whole call):
+                // run the requests one by one, so that only such a request fails.
+                for (size_t k = 0; k < reqs.size(); k++) {
+                    rcs[k] = run_one(reqs[k], st);
+                    if (rcs[k]) errs[k] = smi_last_error();
+                }
+            } else if (group.size() == 1) {
+                rcs[0] = run_one(reqs[0], st);
+                if (rcs[0]) errs[0] = smi_last_error();
             }
             {
                 std::lock_guard<std::mutex> lk(mu);
                 const double t_now = now();
-                for (long long u : group) {
-                    Job &j = jobs[u];
+                for (size_t k = 0; k < group.size(); k++) {
+                    Job &j = jobs[group[k]];
                     j.state = 2;
-                    j.status = rc;
-                    j.error = err;
+                    j.status = rcs[k];
+                    j.error = errs[k];
                     j.t_end = t_now;
                     in_use -= j.bytes;
-                    if (rc) failed++;
+                    if (rcs[k]) failed++;
                     else completed++;
                 }
             }

@@ -64,6 +64,29 @@ def test_shots_of_one_survey_share_a_call(env):
           f"requests; largest difference from alone {worst:.1e}")
 
 
+def test_an_invalid_request_fails_alone_in_a_merged_call(env):
+    """Submission sizes a request without checking positions, so a request
+    whose source lies outside the model can join a merged call: that call
+    fails, the server runs the group's requests one by one, and only the
+    invalid request reports the error."""
+    serve, _, dev = env
+    reqs = [r for r in serve.make_mix(16, seed=321, scale=0.25, surveys=True, n2d=1, n3d=1)
+            if r.w.ndim == 2][:5]
+    assert len(reqs) == 5
+    serve._prepare(reqs, dev)
+    alone, _ = serve.run_alone(reqs, dev)
+    bad = reqs[2]
+    bad.w.srcs = bad.w.srcs.copy()
+    bad.w.srcs[0, 1] = 1e7                 # far outside the model
+    mix = serve.run_mix(reqs, dev, slots=1)
+    status = [r["status"] for r in mix["results"]]
+    assert status[2] == -1, status
+    assert all(st == 0 for k, st in enumerate(status) if k != 2), status
+    assert mix["merged_calls"] >= 1
+    for k in (0, 1, 3, 4):
+        assert _rel(mix["outputs"][k], alone[k]) <= 1e-6
+
+
 def test_per_shot_results_equal_single_shot_calls(env):
     """opts.per_shot: a 3-shot gradient call returns each shot's gradient
     and misfit, equal to the shot alone; the RTM images likewise."""
