@@ -28,16 +28,10 @@ constexpr int kThreads = 256;
 #define SMI_CPML_UZ 2        // adjoint kinds; the forward kinds take twice as many
 #endif
 constexpr int kCpmlChunk = SMI_CPML_U;     // nodes per thread along x, CPML kernel of the x piece
-constexpr int kCpmlChunkZ = SMI_CPML_UZ;   // nodes per lane along x, CPML kernel of the z piece (adjoint)
+constexpr int kCpmlChunkZ = SMI_CPML_UZ;   // x lines a unit of the z-piece kernel k_cpml_zp (adjoint kinds)
 constexpr int kMaxBlocksX = 152 * 16;
-#ifndef SMI_CPML_ZP
-#define SMI_CPML_ZP 1        // z piece: persistent k_cpml_zp (1) or one unit a warp, k_cpml_z (0)
-#endif
 #ifndef SMI_CPML_ZP_MINB
 #define SMI_CPML_ZP_MINB 4   // resident 256-thread blocks of k_cpml_zp (its warps loop: fewer are needed)
-#endif
-#ifndef SMI_CPML_XW
-#define SMI_CPML_XW 1        // adjoint x piece: walking k_cpml_xw (1) or one chunk a thread, k_cpml_x (0)
 #endif
 #ifndef SMI_CPML_XW_U
 #define SMI_CPML_XW_U 4      // nodes a chunk of the walk
@@ -47,9 +41,6 @@ constexpr int kMaxBlocksX = 152 * 16;
 #endif
 #ifndef SMI_CPML_MINB_F
 #define SMI_CPML_MINB_F 4
-#endif
-#ifndef SMI_CPML_MINB_A
-#define SMI_CPML_MINB_A 7
 #endif
 
 __device__ __forceinline__ long long gidx(const Grid &g, int i1, int i2, int i3)
@@ -714,18 +705,16 @@ __device__ __forceinline__ void cpml_zwarp(const Grid &g, const Fields &f, const
     }
 }
 
-// Resident 256-thread blocks per SM that the register budget must allow
-// (the CPML kernels are load-latency bound: more warps hide more latency).
-// Measured on the 340^3 RTM step, box off, 30 steps: without a bound
-// (62-95 registers) forward 18.3 ms, adjoint 24.2 ms; forward kinds 4
-// blocks (64 registers) and adjoint kinds 7 (36 registers, a few spilled)
-// 17.8 ms and 21.6 ms; adjoint 5 / 6 / 8 gave 22.4 / 22.2 / 21.7 ms.
-__host__ __device__ constexpr int cpml_min_blocks(int kind) { return kind >= kAV ? SMI_CPML_MINB_A : SMI_CPML_MINB_F; }
+// Resident 256-thread blocks per SM that k_cpml_x's register budget must
+// allow (the forward kinds' x piece is load-latency bound: more warps hide
+// more latency).  Measured on the 340^3 RTM step, box off, 30 steps: without
+// a bound (62-95 registers) forward 18.3 ms, with 4 blocks (64 registers)
+// 17.8 ms.
 
 // x piece: block = ZB z indices x 256/ZB y indices (ZB = 64 in 3D, 256 in 2D
 // where y has one index); blockIdx.y = chunk along x, blockIdx.z = shot.
 template <int N, int KIND>
-__global__ void __launch_bounds__(256, cpml_min_blocks(KIND)) k_cpml_x(Grid g, Batch b, Fields f, Pieces P, int m)
+__global__ void __launch_bounds__(256, SMI_CPML_MINB_F) k_cpml_x(Grid g, Batch b, Fields f, Pieces P, int m)
 {
     const Piece &p = P.q[1];
     const int zb = g.ndim == 3 ? 64 : 256;
@@ -754,24 +743,6 @@ __global__ void __launch_bounds__(256, SMI_CPML_XW_MINB) k_cpml_xw(Grid g, Batch
     int lo[3], hi[3];
     box_at((KIND == kFV || KIND == kFP) ? b.tab_src : b.tab_rec, b.nt1, s, m, lo, hi);
     cpml_xwalk<N, KIND, SMI_CPML_XW_U>(g, f, p, s, c0, cr, blockIdx.y, lo, hi);
-}
-
-// z piece: 8 warps a block, warp -> (z segment, y index); blockIdx.y =
-// chunk along x, blockIdx.z = shot.
-template <int N, int KIND>
-__global__ void __launch_bounds__(256, cpml_min_blocks(KIND)) k_cpml_z(Grid g, Batch b, Fields f, Pieces P, int m)
-{
-    constexpr int BW = 32 - (2 * N - 1);     // owned lanes of a warp
-    const Piece &p = P.q[0];
-    const int nzw = (p.iv[0][1] + BW - 1) / BW + (p.iv[0][3] + BW - 1) / BW;
-    const int gw = blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int zw = gw % nzw, cr = gw / nzw;
-    if (cr >= p.cnt[2]) return;                                   // warp-uniform
-    const int s = blockIdx.z;
-    int lo[3], hi[3];
-    box_at((KIND == kFV || KIND == kFP) ? b.tab_src : b.tab_rec, b.nt1, s, m, lo, hi);
-    constexpr int UZ = (KIND == kFV || KIND == kFP) ? 2 * kCpmlChunkZ : kCpmlChunkZ;
-    cpml_zwarp<N, KIND, UZ>(g, f, P, p, s, threadIdx.x & 31, zw, cr, blockIdx.y, lo, hi);
 }
 
 // z piece, persistent: blockIdx.y = z warp segment (those of the low band,
@@ -1650,8 +1621,9 @@ Pieces make_pieces(const Grid &g, const int lo[3], const int hi[3], int w_lo, in
         }
         if (cnt == 0) continue;
         P.n++;
-        // launch shape (k_cpml_z / k_cpml_x): y = chunks along x, x = z warps
-        // x y lines (z piece) or blocks of 64 z x 4 y lines (x piece)
+        // x piece: blocks of 64 z x 4 y lines (k_cpml_x: y = chunks along x;
+        // k_cpml_xw: y = band).  z piece: nonzero counts mark the piece as
+        // present (k_cpml_zp sizes its own persistent launch).
         const int u = a == 0 ? uz : kCpmlChunk;
         p.chunks = (p.iv[1][1] + u - 1) / u + (p.iv[1][3] + u - 1) / u;
         if (a == 0) {
@@ -1704,26 +1676,19 @@ void corr_launch(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, i
         const Piece &p = P.q[a];
         if (p.blocks == 0 || p.chunks == 0) continue;
         const dim3 grid(p.blocks, p.chunks, b.nshot);
-        if (a == 0 && SMI_CPML_ZP) {
+        if (a == 0) {
             if (kind == kFV) zp_launch<N, kFV>(lc, g, b, f, P, m);
             else if (kind == kFP) zp_launch<N, kFP>(lc, g, b, f, P, m);
             else if (kind == kAV) zp_launch<N, kAV>(lc, g, b, f, P, m);
             else zp_launch<N, kAP>(lc, g, b, f, P, m);
             continue;                                     // counts its own launch
-        } else if (a == 0) {
-            if (kind == kFV) k_cpml_z<N, kFV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-            else if (kind == kFP) k_cpml_z<N, kFP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-            else if (kind == kAV) k_cpml_z<N, kAV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-            else k_cpml_z<N, kAP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-        } else if (SMI_CPML_XW && kind >= kAV) {   // measured: the walk pays in the adjoint kinds only
+        } else if (kind >= kAV) {                          // measured: the walk pays in the adjoint kinds only
             const dim3 gw(p.blocks, 2, b.nshot);
             if (kind == kAV) k_cpml_xw<N, kAV><<<gw, 256, 0, S(lc)>>>(g, b, f, P, m);
             else k_cpml_xw<N, kAP><<<gw, 256, 0, S(lc)>>>(g, b, f, P, m);
         } else {
             if (kind == kFV) k_cpml_x<N, kFV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-            else if (kind == kFP) k_cpml_x<N, kFP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-            else if (kind == kAV) k_cpml_x<N, kAV><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
-            else k_cpml_x<N, kAP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
+            else k_cpml_x<N, kFP><<<grid, 256, 0, S(lc)>>>(g, b, f, P, m);
         }
         ++*lc.launches;
     }
