@@ -36,6 +36,9 @@ constexpr int kMaxBlocksX = 152 * 16;
 #ifndef SMI_CPML_XW_U
 #define SMI_CPML_XW_U 4      // nodes a chunk of the walk
 #endif
+#ifndef SMI_CPML_XW_PARTS
+#define SMI_CPML_XW_PARTS 2  // runs a band of k_cpml_xw is cut into (more lines walk at once)
+#endif
 #ifndef SMI_CPML_XW_MINB
 #define SMI_CPML_XW_MINB 4   // resident 256-thread blocks of k_cpml_xw
 #endif
@@ -555,7 +558,7 @@ __device__ __forceinline__ void cpml_chunk(const Grid &g, const Fields &f, const
 // for every U nodes).  Same arithmetic as cpml_chunk.
 template <int N, int KIND, int U>
 __device__ __forceinline__ void cpml_xwalk(const Grid &g, const Fields &f, const Piece &p, int s, int c0, int cr,
-                                           int seg, const int lo[3], const int hi[3])
+                                           int seg, int part, int nparts, const int lo[3], const int hi[3])
 {
     constexpr int W = 1;
     constexpr bool VK = KIND == kFV || KIND == kAV;
@@ -565,8 +568,12 @@ __device__ __forceinline__ void cpml_xwalk(const Grid &g, const Fields &f, const
     i[0] = iv_map(p.iv[0], c0);
     i[2] = iv_map(p.iv[2], cr);
     if (i[0] < lo[0] || i[0] > hi[0] || i[2] < lo[2] || i[2] > hi[2]) return;
-    const int js = max(p.iv[W][2 * seg], lo[W]);
-    const int jend = min(p.iv[W][2 * seg] + p.iv[W][2 * seg + 1] - 1, hi[W]);
+    // the band's chunks, cut into nparts runs of whole chunks; this thread walks run `part`
+    const int jb = max(p.iv[W][2 * seg], lo[W]);
+    const int jl = min(p.iv[W][2 * seg] + p.iv[W][2 * seg + 1] - 1, hi[W]);
+    const int per = ((jl - jb + U) / U + nparts - 1) / nparts * U;
+    const int js = jb + part * per;
+    const int jend = min(jl, js + per - 1);
     if (js > jend) return;
     i[W] = js;
     const int k0 = gidx32(g, i[0], i[1], i[2]);
@@ -729,7 +736,9 @@ __global__ void __launch_bounds__(256, SMI_CPML_MINB_F) k_cpml_x(Grid g, Batch b
 }
 
 // x piece, walking (cpml_xwalk): block = ZB z indices x 256/ZB y indices
-// as in k_cpml_x; blockIdx.y = band (low, high), blockIdx.z = shot.
+// as in k_cpml_x; blockIdx.y = band (low, high) x run of the band
+// (SMI_CPML_XW_PARTS runs a band, so that enough lines walk at once),
+// blockIdx.z = shot.
 template <int N, int KIND>
 __global__ void __launch_bounds__(256, SMI_CPML_XW_MINB) k_cpml_xw(Grid g, Batch b, Fields f, Pieces P, int m)
 {
@@ -738,11 +747,12 @@ __global__ void __launch_bounds__(256, SMI_CPML_XW_MINB) k_cpml_xw(Grid g, Batch
     const int nbz = (p.cnt[0] + zb - 1) / zb;
     const int bz = blockIdx.x % nbz, br = blockIdx.x / nbz;
     const int c0 = bz * zb + (int)threadIdx.x % zb, cr = br * (256 / zb) + (int)threadIdx.x / zb;
-    if (c0 >= p.cnt[0] || cr >= p.cnt[2] || p.iv[1][2 * blockIdx.y + 1] == 0) return;
+    const int side = blockIdx.y / SMI_CPML_XW_PARTS, part = blockIdx.y % SMI_CPML_XW_PARTS;
+    if (c0 >= p.cnt[0] || cr >= p.cnt[2] || p.iv[1][2 * side + 1] == 0) return;
     const int s = blockIdx.z;
     int lo[3], hi[3];
     box_at((KIND == kFV || KIND == kFP) ? b.tab_src : b.tab_rec, b.nt1, s, m, lo, hi);
-    cpml_xwalk<N, KIND, SMI_CPML_XW_U>(g, f, p, s, c0, cr, blockIdx.y, lo, hi);
+    cpml_xwalk<N, KIND, SMI_CPML_XW_U>(g, f, p, s, c0, cr, side, part, SMI_CPML_XW_PARTS, lo, hi);
 }
 
 // z piece, persistent: blockIdx.y = z warp segment (those of the low band,
@@ -1683,7 +1693,7 @@ void corr_launch(const LaunchCtx &lc, const Grid &g, const Batch &b, Fields f, i
             else zp_launch<N, kAP>(lc, g, b, f, P, m);
             continue;                                     // counts its own launch
         } else if (kind >= kAV) {                          // measured: the walk pays in the adjoint kinds only
-            const dim3 gw(p.blocks, 2, b.nshot);
+            const dim3 gw(p.blocks, 2 * SMI_CPML_XW_PARTS, b.nshot);
             if (kind == kAV) k_cpml_xw<N, kAV><<<gw, 256, 0, S(lc)>>>(g, b, f, P, m);
             else k_cpml_xw<N, kAP><<<gw, 256, 0, S(lc)>>>(g, b, f, P, m);
         } else {
