@@ -551,11 +551,12 @@ __device__ __forceinline__ void cpml_chunk(const Grid &g, const Fields &f, const
 }
 
 // x piece, walking: a thread takes one line along x (fixed z index i0 and y
-// index i2) and walks one band of it (blockIdx.y: the low band, then the
-// high band) in chunks of U nodes.  The window of h along x rolls from chunk
-// to chunk: the last 2N - 1 values of one chunk's window open the next, so
-// each h value is loaded once per line (cpml_chunk loads U + 2N - 1 values
-// for every U nodes).  Same arithmetic as cpml_chunk.
+// index i2) and walks run `part` of one band of it (seg: the low or the high
+// band, cut into nparts runs of whole chunks) in chunks of U nodes.  The
+// window of h along x rolls from chunk to chunk: the last 2N - 1 values of
+// one chunk's window open the next, so each h value is loaded once per run
+// (cpml_chunk loads U + 2N - 1 values for every U nodes).  Same arithmetic as
+// cpml_chunk.
 template <int N, int KIND, int U>
 __device__ __forceinline__ void cpml_xwalk(const Grid &g, const Fields &f, const Piece &p, int s, int c0, int cr,
                                            int seg, int part, int nparts, const int lo[3], const int hi[3])
